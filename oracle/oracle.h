@@ -1,0 +1,112 @@
+/*
+ * FP64 CPU oracle for the rest-frame FDTD/PIC time step of MITHRA 2.0
+ * (A. Fallahi, arXiv:2009.13645).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this code: only the test-suite, the smoke check and the bench's CPU
+ * baseline leg use it.  It shares no code, header or constant table with the
+ * CUDA library; both receive the same lab-frame particle arrays from the
+ * seeded input generator and nothing else.
+ *
+ * The oracle is plain, serial and unblocked: every function follows one
+ * equation of the manual in its own order and notation.
+ *
+ * Parity pins (tests/test_oracle_*.py) tie it to what the paper and the
+ * mathematics fix: the discrete dispersion relations (Eqs. numericalDispersionCD,
+ * NSFDDispersionCD), the exact one-cell shift of NSFD at c dt = dz, the Mur
+ * coefficient formulas and the Engquist-Majda reflection curves, discrete
+ * charge continuity, the Lorentz gauge residual, Boris rotation invariants,
+ * Lorentz invariants of the transformed undulator field, the single-electron
+ * undulator trajectory, and the on-axis resonance.
+ * The absolute radiated power of undulator radiation through a finite plane
+ * is parity unpinned (the manual prints only figure curves for it); its
+ * plane-wave flux and its coherent scaling are pinned.
+ */
+#ifndef MITHRA_ORACLE_H
+#define MITHRA_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_params {
+    /* mesh, lab frame (Sec. MESH: mesh-lengths, mesh-resolution, mesh-center) */
+    int32_t nx, ny, nz;
+    double dx, dy, dz;        /* lab resolution; the rest frame uses dz*gamma0 (Eq. LorentzTransformB) */
+    double cx, cy, cz;        /* mesh centre relative to the bunch reference point, lab */
+    int32_t solver;           /* 0 NSFD (Eq. updateEquation), 1 FD (central differences) */
+    double courant;           /* FD: dt = courant x the CFL bound (Eq. CFLcondition) */
+    int32_t mur_order;        /* 1 or 2 */
+    int32_t space_charge;     /* 0: phi == 0 and no charge deposition */
+    int32_t substeps;         /* N in dt_b = dt / N */
+    int32_t periodic[3];      /* test-only periodic axes (no Mur on them) */
+    double plane_dist;        /* lab distance of the power plane ahead of the bunch reference */
+    double norm_freq;         /* normalised frequency h of the power diagnostic */
+    /* undulator (Sec. UNDULATOR) */
+    int32_t und_kind;         /* -1 none, 0 planar static, 1 helical static, 2 optical plane wave, 3 optical Gaussian */
+    double K;                 /* undulator parameter, or a0 for an optical undulator */
+    double lambda_u;          /* period, or laser wavelength */
+    double n_periods;
+    double pol_deg;
+    double waist;
+    double pulse_fwhm;        /* c tau, intensity FWHM */
+    int32_t signal;           /* 0 modulated Gaussian, 1 flat-top */
+    double dist_head;
+    /* bunch */
+    double gamma;             /* mean Lorentz factor (sets the rest frame) */
+    double charge_e;          /* electrons in the bunch */
+    double sig_z;             /* lab rms length: the head sits 3 sig_z ahead of the centre */
+} orc_params;
+
+typedef struct orc_run orc_run;
+
+/* Create a run from lab-frame particles lab6 (np x 6: x, y, z, ux, uy, uz; copied). */
+orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np);
+void orc_destroy(orc_run *r);
+
+/* Advance nsteps field steps (Sec. step order: E/B, push+deposit, stencil, Mur, power). */
+void orc_step(orc_run *r, int64_t nsteps);
+
+/* Derived constants: out[0..] = gamma0, beta0, dx, dy, dz, dt, dtb, A_nsfd, x0, y0, z0, T0,
+   omega_h, M (window), kp (plane index), z_ref, q (macro charge), kstar, kb. */
+void orc_info(const orc_run *r, double out[19]);
+
+/* Field access.  which: 0..3 = Ax, Ay, Az, phi at level lev (0: n, 1: n+1 of the current step);
+   4..7 = Jx, Jy, Jz, rho (last deposit); 8..13 = Ex, Ey, Ez, Bx, By, Bz at nodes (last emitted). */
+void orc_get_field(const orc_run *r, int which, int lev, double *out);
+void orc_set_field(orc_run *r, int which, int lev, const double *in);
+
+/* Particles in the rest frame: (np x 6) x, y, z, ux, uy, uz. */
+void orc_get_particles(const orc_run *r, double *out6);
+void orc_set_particles(orc_run *r, const double *rest6);
+int64_t orc_num_particles(const orc_run *r);
+
+/* Per-step series (length = steps taken): lab power (W), lab time (s), on-axis Ex (V/m). */
+int64_t orc_series(const orc_run *r, double *power_lab, double *t_lab, double *onaxis_ex);
+
+/* Diagnostics from the last emitted E/B and the current particles: field energy (J, rest
+   frame) and the bunching factor at the rest-frame ponderomotive wavenumber kb:
+   bunching[0] = |<exp(j kb z)>|, bunching[1], bunching[2] = real and imaginary parts. */
+void orc_diag(const orc_run *r, double *field_energy, double *bunching);
+
+/* Single pieces, for the pins. */
+void orc_external_field(const orc_run *r, double x, double y, double z, double t,
+                        double E[3], double B[3]);
+void orc_lab_field(const orc_run *r, double xl, double yl, double zeta, double tl,
+                   double Ep[3], double Bp[3]);
+void orc_boris(double u[3], const double E[3], const double B[3], double dtb);
+/* One Mur update of component `which` (0..3): writes boundary points of level n+2
+   from levels n+2 (interior), n+1, n. */
+void orc_mur(orc_run *r, int which);
+/* The interior stencil alone for component `which`. */
+void orc_stencil(orc_run *r, int which);
+void orc_rotate_levels(orc_run *r);
+/* Deposition alone: J of the move old6 -> new6 (rest frame, n x 6) and rho at new6. */
+void orc_deposit_moves(orc_run *r, const double *old6, const double *new6, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
