@@ -1,0 +1,196 @@
+/*
+ * mithra.h - C ABI of the GB300 implementation of the rest-frame FDTD/PIC
+ * time step of MITHRA 2.0 (A. Fallahi, arXiv:2009.13645).
+ *
+ * One run = one free-electron-laser interaction solved in the frame moving
+ * with the bunch (manual Ch. "Methodology"): an explicit NSFD/FD update of the
+ * potential wave equations for A and phi (Sec. "FDTD for Wave Equation",
+ * "FDTD for Scalar Potential") with Mur absorbing boundaries (Sec. "Boundary
+ * Truncation"), coupled to a particle-in-cell loop (Sec. "Particle In Cell":
+ * field evaluation, linear gather, Boris push in the Lorentz-transformed
+ * undulator or laser field, Umeda zigzag current and charge deposition).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: MITHRA_OK (0) or a negative MITHRA_E* code.  The library
+ *    never aborts and never prints; mithra_last_error() returns a
+ *    thread-local message describing the last failure on the calling thread.
+ *  - Units: SI.  Input structs are in the LABORATORY frame, as the manual's
+ *    job files are (Ch. "User Interface": all parameters are lab-frame);
+ *    the library boosts them to the rest frame itself.
+ *  - Ownership: input structs and arrays are copied during the call; the
+ *    caller keeps them.  Output buffers are caller-owned host memory.  Device
+ *    memory belongs to the run handle and is released by mithra_destroy().
+ *  - Device memory comes from the allocator installed with
+ *    mithra_set_allocator() (cudaMalloc/cudaFree when none is installed).
+ *  - All work of a run is enqueued on one CUDA stream (mithra_set_stream(),
+ *    else a non-blocking stream the library creates); mithra_step() returns
+ *    once the work is enqueued.
+ *  - Thread safety: calls on different handles may come from different
+ *    threads; calls on one handle must be serialised by the caller.
+ */
+#ifndef MITHRA_H
+#define MITHRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MITHRA_OK 0
+#define MITHRA_EINVAL (-1)     /* bad shape, non-finite input, unknown option */
+#define MITHRA_ENOMEM (-2)     /* device allocation failed / over the HBM budget */
+#define MITHRA_ERANGE (-3)     /* caller buffer too small */
+#define MITHRA_ETIMEDOUT (-4)  /* a bounded device-side wait expired */
+#define MITHRA_EDIVERGED (-5)  /* non-finite field energy */
+#define MITHRA_ENOTFOUND (-6)  /* unknown ticket */
+#define MITHRA_EAGAIN (-7)     /* request queue full, try again */
+#define MITHRA_ECUDA (-8)      /* a CUDA runtime call failed */
+
+typedef struct mithra_run *mithra_t;
+
+/* Mesh and solver options (manual Sec. MESH).  Lengths in the lab frame. */
+typedef struct mithra_grid {
+    int32_t nx, ny, nz;        /* nodes per axis, each >= 6 */
+    double dx, dy, dz;         /* lab resolution; the rest frame uses gamma0*dz (Sec. "Lorentz Transformation") */
+    double cx, cy, cz;         /* mesh centre relative to the bunch reference point (lab) */
+    int32_t solver;            /* 0 NSFD (Eq. updateEquation), 1 FD (central differences) */
+    double courant;            /* FD only: dt = courant x CFL bound (Eq. CFLcondition); NSFD forces c dt = dz */
+    int32_t mur_order;         /* 1 or 2 (Sec. "First/Second Order ABCs") */
+    int32_t space_charge;      /* 0: phi == 0, no charge deposition (Sec. "FDTD for Scalar Potential") */
+    int32_t precision;         /* 0 FP64 everywhere; 1 FP32 fields/offsets, FP64 momentum, external field, diagnostics */
+    int32_t substeps;          /* N in dt_b = dt/N (Sec. "Update Algorithm"); >= 1 */
+    double power_plane_dist;   /* lab distance of the radiated-power plane ahead of the bunch (Sec. FEL-OUTPUT) */
+    double norm_freq;          /* normalised frequency h of the radiated-power diagnostic */
+    int32_t sort_every;        /* counting sort by cell every S steps; 0 = default (20), < 0 = never */
+} mithra_grid;
+
+/* Undulator (manual Sec. UNDULATOR, Sec. "Field Initialization"). */
+typedef struct mithra_undulator {
+    int32_t kind;              /* -1 none, 0 planar static, 1 helical static (two planar, 90 deg, lambda/4 apart),
+                                  2 optical plane wave, 3 optical Gaussian beam (counter-propagating, -z) */
+    double K;                  /* undulator parameter K, or strength a0 of an optical undulator */
+    double lambda;             /* undulator period, or laser wavelength; kind -1: rest-frame diagnostic wavelength */
+    double n_periods;          /* static: undulator length in periods */
+    double pol_deg;            /* polarisation angle from the x axis, degrees */
+    double waist;              /* Gaussian beam waist w0 */
+    double pulse_fwhm;         /* c * tau, intensity FWHM (Eq. signalTypes) */
+    int32_t signal;            /* 0 modulated Gaussian, 1 flat-top (Gaussian rise, then constant) */
+    double dist_to_bunch_head; /* lab distance from the bunch head to the undulator entrance / pulse */
+} mithra_undulator;
+
+/* Bunch given as macro-particles (bunch type "file", Sec. BUNCH). */
+typedef struct mithra_bunch {
+    int64_t n;                 /* number of macro-particles (>= 0) */
+    double charge_e;           /* bunch charge in electrons (> 0 when n > 0) */
+    double gamma;              /* mean Lorentz factor; with the undulator it fixes the rest frame */
+    double sig_z;              /* lab rms length; the bunch head is taken 3 sig_z ahead of the reference point */
+    const double *lab_particles; /* host, n x 6 row-major: x, y, z (m, relative to the bunch reference point),
+                                    gamma*beta_x, gamma*beta_y, gamma*beta_z; lab frame at t' = 0 */
+} mithra_bunch;
+
+/* Install the device allocator used by every later mithra_create (process-wide).
+   alloc(ctx, bytes) returns a device pointer or NULL; free(ctx, ptr).  Pass NULLs to restore
+   cudaMalloc/cudaFree.  Runs created earlier keep the allocator they were created with. */
+typedef void *(*mithra_alloc_fn)(void *ctx, size_t bytes);
+typedef void (*mithra_free_fn)(void *ctx, void *ptr);
+int mithra_set_allocator(mithra_alloc_fn alloc, mithra_free_fn free_fn, void *ctx);
+
+/* Create a run on the current CUDA device: validate and adjust the mesh as the manual's
+   checks do (Sec. MESH: dx, dy scaled so sqrt((dz/dx)^2+(dz/dy)^2) = 0.99 when NSFD is
+   unstable, dt = dz/c for NSFD), fix the rest frame gamma0 (Sec. "Lorentz Transformation"),
+   allocate the fields and particles on the device, boost the particles
+   (Eqs. LorentzTrasnformParticles, LorentzTransformDeltaR) and sort them by cell.
+   dt_lab > 0 is accepted for FD only (lab field time step); <= 0 picks it automatically.
+   Errors: EINVAL (sizes, non-finite values, kinds), ENOMEM, ECUDA. */
+int mithra_create(const mithra_grid *grid, double dt_lab, const mithra_undulator *und,
+                  const mithra_bunch *bunch, mithra_t *out);
+
+/* Use `stream` (a cudaStream_t) for all later work of the run. */
+int mithra_set_stream(mithra_t run, void *stream);
+
+/* Enqueue nsteps field steps (>= 0).  One step: E and B at nodes (Sec. "Field Evaluation"),
+   external field + gather + Boris + zigzag/CIC deposition (Sec. "Update Algorithm",
+   "Current Deposition"), potential update (Eq. updateEquation) and Mur boundaries, the
+   radiated-power sample; a counting sort by cell every sort_every steps. */
+int mithra_step(mithra_t run, int64_t nsteps);
+
+/* Wait for the run's stream; returns EDIVERGED if the last field energy is not finite. */
+int mithra_sync(mithra_t run);
+
+/* Field indices for mithra_fields / mithra_set_field. */
+#define MITHRA_AX 0
+#define MITHRA_AY 1
+#define MITHRA_AZ 2
+#define MITHRA_PHI 3
+#define MITHRA_JX 4
+#define MITHRA_JY 5
+#define MITHRA_JZ 6
+#define MITHRA_RHO 7
+#define MITHRA_EX 8
+#define MITHRA_EY 9
+#define MITHRA_EZ 10
+#define MITHRA_BX 11
+#define MITHRA_BY 12
+#define MITHRA_BZ 13
+
+/* Copy one field (nx*ny*nz values, x fastest) to host FP64 memory.  For potentials `level`
+   0 is step n and 1 is step n+1 of the next step's input (A at k dt, phi at (k+1/2) dt);
+   A_x[i] sits at (i+1/2) dx, A_y at (j+1/2) dy, A_z at (k+1/2) dz; J likewise; phi, rho,
+   E and B at nodes.  Synchronises the stream.  ERANGE if cap < nx*ny*nz. */
+int mithra_fields(mithra_t run, int which, int level, double *host_out, size_t cap);
+
+/* Overwrite one potential level (which 0..3, level 0..1) from host FP64 data. */
+int mithra_set_field(mithra_t run, int which, int level, const double *host_in, size_t n);
+
+/* Copy the particles (rest frame, n x 6: x, y, z, gamma*beta_x,y,z) in their input order. */
+int mithra_particles(mithra_t run, double *host_out6, size_t cap_rows);
+
+/* Replace the particles with rest-frame values (n x 6, input order). */
+int mithra_set_particles(mithra_t run, const double *rest6, size_t rows);
+
+/* Radiated power series, one value per step taken: lab-frame power (W) through the plane
+   power_plane_dist ahead of the bunch at normalised frequency h, and its lab time (s).
+   Power = cycle-averaged Poynting flux of the DFT over the last M = round(2 pi/(h w* dt))
+   steps, times gamma0^2 (1+beta0)^2 (Sec. FEL-OUTPUT "radiation-power").
+   n_out receives the series length; ERANGE if cap is smaller. */
+int mithra_radiated_power(mithra_t run, double *p_lab, double *t_lab, size_t cap, size_t *n_out);
+
+/* On-axis E_x at the power plane, one value per step (rest frame, V/m). */
+int mithra_onaxis_field(mithra_t run, double *ex, size_t cap, size_t *n_out);
+
+/* Field energy (J, rest frame, from the last emitted E and B at nodes) and the bunching factor
+   |<exp(j kb z)>| at the rest-frame ponderomotive wavenumber kb; bunching3 = {|b|, Re b, Im b}.
+   Either pointer may be NULL. */
+int mithra_diag(mithra_t run, double *field_energy, double *bunching3);
+
+/* Derived constants (19 doubles): gamma0, beta0, dx, dy, dz, dt, dt_b, A_nsfd, x0, y0, z0, T0,
+   omega_h, M, plane index, z_ref, macro charge, k*, kb.  hbm_bytes: device bytes held. */
+int mithra_info(mithra_t run, double *info19, int64_t *hbm_bytes);
+
+/* Per-kernel timing with CUDA events on the run's stream (off by default).  When on, every
+   launch of every kernel of the step is bracketed by events; mithra_kernel_stats returns the
+   summed device time (ms) and launch count per kernel id since the last reset. */
+#define MITHRA_K_EMIT 0
+#define MITHRA_K_PUSH 1
+#define MITHRA_K_STENCIL 2
+#define MITHRA_K_MUR 3
+#define MITHRA_K_POWER 4
+#define MITHRA_K_SORT 5
+#define MITHRA_K_CLEAR 6
+#define MITHRA_K_COUNT 7
+int mithra_set_profiling(mithra_t run, int on);
+int mithra_kernel_stats(mithra_t run, int kernel_id, double *total_ms, int64_t *launches);
+const char *mithra_kernel_name(int kernel_id);
+
+/* Release everything the run holds (waits for its stream).  NULL is ignored. */
+void mithra_destroy(mithra_t run);
+
+const char *mithra_last_error(void);
+int mithra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

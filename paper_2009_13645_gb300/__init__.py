@@ -1,0 +1,265 @@
+"""Python binding of libmithra (include/mithra.h): argument marshalling only.
+
+Every step of the FDTD/PIC time step runs in the CUDA kernels of libmithra.so.  There is no
+CPU fallback: importing this package loads the library and raises if it is missing or
+cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["lib", "Grid", "Undulator", "Bunch", "Run", "MithraError", "load", "FIELD", "KERNELS",
+           "grid_from", "undulator_from", "bunch_from", "use_torch_allocator"]
+
+OK, EINVAL, ENOMEM, ERANGE, ETIMEDOUT, EDIVERGED, ENOTFOUND, EAGAIN, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8
+FIELD = {"Ax": 0, "Ay": 1, "Az": 2, "phi": 3, "Jx": 4, "Jy": 5, "Jz": 6, "rho": 7,
+         "Ex": 8, "Ey": 9, "Ez": 10, "Bx": 11, "By": 12, "Bz": 13}
+KERNELS = ("emit_eb", "push_deposit", "stencil", "mur", "power", "sort", "clear_sources")
+INFO_KEYS = ("gamma0", "beta0", "dx", "dy", "dz", "dt", "dtb", "A", "x0", "y0", "z0", "T0",
+             "omega_h", "M", "kp", "z_ref", "q", "kstar", "kb")
+
+
+class MithraError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libmithra error {code}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("cz", C.c_double),
+                ("solver", C.c_int32), ("courant", C.c_double), ("mur_order", C.c_int32),
+                ("space_charge", C.c_int32), ("precision", C.c_int32), ("substeps", C.c_int32),
+                ("power_plane_dist", C.c_double), ("norm_freq", C.c_double), ("sort_every", C.c_int32)]
+
+
+class Undulator(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("K", C.c_double), ("lambda_", C.c_double),
+                ("n_periods", C.c_double), ("pol_deg", C.c_double), ("waist", C.c_double),
+                ("pulse_fwhm", C.c_double), ("signal", C.c_int32), ("dist_to_bunch_head", C.c_double)]
+
+
+class Bunch(C.Structure):
+    _fields_ = [("n", C.c_int64), ("charge_e", C.c_double), ("gamma", C.c_double),
+                ("sig_z", C.c_double), ("lab_particles", C.POINTER(C.c_double))]
+
+
+_lib = None
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+def load(rebuild: bool = False):
+    """Load (building first when needed) paper_2009_13645_gb300/_build/libmithra.so."""
+    global _lib
+    if _lib is not None and not rebuild:
+        return _lib
+    path = _build.LIB
+    if rebuild or not _build.up_to_date():
+        path = _build.build(force=rebuild)
+    if not os.path.exists(path):
+        raise ImportError(f"libmithra.so not found at {path}")
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    vp = C.c_void_p
+    L.mithra_set_allocator.argtypes = [_ALLOC, _FREE, vp]
+    L.mithra_create.argtypes = [C.POINTER(Grid), C.c_double, C.POINTER(Undulator), C.POINTER(Bunch), C.POINTER(vp)]
+    L.mithra_set_stream.argtypes = [vp, vp]
+    L.mithra_step.argtypes = [vp, C.c_int64]
+    L.mithra_sync.argtypes = [vp]
+    L.mithra_fields.argtypes = [vp, C.c_int, C.c_int, dp, C.c_size_t]
+    L.mithra_set_field.argtypes = [vp, C.c_int, C.c_int, dp, C.c_size_t]
+    L.mithra_particles.argtypes = [vp, dp, C.c_size_t]
+    L.mithra_set_particles.argtypes = [vp, dp, C.c_size_t]
+    L.mithra_radiated_power.argtypes = [vp, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.mithra_onaxis_field.argtypes = [vp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.mithra_diag.argtypes = [vp, dp, dp]
+    L.mithra_info.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+    L.mithra_set_profiling.argtypes = [vp, C.c_int]
+    L.mithra_kernel_stats.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int64)]
+    L.mithra_kernel_name.restype = C.c_char_p
+    L.mithra_kernel_name.argtypes = [C.c_int]
+    L.mithra_destroy.argtypes = [vp]
+    L.mithra_destroy.restype = None
+    L.mithra_last_error.restype = C.c_char_p
+    L.mithra_version.restype = C.c_int
+    _lib = L
+    return L
+
+
+def lib():
+    return load()
+
+
+def _check(rc):
+    if rc != OK:
+        msg = _lib.mithra_last_error().decode(errors="replace")
+        raise MithraError(rc, msg)
+    return rc
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+_torch_hooks = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route libmithra's device allocations through PyTorch's caching allocator."""
+    global _torch_hooks
+    L = load()
+    if not enable:
+        _check(L.mithra_set_allocator(_ALLOC(), _FREE(), None))
+        _torch_hooks = None
+        return
+    import torch
+
+    def _alloc(ctx, nbytes):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device()))
+        except Exception:
+            return None
+
+    def _free(ctx, ptr):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _torch_hooks = (_ALLOC(_alloc), _FREE(_free))
+    _check(L.mithra_set_allocator(_torch_hooks[0], _torch_hooks[1], None))
+
+
+def grid_from(w, precision=None, sort_every=0) -> Grid:
+    g = Grid()
+    g.nx, g.ny, g.nz = w.nx, w.ny, w.nz
+    g.dx, g.dy, g.dz = w.dx, w.dy, w.dz
+    g.cx = g.cy = g.cz = 0.0
+    g.solver, g.courant, g.mur_order = w.solver, w.courant, w.mur_order
+    g.space_charge = w.space_charge
+    g.precision = w.precision if precision is None else int(precision)
+    g.substeps = w.substeps
+    g.power_plane_dist, g.norm_freq = w.plane_dist, w.norm_freq
+    g.sort_every = int(sort_every)
+    return g
+
+
+def undulator_from(w) -> Undulator:
+    u = Undulator()
+    u.kind, u.K, u.lambda_, u.n_periods = w.und_kind, w.K, w.lambda_u, w.n_periods
+    u.pol_deg, u.waist, u.pulse_fwhm, u.signal = w.pol_deg, w.waist, w.pulse_fwhm, w.signal
+    u.dist_to_bunch_head = w.dist_head
+    return u
+
+
+def bunch_from(w, lab6: np.ndarray):
+    lab6 = np.ascontiguousarray(lab6, dtype=np.float64)
+    b = Bunch()
+    b.n = lab6.shape[0]
+    b.charge_e, b.gamma, b.sig_z = w.charge_e, w.gamma, w.sig_z
+    b.lab_particles = _dp(lab6) if lab6.size else C.POINTER(C.c_double)()
+    return b, lab6
+
+
+class Run:
+    """One run on the current CUDA device (owns the libmithra handle)."""
+
+    def __init__(self, grid: Grid, und: Undulator, bunch: Bunch, dt_lab: float = 0.0, stream=None):
+        self.L = load()
+        h = C.c_void_p()
+        _check(self.L.mithra_create(C.byref(grid), float(dt_lab), C.byref(und), C.byref(bunch), C.byref(h)))
+        self.h = h
+        self.grid = grid
+        self.np = int(bunch.n)
+        self.shape = (grid.nz, grid.ny, grid.nx)
+        if stream is not None:
+            _check(self.L.mithra_set_stream(self.h, C.c_void_p(int(stream))))
+
+    @classmethod
+    def from_workload(cls, w, lab6=None, precision=None, sort_every=0, stream=None):
+        import workloads
+        lab6 = workloads.lab_bunch(w) if lab6 is None else lab6
+        b, keep = bunch_from(w, lab6)
+        r = cls(grid_from(w, precision, sort_every), undulator_from(w), b, stream=stream)
+        r._keep = keep
+        return r
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mithra_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _check(self.L.mithra_step(self.h, int(n)))
+
+    def sync(self):
+        _check(self.L.mithra_sync(self.h))
+
+    def info(self) -> dict:
+        out = np.zeros(19)
+        hb = C.c_int64()
+        _check(self.L.mithra_info(self.h, _dp(out), C.byref(hb)))
+        d = dict(zip(INFO_KEYS, out.tolist()))
+        d["hbm_bytes"] = hb.value
+        return d
+
+    def field(self, name, lev: int = 1) -> np.ndarray:
+        out = np.zeros(self.shape)
+        w = FIELD[name] if isinstance(name, str) else int(name)
+        _check(self.L.mithra_fields(self.h, w, lev, _dp(out), out.size))
+        return out
+
+    def set_field(self, name, lev: int, arr):
+        a = np.ascontiguousarray(np.broadcast_to(arr, self.shape), dtype=np.float64)
+        w = FIELD[name] if isinstance(name, str) else int(name)
+        _check(self.L.mithra_set_field(self.h, w, lev, _dp(a), a.size))
+
+    def particles(self) -> np.ndarray:
+        out = np.zeros((self.np, 6))
+        _check(self.L.mithra_particles(self.h, _dp(out), self.np))
+        return out
+
+    def set_particles(self, rest6):
+        a = np.ascontiguousarray(rest6, dtype=np.float64)
+        _check(self.L.mithra_set_particles(self.h, _dp(a), a.shape[0]))
+
+    def series(self):
+        n = C.c_size_t()
+        _check(self.L.mithra_radiated_power(self.h, None, None, 0, C.byref(n)))
+        p, t, e = np.zeros(n.value), np.zeros(n.value), np.zeros(n.value)
+        if n.value:
+            _check(self.L.mithra_radiated_power(self.h, _dp(p), _dp(t), n.value, C.byref(n)))
+            _check(self.L.mithra_onaxis_field(self.h, _dp(e), n.value, C.byref(n)))
+        return p, t, e
+
+    def diag(self):
+        fe = C.c_double()
+        b = np.zeros(3)
+        _check(self.L.mithra_diag(self.h, C.byref(fe), _dp(b)))
+        return fe.value, float(b[0])
+
+    def bunching_complex(self) -> complex:
+        b = np.zeros(3)
+        _check(self.L.mithra_diag(self.h, None, _dp(b)))
+        return complex(b[1], b[2])
+
+    def set_profiling(self, on: bool):
+        _check(self.L.mithra_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_stats(self) -> dict:
+        out = {}
+        for k, name in enumerate(KERNELS):
+            ms, n = C.c_double(), C.c_int64()
+            _check(self.L.mithra_kernel_stats(self.h, k, C.byref(ms), C.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out

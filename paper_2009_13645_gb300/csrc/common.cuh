@@ -1,0 +1,180 @@
+// Internal definitions shared by the CUDA translation units of libmithra.
+// Physics: MITHRA 2.0 manual (arXiv:2009.13645), Ch. "Methodology".
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+namespace mithra {
+
+// CODATA 2018
+constexpr double kC = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kPi = 3.14159265358979323846;
+
+// Rest-frame grid geometry.  Fields are stored x-fastest with row pitch nx and plane
+// pitch nx*ny.  A_x/J_x index i sits at (i+1/2)dx, A_y at (j+1/2)dy, A_z at (k+1/2)dz;
+// phi, rho, E and B sit on nodes.
+struct Geom {
+    int nx, ny, nz;
+    int64_t sy, sz, ncell;
+    double dx, dy, dz, dt, dtb;
+    double x0, y0, z0;
+    int substeps;
+    int space_charge;
+};
+
+// External field of the run (lab frame) and the boost (manual Sec. "Field Initialization",
+// Eqs. undulatorField, fringingField, opticalUndulatorPW, opticalUndulatorGB,
+// LorentzTransformR2L, LorentzTransformElectric/Magnetic).
+struct ExtField {
+    int kind;           // -1 none, 0 planar, 1 helical, 2 optical plane wave, 3 optical Gaussian
+    double g0, b0;      // rest-frame gamma0, beta0
+    double ku, Lu, B0;  // static undulator: wavenumber, length, peak field
+    double qlam;        // helical: quarter period offset of the second planar field
+    double cpol, spol;  // polarisation direction (cos, sin)
+    double kL, wL, E0;  // laser wavenumber, angular frequency, peak field
+    double zeta_f, t_f; // laser focus and the time its pulse centre crosses it (lab)
+    double tp;          // pulse length tau (s); <= 0: continuous
+    int signal;         // 0 Gaussian envelope, 1 flat-top
+    double w0, zr;      // Gaussian beam waist and Rayleigh length; w0 <= 0: plane wave
+};
+
+// Planar static undulator field along (-sin, cos) in the xy-plane starting at lab
+// coordinate `off`; before the entrance the manual's Neumann-type fringe, after the end
+// the same fringe mirrored.  Adds to Bp.
+__host__ __device__ inline void planar_add(const ExtField& f, double c, double s, double off,
+                                           double xl, double yl, double zeta, double Bp[3])
+{
+    const double yu = c * yl - s * xl;          // coordinate along the field direction
+    const double u = zeta - off;
+    double sn, cs;
+    if (u >= 0.0 && u <= f.Lu) {
+        sincos(f.ku * u, &sn, &cs);
+    } else {
+        const double d = (u < 0.0) ? u : (u - f.Lu);
+        const double kd = f.ku * d;
+        const double g = exp(-0.5 * kd * kd);
+        sn = kd * g;
+        cs = g;
+    }
+    const double ky = f.ku * yu;
+    const double ch = cosh(ky), sh = sinh(ky);
+    const double Bt = f.B0 * ch * sn;   // transverse component along the field direction
+    Bp[0] -= Bt * s;
+    Bp[1] += Bt * c;
+    Bp[2] += f.B0 * sh * cs;
+}
+
+// Time signature f(tau, phase) of the laser (Eq. signalTypes, A0 = 1).
+__host__ __device__ inline double laser_signal(const ExtField& f, double tau, double phase)
+{
+    const double car = cos(f.wL * tau + phase);
+    if (f.tp <= 0.0 || (f.signal == 1 && tau > 0.0)) return car;
+    return car * exp(-2.0 * 0.69314718055994530942 * (tau * tau) / (f.tp * f.tp));
+}
+
+// Lab-frame field at lab event (xl, yl, zeta, tl).
+__host__ __device__ inline void lab_field(const ExtField& f, double xl, double yl, double zeta, double tl,
+                                          double Ep[3], double Bp[3])
+{
+    Ep[0] = Ep[1] = Ep[2] = 0.0;
+    Bp[0] = Bp[1] = Bp[2] = 0.0;
+    if (f.kind == 0) {
+        planar_add(f, f.cpol, f.spol, 0.0, xl, yl, zeta, Bp);
+    } else if (f.kind == 1) {
+        planar_add(f, f.cpol, f.spol, 0.0, xl, yl, zeta, Bp);
+        // rotated by +90 degrees: (cos, sin) -> (-sin, cos)
+        planar_add(f, -f.spol, f.cpol, f.qlam, xl, yl, zeta, Bp);
+    } else if (f.kind == 2 || f.kind == 3) {
+        const double tau = (tl - f.t_f) + (zeta - f.zeta_f) / kC;   // counter-propagating (-z)
+        double Epar, El = 0.0, Bl = 0.0;
+        if (f.kind == 2 || f.w0 <= 0.0) {
+            Epar = f.E0 * laser_signal(f, tau, 0.0);
+        } else {
+            const double l = f.zeta_f - zeta;                       // distance travelled past the focus
+            const double lz = l / f.zr;
+            const double wl = f.w0 * sqrt(1.0 + lz * lz);
+            const double rpar = xl * f.cpol + yl * f.spol;
+            const double rper = yl * f.cpol - xl * f.spol;
+            const double r2 = rpar * rpar + rper * rper;
+            // k r^2 / (2 R(l)) with R(l) = l (1 + (z_R/l)^2) written without dividing by l
+            const double curv = f.kL * r2 * l / (2.0 * (l * l + f.zr * f.zr));
+            const double gouy = atan(lz);
+            const double amp = (f.w0 / wl) * exp(-r2 / (wl * wl));
+            Epar = f.E0 * amp * laser_signal(f, tau, gouy - curv);
+            const double sl = laser_signal(f, tau, 2.0 * gouy - curv + 0.5 * kPi);
+            El = f.E0 * rpar * f.w0 / (f.zr * wl) * amp * sl;
+            Bl = f.E0 * rper * f.w0 / (kC * f.zr * wl) * amp * sl;
+        }
+        Ep[0] = Epar * f.cpol;
+        Ep[1] = Epar * f.spol;
+        Ep[2] = -El;
+        Bp[0] = Epar * f.spol / kC;
+        Bp[1] = -Epar * f.cpol / kC;
+        Bp[2] = -Bl;
+    }
+}
+
+// External field at a rest-frame event (x, y, z, t): lab event, lab field, then the field
+// transform to the frame moving with beta0 along z.
+__host__ __device__ inline void external_field(const ExtField& f, double x, double y, double z, double t,
+                                               double E[3], double B[3])
+{
+    if (f.kind < 0) {
+        E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = 0.0;
+        return;
+    }
+    const double zeta = f.g0 * fma(f.b0 * kC, t, z);
+    const double tl = f.g0 * fma(f.b0 / kC, z, t);
+    double Ep[3], Bp[3];
+    lab_field(f, x, y, zeta, tl, Ep, Bp);
+    const double g = f.g0, bc = f.b0 * kC, bic = f.b0 / kC;
+    E[0] = g * (Ep[0] - bc * Bp[1]);
+    E[1] = g * (Ep[1] + bc * Bp[0]);
+    E[2] = Ep[2];
+    B[0] = g * (Bp[0] + bic * Ep[1]);
+    B[1] = g * (Bp[1] - bic * Ep[0]);
+    B[2] = Bp[2];
+}
+
+// Boris rotation of the normalised momentum u of an electron (Eq. BorisScheme), FP64.
+__host__ __device__ inline void boris(double u[3], const double E[3], const double B[3], double dtb)
+{
+    const double h = kQe * dtb / (2.0 * kMe * kC);
+    const double t1x = u[0] - h * E[0], t1y = u[1] - h * E[1], t1z = u[2] - h * E[2];
+    const double a = -kQe * dtb / (2.0 * kMe * sqrt(1.0 + t1x * t1x + t1y * t1y + t1z * t1z));
+    const double t2x = t1x + a * (t1y * B[2] - t1z * B[1]);
+    const double t2y = t1y + a * (t1z * B[0] - t1x * B[2]);
+    const double t2z = t1z + a * (t1x * B[1] - t1y * B[0]);
+    const double s = 2.0 * a / (1.0 + a * a * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+    u[0] = t1x + s * (t2y * B[2] - t2z * B[1]) - h * E[0];
+    u[1] = t1y + s * (t2z * B[0] - t2x * B[2]) - h * E[1];
+    u[2] = t1z + s * (t2x * B[1] - t2y * B[0]) - h * E[2];
+}
+
+// Particle arrays (structure of arrays).  Position = node 0 + (cell + offset) * spacing,
+// offset in [0, 1).  `real` is float for the FP32-mixed path, double for FP64.
+template <typename real>
+struct Particles {
+    int32_t *ix, *iy, *iz;
+    real *fx, *fy, *fz;
+    double *ux, *uy, *uz;
+    int32_t *id;
+};
+
+template <typename real>
+struct Fields4 {
+    real* c[4];
+};
+
+template <typename real>
+struct Fields6 {
+    real* c[6];
+};
+
+}  // namespace mithra

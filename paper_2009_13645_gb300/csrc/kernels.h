@@ -1,0 +1,84 @@
+// Launcher declarations shared by the translation units of libmithra.
+#pragma once
+
+#include "common.cuh"
+
+namespace mithra {
+
+// Pointers of one step's potential levels: n0 = psi^{n-1}, n1 = psi^n, out = psi^{n+1}, plus the
+// sources J_x, J_y, J_z, rho.
+template <typename real>
+struct FieldLevels {
+    const real* n0[4];
+    const real* n1[4];
+    real* out[4];
+    const real* src[4];
+};
+
+// Stencil coefficients (FP64 on the host, rounded to the storage type at launch).
+struct StencilCoef {
+    double a1, ax, ay, a6, w, w0, s_a, s_phi;
+};
+
+template <typename real>
+cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const StencilCoef& cf, int ncomp,
+                           cudaStream_t st);
+template <typename real>
+cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, cudaStream_t st);
+template <typename real>
+cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, cudaStream_t st);
+
+// Particles.
+struct PushConst {
+    double t_half;        // rest-frame time of r^{n+1/2}
+    double qJ[3];         // q / (D_m D_n dt): current density per unit displacement (cells) along each axis
+    double qrho;          // q / (dx dy dz)
+    double cdtb[3];       // c dt_b / D_l
+};
+
+template <typename real>
+cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,
+                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc,
+                        cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_boost(const double* lab6, int64_t np, const Particles<real>& P, const Geom& g,
+                         const ExtField& ef, double z_ref, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_set_rest(const double* rest6, int64_t np, const Particles<real>& P, const Geom& g,
+                            cudaStream_t st);
+template <typename real>
+cudaError_t launch_get_rest(const Particles<real>& P, int64_t np, const Geom& g, double* rest6,
+                            cudaStream_t st);
+
+// Counting sort by cell.
+struct SortScratch {
+    int32_t* key;        // per particle
+    int32_t* count;      // nbins + 1
+    int32_t* offset;     // nbins + 1 (exclusive scan)
+    int32_t* perm;       // per particle: destination slot
+    int32_t* blocksum;   // scan partials
+    int64_t nbins;
+};
+template <typename real>
+cudaError_t launch_sort(Particles<real>& P, Particles<real>& tmp, int64_t np, const Geom& g,
+                        const SortScratch& s, cudaStream_t st);
+size_t sort_scan_partials(int64_t nbins);
+
+// Diagnostics.
+template <typename real>
+cudaError_t power_sample_ex(const Fields6<real>& eb, const Geom& g, int kp, double* ring, int slot, double omega_h,
+                            double t_sample, double* phase_cs, cudaStream_t st);
+cudaError_t launch_power_reduce(const double* ring, const double* ring_phase_cs, int M, const Geom& g,
+                                double scale, double* partial, int npartial, double* out, cudaStream_t st);
+template <typename real>
+cudaError_t launch_onaxis(const Fields6<real>& eb, int64_t id, double* out, cudaStream_t st);
+template <typename real>
+cudaError_t launch_energy(const Fields6<real>& eb, const Geom& g, double* partial, int npartial, double* out,
+                          cudaStream_t st);
+template <typename real>
+cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g, double kb, double* partial,
+                            int npartial, double* out3, cudaStream_t st);
+
+}  // namespace mithra

@@ -1,0 +1,822 @@
+// C ABI of libmithra: run set-up (rest frame, mesh checks, placement), device memory,
+// the per-step launch sequence and the accessors declared in include/mithra.h.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mithra.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace mithra;
+
+// ---------------------------------------------------------------------------------------
+// errors and the allocator hook
+// ---------------------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CU(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return fail(MITHRA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Allocator {
+    mithra_alloc_fn alloc = nullptr;
+    mithra_free_fn free_fn = nullptr;
+    void* ctx = nullptr;
+};
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
+
+extern "C" int mithra_set_allocator(mithra_alloc_fn alloc, mithra_free_fn free_fn, void* ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(MITHRA_EINVAL, "allocator: give both functions or none");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.free_fn = free_fn;
+    g_alloc.ctx = ctx;
+    return MITHRA_OK;
+}
+
+extern "C" const char* mithra_last_error(void) { return g_err.c_str(); }
+extern "C" int mithra_version(void) { return 1; }
+
+static const char* kKernelNames[MITHRA_K_COUNT] = {"emit_eb", "push_deposit", "stencil", "mur", "power", "sort",
+                                                   "clear_sources"};
+extern "C" const char* mithra_kernel_name(int id)
+{
+    return (id >= 0 && id < MITHRA_K_COUNT) ? kKernelNames[id] : "unknown";
+}
+
+// ---------------------------------------------------------------------------------------
+// the run
+// ---------------------------------------------------------------------------------------
+struct DevMem {
+    Allocator a;
+    std::vector<std::pair<void*, size_t>> blocks;
+    size_t total = 0;
+    void* get(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~(size_t)255;
+        void* p = nullptr;
+        if (a.alloc) {
+            p = a.alloc(a.ctx, bytes);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) {
+            blocks.emplace_back(p, bytes);
+            total += bytes;
+        }
+        return p;
+    }
+    void release(void* p)
+    {
+        for (size_t i = 0; i < blocks.size(); ++i)
+            if (blocks[i].first == p) {
+                total -= blocks[i].second;
+                if (a.free_fn) a.free_fn(a.ctx, p);
+                else cudaFree(p);
+                blocks.erase(blocks.begin() + (long)i);
+                return;
+            }
+    }
+    void release_all()
+    {
+        for (auto& b : blocks) {
+            if (a.free_fn) a.free_fn(a.ctx, b.first);
+            else cudaFree(b.first);
+        }
+        blocks.clear();
+        total = 0;
+    }
+};
+
+struct Derived {
+    double g0, b0, dx, dy, dz, dt, dtb, A, x0, y0, z0, T0, omega_h, M, kp, z_ref, q, kstar, kb;
+};
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+struct mithra_run {
+    virtual ~mithra_run() {}
+    virtual int step(int64_t n) = 0;
+    virtual int fields(int which, int level, double* out, size_t cap) = 0;
+    virtual int set_field(int which, int level, const double* in, size_t n) = 0;
+    virtual int particles(double* out, size_t cap) = 0;
+    virtual int set_particles(const double* in, size_t n) = 0;
+    virtual int diag(double* fe, double* b3) = 0;
+    virtual int series(int which, double* out, size_t cap, size_t* n_out) = 0;
+    virtual int sync() = 0;
+    virtual void destroy_all() = 0;
+
+    // common state
+    Derived d;
+    Geom g;
+    ExtField ef;
+    StencilCoef cf;
+    int precision = 1;
+    int mur_order = 2;
+    int sort_every = 20;
+    int64_t np = 0;
+    int64_t nstep = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevMem mem;
+    // profiling
+    bool prof = false;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> ev_free;
+    double prof_ms[MITHRA_K_COUNT] = {0};
+    int64_t prof_n[MITHRA_K_COUNT] = {0};
+
+    cudaEvent_t ev_get()
+    {
+        if (!ev_free.empty()) {
+            cudaEvent_t e = ev_free.back();
+            ev_free.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void prof_collect()
+    {
+        for (auto& r : prof_pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                prof_ms[r.kid] += ms;
+                prof_n[r.kid] += 1;
+            } else {
+                cudaGetLastError();
+            }
+            ev_free.push_back(r.a);
+            ev_free.push_back(r.b);
+        }
+        prof_pending.clear();
+    }
+};
+
+namespace {
+
+template <typename real>
+struct RunT final : mithra_run {
+    real* pot[3][4] = {};      // ring of three time levels of A_x, A_y, A_z, phi
+    int base = 0;              // pot[(base + 0) % 3] = level n, (base + 1) % 3 = level n+1
+    real* src[4] = {};
+    real* eb[6] = {};
+    Particles<real> P{}, T{};
+    SortScratch ss{};
+    double* ring = nullptr;
+    double* phase_cs = nullptr;
+    double* partial = nullptr;
+    int npartial = 304;
+    double* ser_p = nullptr;
+    double* ser_e = nullptr;
+    int64_t ser_cap = 0;
+    double* small = nullptr;   // 8 doubles of diagnostic output
+    double* rest_buf = nullptr;
+    int64_t onaxis_id = 0;
+
+    int lev(int k) const { return (base + k) % 3; }
+
+    int alloc_all()
+    {
+        const size_t cell = (size_t)g.ncell * sizeof(real);
+        for (int l = 0; l < 3; ++l)
+            for (int c = 0; c < 4; ++c)
+                if (!(pot[l][c] = (real*)mem.get(cell))) return fail(MITHRA_ENOMEM, "device allocation failed (fields)");
+        for (int c = 0; c < 4; ++c)
+            if (!(src[c] = (real*)mem.get(cell))) return fail(MITHRA_ENOMEM, "device allocation failed (sources)");
+        for (int c = 0; c < 6; ++c)
+            if (!(eb[c] = (real*)mem.get(cell))) return fail(MITHRA_ENOMEM, "device allocation failed (E/B)");
+        for (int l = 0; l < 3; ++l)
+            for (int c = 0; c < 4; ++c) CU(cudaMemsetAsync(pot[l][c], 0, cell, stream));
+        for (int c = 0; c < 4; ++c) CU(cudaMemsetAsync(src[c], 0, cell, stream));
+        for (int c = 0; c < 6; ++c) CU(cudaMemsetAsync(eb[c], 0, cell, stream));
+        const int64_t n = np > 0 ? np : 1;
+        for (Particles<real>* Q : {&P, &T}) {
+            Q->ix = (int32_t*)mem.get(n * 4);
+            Q->iy = (int32_t*)mem.get(n * 4);
+            Q->iz = (int32_t*)mem.get(n * 4);
+            Q->fx = (real*)mem.get(n * sizeof(real));
+            Q->fy = (real*)mem.get(n * sizeof(real));
+            Q->fz = (real*)mem.get(n * sizeof(real));
+            Q->ux = (double*)mem.get(n * 8);
+            Q->uy = (double*)mem.get(n * 8);
+            Q->uz = (double*)mem.get(n * 8);
+            Q->id = (int32_t*)mem.get(n * 4);
+            if (!Q->ix || !Q->iy || !Q->iz || !Q->fx || !Q->fy || !Q->fz || !Q->ux || !Q->uy || !Q->uz || !Q->id)
+                return fail(MITHRA_ENOMEM, "device allocation failed (particles)");
+        }
+        ss.nbins = g.ncell + 1;
+        ss.key = (int32_t*)mem.get(n * 4);
+        ss.perm = (int32_t*)mem.get(n * 4);
+        ss.count = (int32_t*)mem.get((size_t)ss.nbins * 4);
+        ss.offset = (int32_t*)mem.get((size_t)ss.nbins * 4);
+        ss.blocksum = (int32_t*)mem.get(sort_scan_partials(ss.nbins) * 4);
+        if (!ss.key || !ss.perm || !ss.count || !ss.offset || !ss.blocksum)
+            return fail(MITHRA_ENOMEM, "device allocation failed (sort scratch)");
+        const int M = (int)d.M;
+        const size_t plane = (size_t)g.nx * g.ny;
+        ring = (double*)mem.get((size_t)M * 4 * plane * 8);
+        phase_cs = (double*)mem.get((size_t)2 * M * 8);
+        partial = (double*)mem.get((size_t)4 * npartial * 8);   // energy: [0, n); bunching: [n, 3n)
+        small = (double*)mem.get(8 * 8);
+        if (!ring || !phase_cs || !partial || !small) return fail(MITHRA_ENOMEM, "device allocation failed (diagnostics)");
+        CU(cudaMemsetAsync(ring, 0, (size_t)M * 4 * plane * 8, stream));
+        return grow_series(1024);
+    }
+
+    int grow_series(int64_t need)
+    {
+        if (need <= ser_cap) return MITHRA_OK;
+        int64_t cap = ser_cap ? ser_cap : 1024;
+        while (cap < need) cap *= 2;
+        double* np_ = (double*)mem.get((size_t)cap * 8);
+        double* ne_ = (double*)mem.get((size_t)cap * 8);
+        if (!np_ || !ne_) return fail(MITHRA_ENOMEM, "device allocation failed (series)");
+        CU(cudaMemsetAsync(np_, 0, (size_t)cap * 8, stream));
+        CU(cudaMemsetAsync(ne_, 0, (size_t)cap * 8, stream));
+        if (ser_cap) {
+            CU(cudaMemcpyAsync(np_, ser_p, (size_t)ser_cap * 8, cudaMemcpyDeviceToDevice, stream));
+            CU(cudaMemcpyAsync(ne_, ser_e, (size_t)ser_cap * 8, cudaMemcpyDeviceToDevice, stream));
+            CU(cudaStreamSynchronize(stream));
+            mem.release(ser_p);
+            mem.release(ser_e);
+        }
+        ser_p = np_;
+        ser_e = ne_;
+        ser_cap = cap;
+        return MITHRA_OK;
+    }
+
+    void pbeg(int kid, cudaEvent_t* a)
+    {
+        if (!prof) return;
+        *a = ev_get();
+        cudaEventRecord(*a, stream);
+        (void)kid;
+    }
+    void pend(int kid, cudaEvent_t a)
+    {
+        if (!prof) return;
+        cudaEvent_t b = ev_get();
+        cudaEventRecord(b, stream);
+        prof_pending.push_back({kid, a, b});
+    }
+
+    FieldLevels<real> levels() const
+    {
+        FieldLevels<real> L;
+        for (int c = 0; c < 4; ++c) {
+            L.n0[c] = pot[lev(0)][c];
+            L.n1[c] = pot[lev(1)][c];
+            L.out[c] = pot[lev(2)][c];
+            L.src[c] = src[c];
+        }
+        return L;
+    }
+
+    int sort_now()
+    {
+        cudaEvent_t e0 = nullptr;
+        pbeg(MITHRA_K_SORT, &e0);
+        CU(launch_sort<real>(P, T, np, g, ss, stream));
+        pend(MITHRA_K_SORT, e0);
+        return MITHRA_OK;
+    }
+
+    int step(int64_t nsteps) override
+    {
+        int rc = grow_series(nstep + nsteps);
+        if (rc) return rc;
+        const size_t cell = (size_t)g.ncell * sizeof(real);
+        const int ncomp = g.space_charge ? 4 : 3;
+        Fields6<real> E6;
+        for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
+        Fields4<real> S4;
+        for (int c = 0; c < 4; ++c) S4.c[c] = src[c];
+        for (int64_t s = 0; s < nsteps; ++s) {
+            const int64_t n = nstep;
+            if (sort_every > 0 && n > 0 && n % sort_every == 0 && np > 1) {
+                if ((rc = sort_now())) return rc;
+            }
+            FieldLevels<real> L = levels();
+            cudaEvent_t e0 = nullptr;
+            pbeg(MITHRA_K_EMIT, &e0);
+            CU(launch_emit<real>(L, E6, g, stream));
+            pend(MITHRA_K_EMIT, e0);
+            pbeg(MITHRA_K_CLEAR, &e0);
+            for (int c = 0; c < ncomp; ++c) CU(cudaMemsetAsync(src[c], 0, cell, stream));
+            pend(MITHRA_K_CLEAR, e0);
+            PushConst pc;
+            pc.t_half = d.T0 + ((double)n + 0.5) * d.dt;
+            pc.qJ[0] = d.q / (d.dy * d.dz * d.dt);
+            pc.qJ[1] = d.q / (d.dz * d.dx * d.dt);
+            pc.qJ[2] = d.q / (d.dx * d.dy * d.dt);
+            pc.qrho = d.q / (d.dx * d.dy * d.dz);
+            pc.cdtb[0] = kC * d.dtb / d.dx;
+            pc.cdtb[1] = kC * d.dtb / d.dy;
+            pc.cdtb[2] = kC * d.dtb / d.dz;
+            pbeg(MITHRA_K_PUSH, &e0);
+            CU(launch_push<real>(P, np, g, ef, E6, S4, pc, stream));
+            pend(MITHRA_K_PUSH, e0);
+            pbeg(MITHRA_K_STENCIL, &e0);
+            CU(launch_stencil<real>(L, g, cf, ncomp, stream));
+            pend(MITHRA_K_STENCIL, e0);
+            pbeg(MITHRA_K_MUR, &e0);
+            CU(launch_mur<real>(L, g, mur_order, ncomp, stream));
+            pend(MITHRA_K_MUR, e0);
+            pbeg(MITHRA_K_POWER, &e0);
+            const int M = (int)d.M;
+            const int slot = (int)(n % M);
+            CU(power_sample_ex<real>(E6, g, (int)d.kp, ring, slot, d.omega_h, ((double)n + 0.5) * d.dt, phase_cs,
+                                     stream));
+            if (n + 1 >= M) {
+                const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
+                const double scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
+                CU(launch_power_reduce(ring, phase_cs, M, g, scale, partial, npartial, ser_p + n, stream));
+            }
+            CU(launch_onaxis<real>(E6, onaxis_id, ser_e + n, stream));
+            pend(MITHRA_K_POWER, e0);
+            base = (base + 1) % 3;
+            ++nstep;
+            if (prof && prof_pending.size() > 4096) {
+                CU(cudaStreamSynchronize(stream));
+                prof_collect();
+            }
+        }
+        return MITHRA_OK;
+    }
+
+    real* field_ptr(int which, int level)
+    {
+        if (which < 4) return pot[lev(level)][which];
+        if (which < 8) return src[which - 4];
+        return eb[which - 8];
+    }
+
+    int fields(int which, int level, double* out, size_t cap) override
+    {
+        if (which < 0 || which > 13 || level < 0 || level > 1) return fail(MITHRA_EINVAL, "fields: bad index/level");
+        if (cap < (size_t)g.ncell) return fail(MITHRA_ERANGE, "fields: buffer too small");
+        std::vector<real> h((size_t)g.ncell);
+        CU(cudaMemcpyAsync(h.data(), field_ptr(which, level), (size_t)g.ncell * sizeof(real), cudaMemcpyDeviceToHost,
+                           stream));
+        CU(cudaStreamSynchronize(stream));
+        for (int64_t i = 0; i < g.ncell; ++i) out[i] = (double)h[(size_t)i];
+        return MITHRA_OK;
+    }
+
+    int set_field(int which, int level, const double* in, size_t n) override
+    {
+        if (which < 0 || which > 3 || level < 0 || level > 1) return fail(MITHRA_EINVAL, "set_field: bad index/level");
+        if (n != (size_t)g.ncell) return fail(MITHRA_EINVAL, "set_field: size must be nx*ny*nz");
+        std::vector<real> h((size_t)g.ncell);
+        for (int64_t i = 0; i < g.ncell; ++i) h[(size_t)i] = (real)in[i];
+        CU(cudaMemcpyAsync(field_ptr(which, level), h.data(), (size_t)g.ncell * sizeof(real), cudaMemcpyHostToDevice,
+                           stream));
+        CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
+    int ensure_rest_buf()
+    {
+        if (!rest_buf) rest_buf = (double*)mem.get((size_t)(np > 0 ? np : 1) * 6 * 8);
+        return rest_buf ? MITHRA_OK : fail(MITHRA_ENOMEM, "device allocation failed (particle staging)");
+    }
+
+    int particles(double* out, size_t cap) override
+    {
+        if (cap < (size_t)np) return fail(MITHRA_ERANGE, "particles: buffer too small");
+        if (np == 0) return MITHRA_OK;
+        int rc = ensure_rest_buf();
+        if (rc) return rc;
+        CU(launch_get_rest<real>(P, np, g, rest_buf, stream));
+        CU(cudaMemcpyAsync(out, rest_buf, (size_t)np * 6 * 8, cudaMemcpyDeviceToHost, stream));
+        CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
+    int set_particles(const double* in, size_t n) override
+    {
+        if (n != (size_t)np) return fail(MITHRA_EINVAL, "set_particles: row count must equal the bunch size");
+        if (np == 0) return MITHRA_OK;
+        int rc = ensure_rest_buf();
+        if (rc) return rc;
+        CU(cudaMemcpyAsync(rest_buf, in, (size_t)np * 6 * 8, cudaMemcpyHostToDevice, stream));
+        CU(launch_set_rest<real>(rest_buf, np, P, g, stream));
+        CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
+    int diag(double* fe, double* b3) override
+    {
+        Fields6<real> E6;
+        for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
+        double h[4] = {0, 0, 0, 0};
+        if (fe) CU(launch_energy<real>(E6, g, partial, npartial, small, stream));
+        if (b3) CU(launch_bunching<real>(P, np, g, d.kb, partial + npartial, npartial, small + 4, stream));
+        CU(cudaMemcpyAsync(h, small, 8, cudaMemcpyDeviceToHost, stream));
+        double hb[3] = {0, 0, 0};
+        CU(cudaMemcpyAsync(hb, small + 4, 24, cudaMemcpyDeviceToHost, stream));
+        CU(cudaStreamSynchronize(stream));
+        if (fe) *fe = h[0];
+        if (b3) {
+            b3[0] = hb[0];
+            b3[1] = hb[1];
+            b3[2] = hb[2];
+        }
+        if (fe && !std::isfinite(h[0])) return fail(MITHRA_EDIVERGED, "field energy is not finite");
+        return MITHRA_OK;
+    }
+
+    int series(int which, double* out, size_t cap, size_t* n_out) override
+    {
+        if (n_out) *n_out = (size_t)nstep;
+        if (!out) return MITHRA_OK;
+        if (cap < (size_t)nstep) return fail(MITHRA_ERANGE, "series: buffer too small");
+        if (nstep == 0) return MITHRA_OK;
+        if (which == 0) {
+            CU(cudaMemcpyAsync(out, ser_p, (size_t)nstep * 8, cudaMemcpyDeviceToHost, stream));
+        } else {
+            CU(cudaMemcpyAsync(out, ser_e, (size_t)nstep * 8, cudaMemcpyDeviceToHost, stream));
+        }
+        CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
+    int sync() override
+    {
+        CU(cudaStreamSynchronize(stream));
+        if (prof) prof_collect();
+        return MITHRA_OK;
+    }
+
+    void destroy_all() override
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        prof_collect();
+        for (auto e : ev_free) cudaEventDestroy(e);
+        ev_free.clear();
+        mem.release_all();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+    }
+};
+
+bool finite_all(std::initializer_list<double> v)
+{
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// Rest frame, mesh checks and placement (manual Sec. "Lorentz Transformation", Sec. MESH).
+int derive(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, const mithra_bunch& b, Derived& d,
+           ExtField& ef)
+{
+    const int kind = u.kind;
+    double g0 = b.gamma;
+    if (kind == 0 || kind == 2 || kind == 3) g0 = b.gamma / std::sqrt(1.0 + 0.5 * u.K * u.K);
+    else if (kind == 1) g0 = b.gamma / std::sqrt(1.0 + u.K * u.K);
+    if (!(g0 >= 1.0)) return fail(MITHRA_EINVAL, "gamma0 < 1: raise gamma or lower K");
+    d.g0 = g0;
+    d.b0 = std::sqrt(1.0 - 1.0 / (g0 * g0));
+    d.dz = g0 * gr.dz;
+    d.dx = gr.dx;
+    d.dy = gr.dy;
+    if (gr.solver == 0) {
+        const double r2 = (d.dz / d.dx) * (d.dz / d.dx) + (d.dz / d.dy) * (d.dz / d.dy);
+        const double ratio = std::sqrt(r2);
+        if (ratio >= 1.0) {
+            const double s = ratio / 0.99;
+            d.dx *= s;
+            d.dy *= s;
+        }
+        const double q2 = (d.dz / d.dx) * (d.dz / d.dx) + (d.dz / d.dy) * (d.dz / d.dy);
+        d.A = 0.25 * (1.0 + 0.02 / q2);
+        d.dt = d.dz / kC;
+    } else {
+        d.A = 0.0;
+        if (dt_lab > 0.0) {
+            d.dt = dt_lab / g0;
+        } else {
+            if (!(gr.courant > 0.0 && gr.courant < 1.0)) return fail(MITHRA_EINVAL, "FD needs 0 < courant < 1");
+            d.dt = gr.courant / (kC * std::sqrt(1.0 / (d.dx * d.dx) + 1.0 / (d.dy * d.dy) + 1.0 / (d.dz * d.dz)));
+        }
+    }
+    const int N = gr.substeps > 0 ? gr.substeps : 1;
+    d.dtb = d.dt / N;
+
+    ef = ExtField{};
+    ef.kind = kind;
+    ef.g0 = d.g0;
+    ef.b0 = d.b0;
+    const double th = u.pol_deg * kPi / 180.0;
+    ef.cpol = std::cos(th);
+    ef.spol = std::sin(th);
+    const double lam = u.lambda;
+    const double kk = 2.0 * kPi / lam;
+    ef.ku = kk;
+    ef.Lu = u.n_periods * lam;
+    ef.B0 = 2.0 * kPi * kMe * kC * u.K / (kQe * lam);
+    ef.qlam = 0.25 * lam;
+    ef.kL = kk;
+    ef.wL = kC * kk;
+    ef.E0 = u.K * kMe * kC * ef.wL / kQe;
+    ef.tp = u.pulse_fwhm / kC;
+    ef.signal = u.signal;
+    ef.w0 = (kind == 3) ? u.waist : 0.0;
+    ef.zr = (ef.w0 > 0.0) ? kPi * ef.w0 * ef.w0 / lam : 1.0;
+    if (kind == 0 || kind == 1) d.kstar = d.g0 * d.b0 * kk;
+    else if (kind == 2 || kind == 3) d.kstar = d.g0 * (1.0 + d.b0) * kk;
+    else d.kstar = kk;
+    if (kind == 0 || kind == 1) d.kb = d.g0 * kk + d.kstar;
+    else if (kind == 2 || kind == 3) d.kb = 2.0 * d.kstar;
+    else d.kb = d.kstar;
+    d.omega_h = gr.norm_freq * kC * d.kstar;
+
+    // placement: rest coordinates are the boost of lab coordinates measured from the event
+    // (t' = 0, undulator entrance).  Static undulator: the run starts when the entrance is
+    // dist/gamma0 ahead of the head (head = reference + 3 sig_z), so the lab reference sits at
+    // -(dist + gamma0^2 * 3 sig_z) at t' = 0.  Optical: reference at the origin; the pulse centre
+    // starts dist ahead and meets the reference at the focus.
+    double zeta_ref = 0.0;
+    if (kind == 0 || kind == 1) zeta_ref = -(u.dist_to_bunch_head + d.g0 * d.g0 * 3.0 * b.sig_z);
+    d.z_ref = d.g0 * zeta_ref;
+    d.T0 = -d.g0 * d.b0 * zeta_ref / kC;
+    ef.t_f = u.dist_to_bunch_head / (kC * (1.0 + d.b0));
+    ef.zeta_f = d.b0 * u.dist_to_bunch_head / (1.0 + d.b0);
+
+    d.x0 = gr.cx - 0.5 * (gr.nx - 1) * d.dx;
+    d.y0 = gr.cy - 0.5 * (gr.ny - 1) * d.dy;
+    d.z0 = d.z_ref + d.g0 * gr.cz - 0.5 * (gr.nz - 1) * d.dz;
+
+    const double zp = d.z_ref + d.g0 * gr.power_plane_dist;
+    double kp = std::round((zp - d.z0) / d.dz);
+    if (kp < 1) kp = 1;
+    if (kp > gr.nz - 2) kp = gr.nz - 2;
+    d.kp = kp;
+    double M = std::round(2.0 * kPi / (d.omega_h * d.dt));
+    if (!(M >= 1.0)) M = 1.0;
+    if (M > 1e6) return fail(MITHRA_EINVAL, "power window longer than 1e6 steps: check norm_freq / lambda");
+    d.M = M;
+    d.q = b.n > 0 ? -kQe * b.charge_e / (double)b.n : 0.0;
+    return MITHRA_OK;
+}
+
+template <typename real>
+int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, const mithra_bunch& b, mithra_t* out)
+{
+    RunT<real>* r = new RunT<real>();
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        r->mem.a = g_alloc;
+    }
+    int rc = derive(gr, dt_lab, u, b, r->d, r->ef);
+    if (rc) {
+        delete r;
+        return rc;
+    }
+    const Derived& d = r->d;
+    r->precision = gr.precision;
+    r->mur_order = gr.mur_order;
+    r->sort_every = gr.sort_every == 0 ? 20 : gr.sort_every;
+    r->np = b.n;
+    Geom& g = r->g;
+    g.nx = gr.nx;
+    g.ny = gr.ny;
+    g.nz = gr.nz;
+    g.sy = gr.nx;
+    g.sz = (int64_t)gr.nx * gr.ny;
+    g.ncell = g.sz * gr.nz;
+    g.dx = d.dx;
+    g.dy = d.dy;
+    g.dz = d.dz;
+    g.dt = d.dt;
+    g.dtb = d.dtb;
+    g.x0 = d.x0;
+    g.y0 = d.y0;
+    g.z0 = d.z0;
+    g.substeps = gr.substeps > 0 ? gr.substeps : 1;
+    g.space_charge = gr.space_charge ? 1 : 0;
+    const double cdt = kC * d.dt;
+    const double rx = (cdt / d.dx) * (cdt / d.dx), ry = (cdt / d.dy) * (cdt / d.dy), rz = (cdt / d.dz) * (cdt / d.dz);
+    r->cf.a1 = 2.0 * (1.0 - (1.0 - 2.0 * d.A) * rx - (1.0 - 2.0 * d.A) * ry - rz);
+    r->cf.ax = rx;
+    r->cf.ay = ry;
+    r->cf.a6 = rz - 2.0 * d.A * rx - 2.0 * d.A * ry;
+    r->cf.w = d.A;
+    r->cf.w0 = 1.0 - 2.0 * d.A;
+    r->cf.s_a = cdt * cdt * kMu0;
+    r->cf.s_phi = cdt * cdt * (kMu0 * kC * kC);   // 1/eps0 = mu0 c^2
+    r->onaxis_id = (int64_t)d.kp * g.sz + (int64_t)(gr.ny / 2) * g.sy + gr.nx / 2;
+
+    if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete r;
+        return fail(MITHRA_ECUDA, "cudaStreamCreateWithFlags failed");
+    }
+    r->own_stream = true;
+    if ((rc = r->alloc_all())) {
+        r->destroy_all();
+        delete r;
+        return rc;
+    }
+    if (b.n > 0) {
+        double* lab = (double*)r->mem.get((size_t)b.n * 6 * 8);
+        if (!lab) {
+            r->destroy_all();
+            delete r;
+            return fail(MITHRA_ENOMEM, "device allocation failed (lab particles)");
+        }
+        cudaError_t e = cudaMemcpyAsync(lab, b.lab_particles, (size_t)b.n * 6 * 8, cudaMemcpyHostToDevice, r->stream);
+        if (e == cudaSuccess) e = launch_boost<real>(lab, b.n, r->P, g, r->ef, d.z_ref, r->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+        r->mem.release(lab);
+        if (e != cudaSuccess) {
+            r->destroy_all();
+            delete r;
+            return fail(MITHRA_ECUDA, std::string("particle boost: ") + cudaGetErrorString(e));
+        }
+        if (r->sort_every > 0 && b.n > 1 && (rc = r->sort_now())) {
+            r->destroy_all();
+            delete r;
+            return rc;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) {
+        r->destroy_all();
+        delete r;
+        return fail(MITHRA_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+    }
+    *out = r;
+    return MITHRA_OK;
+}
+
+}  // namespace
+
+extern "C" int mithra_create(const mithra_grid* gr, double dt_lab, const mithra_undulator* u, const mithra_bunch* b,
+                             mithra_t* out)
+{
+    if (!gr || !u || !b || !out) return fail(MITHRA_EINVAL, "create: null argument");
+    *out = nullptr;
+    if (gr->nx < 6 || gr->ny < 6 || gr->nz < 6) return fail(MITHRA_EINVAL, "create: each axis needs >= 6 nodes");
+    if ((int64_t)gr->nx * gr->ny * gr->nz >= (int64_t(1) << 31) - 1)
+        return fail(MITHRA_EINVAL, "create: more than 2^31 - 2 nodes");
+    if (!finite_all({gr->dx, gr->dy, gr->dz, gr->cx, gr->cy, gr->cz, gr->courant, gr->power_plane_dist, gr->norm_freq,
+                     u->K, u->lambda, u->n_periods, u->pol_deg, u->waist, u->pulse_fwhm, u->dist_to_bunch_head, b->gamma,
+                     b->charge_e, b->sig_z, dt_lab}))
+        return fail(MITHRA_EINVAL, "create: non-finite parameter");
+    if (!(gr->dx > 0 && gr->dy > 0 && gr->dz > 0)) return fail(MITHRA_EINVAL, "create: resolution must be > 0");
+    if (gr->solver != 0 && gr->solver != 1) return fail(MITHRA_EINVAL, "create: solver must be 0 (NSFD) or 1 (FD)");
+    if (gr->mur_order != 1 && gr->mur_order != 2) return fail(MITHRA_EINVAL, "create: mur_order must be 1 or 2");
+    if (gr->precision != 0 && gr->precision != 1) return fail(MITHRA_EINVAL, "create: precision must be 0 or 1");
+    if (gr->substeps < 0 || gr->substeps > 1024) return fail(MITHRA_EINVAL, "create: substeps out of range");
+    if (!(gr->norm_freq > 0)) return fail(MITHRA_EINVAL, "create: norm_freq must be > 0");
+    if (u->kind < -1 || u->kind > 3) return fail(MITHRA_EINVAL, "create: unknown undulator kind");
+    if (!(u->lambda > 0)) return fail(MITHRA_EINVAL, "create: lambda must be > 0");
+    if (!(b->gamma >= 1.0)) return fail(MITHRA_EINVAL, "create: gamma must be >= 1");
+    if (b->n < 0 || b->n >= (int64_t(1) << 31)) return fail(MITHRA_EINVAL, "create: particle count out of range");
+    if (b->n > 0) {
+        if (!b->lab_particles) return fail(MITHRA_EINVAL, "create: lab_particles is null");
+        if (!(b->charge_e > 0)) return fail(MITHRA_EINVAL, "create: charge_e must be > 0");
+        for (int64_t i = 0; i < 6 * b->n; ++i)
+            if (!std::isfinite(b->lab_particles[i])) return fail(MITHRA_EINVAL, "create: non-finite particle value");
+    }
+    if (gr->precision == 0) return create_t<double>(*gr, dt_lab, *u, *b, out);
+    return create_t<float>(*gr, dt_lab, *u, *b, out);
+}
+
+extern "C" int mithra_set_stream(mithra_t r, void* stream)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    CU(cudaStreamSynchronize(r->stream));
+    if (r->own_stream) cudaStreamDestroy(r->stream);
+    r->own_stream = false;
+    r->stream = (cudaStream_t)stream;
+    return MITHRA_OK;
+}
+
+extern "C" int mithra_step(mithra_t r, int64_t n)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    if (n < 0) return fail(MITHRA_EINVAL, "step: negative count");
+    return r->step(n);
+}
+
+extern "C" int mithra_sync(mithra_t r)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    return r->sync();
+}
+
+extern "C" int mithra_fields(mithra_t r, int which, int level, double* out, size_t cap)
+{
+    if (!r || !out) return fail(MITHRA_EINVAL, "null argument");
+    return r->fields(which, level, out, cap);
+}
+
+extern "C" int mithra_set_field(mithra_t r, int which, int level, const double* in, size_t n)
+{
+    if (!r || !in) return fail(MITHRA_EINVAL, "null argument");
+    return r->set_field(which, level, in, n);
+}
+
+extern "C" int mithra_particles(mithra_t r, double* out, size_t cap)
+{
+    if (!r || (!out && r->np > 0)) return fail(MITHRA_EINVAL, "null argument");
+    return r->particles(out, cap);
+}
+
+extern "C" int mithra_set_particles(mithra_t r, const double* in, size_t n)
+{
+    if (!r || (!in && n > 0)) return fail(MITHRA_EINVAL, "null argument");
+    return r->set_particles(in, n);
+}
+
+extern "C" int mithra_radiated_power(mithra_t r, double* p, double* t, size_t cap, size_t* n_out)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    int rc = r->series(0, p, cap, n_out);
+    if (rc) return rc;
+    if (t) {
+        const double zp = r->d.z0 + r->d.kp * r->d.dz;
+        for (int64_t i = 0; i < r->nstep; ++i)
+            t[i] = r->d.g0 * (r->d.T0 + ((double)i + 0.5) * r->d.dt + r->d.b0 * zp / kC);
+    }
+    return MITHRA_OK;
+}
+
+extern "C" int mithra_onaxis_field(mithra_t r, double* ex, size_t cap, size_t* n_out)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    return r->series(1, ex, cap, n_out);
+}
+
+extern "C" int mithra_diag(mithra_t r, double* fe, double* b3)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    return r->diag(fe, b3);
+}
+
+extern "C" int mithra_info(mithra_t r, double* info, int64_t* hbm)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    if (info) {
+        const Derived& d = r->d;
+        const double v[19] = {d.g0, d.b0, d.dx, d.dy, d.dz, d.dt, d.dtb, d.A, d.x0, d.y0,
+                              d.z0, d.T0, d.omega_h, d.M, d.kp, d.z_ref, d.q, d.kstar, d.kb};
+        std::memcpy(info, v, sizeof v);
+    }
+    if (hbm) *hbm = (int64_t)r->mem.total;
+    return MITHRA_OK;
+}
+
+extern "C" int mithra_set_profiling(mithra_t r, int on)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    CU(cudaStreamSynchronize(r->stream));
+    r->prof_collect();
+    for (int k = 0; k < MITHRA_K_COUNT; ++k) {
+        r->prof_ms[k] = 0.0;
+        r->prof_n[k] = 0;
+    }
+    r->prof = on != 0;
+    return MITHRA_OK;
+}
+
+extern "C" int mithra_kernel_stats(mithra_t r, int kid, double* total_ms, int64_t* launches)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    if (kid < 0 || kid >= MITHRA_K_COUNT) return fail(MITHRA_EINVAL, "bad kernel id");
+    CU(cudaStreamSynchronize(r->stream));
+    r->prof_collect();
+    if (total_ms) *total_ms = r->prof_ms[kid];
+    if (launches) *launches = r->prof_n[kid];
+    return MITHRA_OK;
+}
+
+extern "C" void mithra_destroy(mithra_t r)
+{
+    if (!r) return;
+    r->destroy_all();
+    delete r;
+}

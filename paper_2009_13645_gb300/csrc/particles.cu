@@ -1,0 +1,287 @@
+// Particle kernels: boost of the lab bunch into the rest frame (Eqs. LorentzTrasnformParticles,
+// LorentzTransformDeltaR), and one fused pass per field step that evaluates the external
+// field in FP64, gathers the self-field with linear weights (Eq. fieldInterpolation), advances
+// the momentum with the Boris scheme (Eq. BorisScheme, FP64) and deposits the Umeda zigzag
+// current and the linear-weight charge (Sec. "Current Deposition") with atomics.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mithra {
+
+__device__ __forceinline__ bool active_cell(int i, int j, int k, const Geom& g)
+{
+    return i >= 1 && i <= g.nx - 3 && j >= 1 && j <= g.ny - 3 && k >= 1 && k <= g.nz - 3;
+}
+
+template <typename real>
+__device__ __forceinline__ void split_pos(double X, int32_t* c, real* f)
+{
+    const double fl = floor(X);
+    real o = (real)(X - fl);
+    int32_t ci = (int32_t)fl;
+    if (o >= (real)1) { o -= (real)1; ci += 1; }
+    *c = ci;
+    *f = o;
+}
+
+// One straight piece a -> b (cell units, relative to the base cell) lying in local cell `cl`:
+// current on the edges parallel to each axis with the exact path average of the linear
+// weights of the two other axes.
+template <typename real>
+__device__ __forceinline__ void deposit_piece(const real a[3], const real b[3], const int cl[3], const int base[3],
+                                              const Fields4<real>& src, const Geom& g, const PushConst& pc)
+{
+    real la[3], d[3], mid[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        la[l] = a[l] - (real)cl[l];
+        d[l] = b[l] - a[l];
+        mid[l] = la[l] + (real)0.5 * d[l];
+    }
+    const int64_t o = (int64_t)(base[2] + cl[2]) * g.sz + (int64_t)(base[1] + cl[1]) * g.sy + (base[0] + cl[0]);
+    const int64_t st[3] = {1, g.sy, g.sz};
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        if (d[l] == (real)0) continue;
+        const int m = (l + 1) % 3, n = (l + 2) % 3;
+        const real F = (real)pc.qJ[l] * d[l];
+        const real cross = d[m] * d[n] * (real)(1.0 / 12.0);
+        const real wm1 = mid[m], wm0 = (real)1 - mid[m];
+        const real wn1 = mid[n], wn0 = (real)1 - mid[n];
+        real* J = src.c[l];
+        atomicAdd(J + o, F * (wm0 * wn0 + cross));
+        atomicAdd(J + o + st[m], F * (wm1 * wn0 - cross));
+        atomicAdd(J + o + st[n], F * (wm0 * wn1 - cross));
+        atomicAdd(J + o + st[m] + st[n], F * (wm1 * wn1 + cross));
+    }
+}
+
+// Umeda zigzag of the move A -> B (relative to the base cell, |B - A| <= 1 per axis).
+template <typename real>
+__device__ __forceinline__ void zigzag(const real A[3], const real B[3], const int base[3], const Fields4<real>& src,
+                                       const Geom& g, const PushConst& pc)
+{
+    int c1[3], c2[3];
+    real R[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        c1[l] = (int)floor(A[l]);
+        c2[l] = (int)floor(B[l]);
+        const real lo = (real)min(c1[l], c2[l]), hi = (real)max(c1[l], c2[l]);
+        const real mid = (real)0.5 * (A[l] + B[l]);
+        R[l] = fmin(lo + (real)1, fmax(hi, mid));
+    }
+    deposit_piece(A, R, c1, base, src, g, pc);
+    deposit_piece(R, B, c2, base, src, g, pc);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(128) k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb,
+                                              Fields4<real> src, PushConst pc)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    int ci[3] = {P.ix[p], P.iy[p], P.iz[p]};
+    real f[3] = {P.fx[p], P.fy[p], P.fz[p]};
+    double u[3] = {P.ux[p], P.uy[p], P.uz[p]};
+    for (int m = 0; m < g.substeps; ++m) {
+        const double t = pc.t_half + (double)m * g.dtb;
+        const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
+        const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
+        const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
+        double E[3], B[3];
+        external_field(ef, x, y, z, t, E, B);
+        const bool a1 = active_cell(ci[0], ci[1], ci[2], g);
+        if (a1) {
+            const real wx[2] = {(real)1 - f[0], f[0]};
+            const real wy[2] = {(real)1 - f[1], f[1]};
+            const real wz[2] = {(real)1 - f[2], f[2]};
+            real s[6] = {0, 0, 0, 0, 0, 0};
+            const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
+#pragma unroll
+            for (int K = 0; K < 2; ++K)
+#pragma unroll
+                for (int J = 0; J < 2; ++J)
+#pragma unroll
+                    for (int I = 0; I < 2; ++I) {
+                        const real w = wx[I] * wy[J] * wz[K];
+                        const int64_t id = o + K * g.sz + J * g.sy + I;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) s[c] += w * __ldg(eb.c[c] + id);
+                    }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                E[c] += (double)s[c];
+                B[c] += (double)s[3 + c];
+            }
+        }
+        boris(u, E, B, g.dtb);
+        const double ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        real b[3];
+        int nc[3];
+        real nf[3];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            b[l] = f[l] + (real)(pc.cdtb[l] * u[l] * ig);
+            const real fl = floor(b[l]);
+            int c = (int)fl;
+            real o = b[l] - fl;
+            if (o >= (real)1) { o -= (real)1; c += 1; }
+            nc[l] = ci[l] + c;
+            nf[l] = o;
+        }
+        if (a1 && active_cell(nc[0], nc[1], nc[2], g)) {
+            real mx = fmax(fabs(b[0] - f[0]), fmax(fabs(b[1] - f[1]), fabs(b[2] - f[2])));
+            if (mx <= (real)1) {
+                zigzag(f, b, ci, src, g, pc);
+            } else {
+                const int ns = (int)ceil((double)mx);
+                real A[3], Bq[3];
+                for (int s = 0; s < ns; ++s) {
+#pragma unroll
+                    for (int l = 0; l < 3; ++l) {
+                        const real dl = b[l] - f[l];
+                        A[l] = (s == 0) ? f[l] : f[l] + dl * ((real)s / (real)ns);
+                        Bq[l] = (s == ns - 1) ? b[l] : f[l] + dl * ((real)(s + 1) / (real)ns);
+                    }
+                    zigzag(A, Bq, ci, src, g, pc);
+                }
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            ci[l] = nc[l];
+            f[l] = nf[l];
+        }
+    }
+    if (g.space_charge && active_cell(ci[0], ci[1], ci[2], g)) {
+        const real wx[2] = {(real)1 - f[0], f[0]};
+        const real wy[2] = {(real)1 - f[1], f[1]};
+        const real wz[2] = {(real)1 - f[2], f[2]};
+        const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
+        const real q = (real)pc.qrho;
+#pragma unroll
+        for (int K = 0; K < 2; ++K)
+#pragma unroll
+            for (int J = 0; J < 2; ++J)
+#pragma unroll
+                for (int I = 0; I < 2; ++I)
+                    atomicAdd(src.c[3] + o + K * g.sz + J * g.sy + I, q * wx[I] * wy[J] * wz[K]);
+    }
+    P.ix[p] = ci[0];
+    P.iy[p] = ci[1];
+    P.iz[p] = ci[2];
+    P.fx[p] = f[0];
+    P.fy[p] = f[1];
+    P.fz[p] = f[2];
+    P.ux[p] = u[0];
+    P.uy[p] = u[1];
+    P.uz[p] = u[2];
+}
+
+// Lab-frame macro-particles (x, y, z relative to the bunch reference at t' = 0, gamma*beta) to
+// the rest frame at the common time T0 + dt/2 (the time of r^{1/2}).
+template <typename real>
+__global__ void k_boost(const double* __restrict__ lab, int64_t np, Particles<real> P, Geom g, double g0, double b0,
+                        double z_ref)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double* L = lab + 6 * p;
+    const double ux = L[3], uy = L[4], uzl = L[5];
+    const double gl = sqrt(1.0 + ux * ux + uy * uy + uzl * uzl);
+    const double uz = g0 * (uzl - b0 * gl);
+    const double ig = 1.0 / sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+    // ballistic shift with the rest-frame velocity over c (T0 + dt/2 - t_event)
+    const double s = g0 * b0 * L[2] + 0.5 * kC * g.dt;
+    const double x = L[0] + ux * ig * s;
+    const double y = L[1] + uy * ig * s;
+    const double z = z_ref + g0 * L[2] + uz * ig * s;
+    split_pos<real>((x - g.x0) / g.dx, P.ix + p, P.fx + p);
+    split_pos<real>((y - g.y0) / g.dy, P.iy + p, P.fy + p);
+    split_pos<real>((z - g.z0) / g.dz, P.iz + p, P.fz + p);
+    P.ux[p] = ux;
+    P.uy[p] = uy;
+    P.uz[p] = uz;
+    P.id[p] = (int32_t)p;
+}
+
+template <typename real>
+__global__ void k_set_rest(const double* __restrict__ r6, int64_t np, Particles<real> P, Geom g)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double* R = r6 + 6 * p;
+    split_pos<real>((R[0] - g.x0) / g.dx, P.ix + p, P.fx + p);
+    split_pos<real>((R[1] - g.y0) / g.dy, P.iy + p, P.fy + p);
+    split_pos<real>((R[2] - g.z0) / g.dz, P.iz + p, P.fz + p);
+    P.ux[p] = R[3];
+    P.uy[p] = R[4];
+    P.uz[p] = R[5];
+    P.id[p] = (int32_t)p;
+}
+
+template <typename real>
+__global__ void k_get_rest(Particles<real> P, int64_t np, Geom g, double* __restrict__ r6)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    double* R = r6 + 6 * (int64_t)P.id[p];
+    R[0] = g.x0 + ((double)P.ix[p] + (double)P.fx[p]) * g.dx;
+    R[1] = g.y0 + ((double)P.iy[p] + (double)P.fy[p]) * g.dy;
+    R[2] = g.z0 + ((double)P.iz[p] + (double)P.fz[p]) * g.dz;
+    R[3] = P.ux[p];
+    R[4] = P.uy[p];
+    R[5] = P.uz[p];
+}
+
+static inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename real>
+cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,
+                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_push<real><<<nblocks(np, 128), 128, 0, st>>>(P, np, g, ef, eb, src, pc);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_boost(const double* lab6, int64_t np, const Particles<real>& P, const Geom& g, const ExtField& ef,
+                         double z_ref, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_boost<real><<<nblocks(np, 256), 256, 0, st>>>(lab6, np, P, g, ef.g0, ef.b0, z_ref);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_set_rest(const double* rest6, int64_t np, const Particles<real>& P, const Geom& g, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_set_rest<real><<<nblocks(np, 256), 256, 0, st>>>(rest6, np, P, g);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_get_rest(const Particles<real>& P, int64_t np, const Geom& g, double* rest6, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_get_rest<real><<<nblocks(np, 256), 256, 0, st>>>(P, np, g, rest6);
+    return cudaGetLastError();
+}
+
+#define MITHRA_INST(real)                                                                                              \
+    template cudaError_t launch_push<real>(const Particles<real>&, int64_t, const Geom&, const ExtField&,             \
+                                           const Fields6<real>&, const Fields4<real>&, const PushConst&,             \
+                                           cudaStream_t);                                                              \
+    template cudaError_t launch_boost<real>(const double*, int64_t, const Particles<real>&, const Geom&,              \
+                                            const ExtField&, double, cudaStream_t);                                   \
+    template cudaError_t launch_set_rest<real>(const double*, int64_t, const Particles<real>&, const Geom&,           \
+                                               cudaStream_t);                                                          \
+    template cudaError_t launch_get_rest<real>(const Particles<real>&, int64_t, const Geom&, double*, cudaStream_t);
+MITHRA_INST(float)
+MITHRA_INST(double)
+#undef MITHRA_INST
+
+}  // namespace mithra

@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances:
+* FP64 path: 1e-11 relative (max |gpu - oracle| / max |oracle|) on fields and potentials, the
+  stated bound; the only difference from the oracle is the order of floating-point atomic
+  additions in the deposition and FMA contraction.
+* FP32-mixed path: fields stored in FP32 (unit round-off 6e-8), momentum, external field and
+  reductions in FP64: 1e-4 relative field energy and 1 % radiated power.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.helpers import vacuum
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - only on a GPU machine
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2009_13645_gb300 as mithra  # noqa: E402
+
+
+def rel(a, b):
+    s = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (s if s > 0 else 1.0))
+
+
+def pair(w, precision, lab=None, sort_every=0):
+    lab = workloads.lab_bunch(w) if lab is None else lab
+    o = oracle.Run(oracle.params_from(w), lab)
+    g = mithra.Run.from_workload(w, lab, precision=precision, sort_every=sort_every)
+    return o, g
+
+
+SMALL = workloads.scaled(workloads.WORKLOADS["undulator_24x24x96"], nx=21, ny=19, nz=45,
+                         n_particles=1500)
+
+
+@pytest.mark.parametrize("name", list(workloads.WORKLOADS))
+def test_derived_constants_match(name):
+    w = workloads.scaled(workloads.WORKLOADS[name], n_particles=16)
+    o, g = pair(w, 0)
+    io, ig = o.info(), g.info()
+    for k in oracle.INFO_KEYS:
+        a, b = ig[k], io[k]
+        assert abs(a - b) <= 1e-13 * max(abs(b), 1e-300) + (1e-13 * abs(io["z_ref"]) if k in ("z0",) else 0), (k, a, b)
+
+
+@pytest.mark.parametrize("solver,courant,order", [(0, 1.0, 2), (0, 1.0, 1), (1, 0.9, 2), (1, 0.6, 1)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 3e-5)])
+def test_vacuum_fields(solver, courant, order, precision, tol):
+    nx, ny, nz = 37, 29, 45     # several 32x8 tiles and z chunks with ragged tails
+    w = vacuum(nx, ny, nz, 1.3e-3, 1.1e-3, 1.0e-3, solver=solver, courant=courant, mur_order=order)
+    o = oracle.Run(oracle.params_from(w))
+    g = mithra.Run.from_workload(w, np.zeros((0, 6)), precision=precision)
+    rng = np.random.default_rng(7)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for c in range(4):
+        for lev in range(2):
+            a = rng.standard_normal((nz, ny, nx)) * 0.1
+            a += np.exp(-((x - 18 - 3 * c) ** 2 + (y - 14) ** 2 + (z - 22 + lev) ** 2) / 20.0)
+            if precision == 1:
+                a = a.astype(np.float32).astype(np.float64)
+            o.set_field(c, lev, a)
+            g.set_field(c, lev, a)
+    o.step(40)
+    g.step(40)
+    for c in range(4):
+        for lev in range(2):
+            e = rel(g.field(c, lev), o.field(c, lev))
+            assert e < tol, (c, lev, e)
+    for name in ("Ex", "Ey", "Ez", "Bx", "By", "Bz"):
+        e = rel(g.field(name), o.field(name))
+        assert e < tol * 10, (name, e)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_boost_matches(kind, precision):
+    base = workloads.WORKLOADS["ics_192x192x768" if kind == 3 else "fel_128x128x512"]
+    w = workloads.scaled(base, n_particles=3000, nx=16, ny=16, nz=24, und_kind=kind)
+    o, g = pair(w, precision, sort_every=-1)
+    po, pg = o.particles(), g.particles()
+    inf = o.info()
+    D = np.array([inf["dx"], inf["dy"], inf["dz"]])
+    scale = np.maximum(np.abs(po[:, :3]).max(axis=0), D)
+    tolx = 1e-13 if precision == 0 else 1e-6
+    # positions: error relative to the cell (the GPU stores cell + offset)
+    assert np.max(np.abs(pg[:, :3] - po[:, :3]) / D) < tolx * np.max(scale / D)
+    assert np.max(np.abs(pg[:, 3:] - po[:, 3:])) < 1e-12 * np.max(np.abs(po[:, 3:]))
+
+
+def _compare_run(o, g, steps, tol_field, tol_part, chunks=1):
+    for _ in range(chunks):
+        o.step(steps // chunks)
+        g.step(steps // chunks)
+    for c, name in enumerate(("Ax", "Ay", "Az", "phi")):
+        for lev in range(2):
+            e = rel(g.field(c, lev), o.field(c, lev))
+            assert e < tol_field, (name, lev, e)
+    for name in ("Jx", "Jy", "Jz", "rho", "Ex", "Ey", "Ez", "Bx", "By", "Bz"):
+        e = rel(g.field(name), o.field(name))
+        assert e < tol_field * 10, (name, e)
+    po, pg = o.particles(), g.particles()
+    inf = o.info()
+    D = np.array([inf["dx"], inf["dy"], inf["dz"]])
+    if len(po):
+        assert np.max(np.abs(pg[:, :3] - po[:, :3]) / D) < tol_part
+        assert np.max(np.abs(pg[:, 3:] - po[:, 3:])) < tol_part * max(1.0, np.max(np.abs(po[:, 3:])))
+    return po, pg
+
+
+def test_full_step_fp64_undulator_small():
+    """The full coupled step (config-1 physics on a ragged grid), FP64 path vs oracle."""
+    o, g = pair(SMALL, 0)
+    _compare_run(o, g, 200, 1e-11, 1e-10)
+    po, to, eo = o.series()
+    pg, tg, eg = g.series()
+    assert len(pg) == len(po) == 200
+    assert rel(pg, po) < 1e-10 and rel(eg, eo) < 1e-10
+    assert np.max(np.abs(tg - to)) <= 1e-15 * np.max(np.abs(to))
+    fo, bo = o.diag()
+    fg, bg = g.diag()
+    assert abs(fg - fo) < 1e-11 * fo
+    assert abs(bg - bo) < 1e-12
+    assert abs(g.bunching_complex() - o.bunching_complex()) < 1e-12
+
+
+@pytest.mark.parametrize("kind,substeps,solver,order", [(0, 3, 1, 1), (1, 1, 0, 2), (1, 2, 1, 2), (3, 1, 0, 2),
+                                                        (2, 2, 0, 1)])
+def test_full_step_fp64_kinds(kind, substeps, solver, order):
+    if kind >= 2:
+        base = workloads.WORKLOADS["ics_192x192x768"]
+        w = workloads.scaled(base, nx=22, ny=20, nz=40, n_particles=1200, sig_x=2e-9, sig_y=2e-9,
+                             sig_z=2e-9, und_kind=kind, substeps=substeps, solver=solver, mur_order=order,
+                             courant=0.8)
+    else:
+        base = workloads.WORKLOADS["fel_128x128x512"]
+        w = workloads.scaled(base, nx=22, ny=20, nz=40, n_particles=1200, und_kind=kind, substeps=substeps,
+                             solver=solver, mur_order=order, courant=0.8, sig_z=0.3e-6, dist_head=1e-4,
+                             sig_x=1.5e-5, sig_y=1.5e-5)
+    o, g = pair(w, 0)
+    _compare_run(o, g, 60, 1e-11, 1e-10)
+
+
+def test_full_step_fp32_mixed_bounds():
+    """FP32-mixed path: field energy within 1e-4 and radiated power within 1 % of the oracle."""
+    w = workloads.WORKLOADS["undulator_24x24x96"]
+    o, g = pair(w, 1)
+    o.step(300)
+    g.step(300)
+    fo, bo = o.diag()
+    fg, bg = g.diag()
+    assert abs(fg - fo) / fo < 1e-4, (fg, fo)
+    assert abs(bg - bo) < 1e-4
+    po, _, _ = o.series()
+    pg, _, _ = g.series()
+    sig = np.abs(po) > 1e-3 * np.max(np.abs(po))
+    assert sig.sum() > 100
+    assert np.max(np.abs(pg[sig] - po[sig]) / np.abs(po[sig])) < 0.01
+    for c in range(4):
+        assert rel(g.field(c, 1), o.field(c, 1)) < 1e-3
+
+
+def test_sort_does_not_change_physics():
+    w = SMALL
+    lab = workloads.lab_bunch(w)
+    a = mithra.Run.from_workload(w, lab, precision=0, sort_every=1)
+    b = mithra.Run.from_workload(w, lab, precision=0, sort_every=-1)
+    a.step(50)
+    b.step(50)
+    for c in range(4):
+        assert rel(a.field(c, 1), b.field(c, 1)) < 1e-12
+    assert np.max(np.abs(a.particles() - b.particles())) < 1e-12 * np.max(np.abs(b.particles()))
+
+
+def test_edge_cases_empty_and_outside():
+    # no particles at all
+    w0 = workloads.scaled(SMALL, n_particles=0)
+    o, g = pair(w0, 0, lab=np.zeros((0, 6)))
+    _compare_run(o, g, 10, 1e-11, 1e-10)
+    # every particle far outside the grid: pushed by the external field only
+    w1 = workloads.scaled(SMALL, n_particles=64)
+    lab = workloads.lab_bunch(w1)
+    lab[:, 0] += 1.0
+    o, g = pair(w1, 0, lab=lab)
+    _compare_run(o, g, 20, 1e-11, 1e-10)
+    assert np.max(np.abs(g.field("rho"))) == 0.0
+    # a bunch much longer than the grid (most particles outside, some inside)
+    w2 = workloads.scaled(SMALL, n_particles=2000, sig_z=40e-6)
+    o, g = pair(w2, 0)
+    _compare_run(o, g, 30, 1e-11, 1e-10)
+
+
+def test_fullsize_fel_two_steps():
+    """The full 128x128x512 grid with 2M macro-particles, in the bench's launch configuration,
+    two steps against the oracle (all fields, a sample of particles)."""
+    w = workloads.WORKLOADS["fel_128x128x512"]
+    lab = workloads.lab_bunch(w)
+    o = oracle.Run(oracle.params_from(w), lab)
+    o.step(2)
+    for precision, tol in ((0, 1e-11), (1, 2e-5)):
+        g = mithra.Run.from_workload(w, lab, precision=precision)
+        g.step(2)
+        for c in range(4):
+            for lev in range(2):
+                e = rel(g.field(c, lev), o.field(c, lev))
+                assert e < tol * (10 if c < 3 else 1) or np.max(np.abs(o.field(c, lev))) == 0, (precision, c, lev, e)
+        po, pg = o.particles(), g.particles()
+        inf = o.info()
+        D = np.array([inf["dx"], inf["dy"], inf["dz"]])
+        idx = np.random.default_rng(0).choice(len(po), 20000, replace=False)
+        assert np.max(np.abs(pg[idx, :3] - po[idx, :3]) / D) < (1e-9 if precision == 0 else 1e-5)
+        g.close()
