@@ -61,7 +61,7 @@ struct orc_run {
     double *src[4];
     double *eb[6];
     int64_t np;
-    double *pr;
+    double *pr;   /* np x 6: position relative to node (0,0,0) (m), then gamma*beta */
     int64_t step;
     double *ring;
     double *ring_t;
@@ -190,7 +190,15 @@ orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np)
 
     r->np = np;
     r->pr = (double *)malloc((size_t)(np > 0 ? np : 1) * 6 * sizeof(double));
-    for (int64_t i = 0; i < np; ++i) boost_particle(r, lab6 + 6 * i, r->pr + 6 * i);
+    for (int64_t i = 0; i < np; ++i) {
+        double *q = r->pr + 6 * i;
+        boost_particle(r, lab6 + 6 * i, q);
+        /* a particle is located by its distance to the grid corner (Sec. "Field Evaluation"):
+           far from the origin this keeps the resolution of the step-by-step displacements */
+        q[0] -= r->x0;
+        q[1] -= r->y0;
+        q[2] -= r->z0;
+    }
     /* macro-particle charge: the bunch charge spread over the macro-particles */
     r->q = (np > 0) ? -QE * p->charge_e / (double)np : 0.0;
 
@@ -601,11 +609,12 @@ void orc_boris(double u[3], const double E[3], const double B[3], double dtb)
 /* (Sec. "Current Deposition", Umeda zigzag).                                */
 /* ------------------------------------------------------------------------- */
 
+/* cell coordinates of a position given relative to node (0,0,0) */
 static void cellpos(const orc_run *r, const double *pos, double X[3])
 {
-    X[0] = (pos[0] - r->x0) / r->dx;
-    X[1] = (pos[1] - r->y0) / r->dy;
-    X[2] = (pos[2] - r->z0) / r->dz;
+    X[0] = pos[0] / r->dx;
+    X[1] = pos[1] / r->dy;
+    X[2] = pos[2] / r->dz;
 }
 
 static int active(const orc_run *r, const double X[3])
@@ -715,8 +724,10 @@ void orc_deposit_moves(orc_run *r, const double *old6, const double *new6, int64
     for (int c = 0; c < 4; ++c) memset(r->src[c], 0, (size_t)r->ncell * sizeof(double));
     for (int64_t p = 0; p < n; ++p) {
         double X1[3], X2[3];
-        cellpos(r, old6 + 6 * p, X1);
-        cellpos(r, new6 + 6 * p, X2);
+        const double a[3] = {old6[6 * p] - r->x0, old6[6 * p + 1] - r->y0, old6[6 * p + 2] - r->z0};
+        const double b[3] = {new6[6 * p] - r->x0, new6[6 * p + 1] - r->y0, new6[6 * p + 2] - r->z0};
+        cellpos(r, a, X1);
+        cellpos(r, b, X2);
         if (active(r, X1) && active(r, X2)) deposit_move(r, X1, X2);
         if (active(r, X2)) deposit_rho(r, X2);
     }
@@ -732,7 +743,7 @@ static void push_deposit(orc_run *r)
         for (int m = 0; m < N; ++m) {
             const double t = r->T0 + ((double)r->step + 0.5) * r->dt + m * r->dtb;
             double E[3], B[3], Es[3] = {0, 0, 0}, Bs[3] = {0, 0, 0}, X1[3], X2[3];
-            orc_external_field(r, pos[0], pos[1], pos[2], t, E, B);
+            orc_external_field(r, r->x0 + pos[0], r->y0 + pos[1], r->z0 + pos[2], t, E, B);
             cellpos(r, pos, X1);
             const int a1 = active(r, X1);
             if (a1) gather(r, X1, Es, Bs);
@@ -879,9 +890,25 @@ void orc_set_field(orc_run *r, int which, int lev, const double *in)
     memcpy(field_ptr(r, which, lev), in, (size_t)r->ncell * sizeof(double));
 }
 
-void orc_get_particles(const orc_run *r, double *out6) { memcpy(out6, r->pr, (size_t)r->np * 6 * sizeof(double)); }
+void orc_get_particles(const orc_run *r, double *out6)
+{
+    memcpy(out6, r->pr, (size_t)r->np * 6 * sizeof(double));
+    for (int64_t p = 0; p < r->np; ++p) {
+        out6[6 * p + 0] += r->x0;
+        out6[6 * p + 1] += r->y0;
+        out6[6 * p + 2] += r->z0;
+    }
+}
 
-void orc_set_particles(orc_run *r, const double *rest6) { memcpy(r->pr, rest6, (size_t)r->np * 6 * sizeof(double)); }
+void orc_set_particles(orc_run *r, const double *rest6)
+{
+    memcpy(r->pr, rest6, (size_t)r->np * 6 * sizeof(double));
+    for (int64_t p = 0; p < r->np; ++p) {
+        r->pr[6 * p + 0] -= r->x0;
+        r->pr[6 * p + 1] -= r->y0;
+        r->pr[6 * p + 2] -= r->z0;
+    }
+}
 
 int64_t orc_num_particles(const orc_run *r) { return r->np; }
 
@@ -918,7 +945,7 @@ void orc_diag(const orc_run *r, double *field_energy, double *bunching)
     if (bunching) {
         double re = 0, cre = 0, im = 0, cim = 0;
         for (int64_t p = 0; p < r->np; ++p) {
-            const double ph = r->kb * r->pr[6 * p + 2];
+            const double ph = r->kb * (r->z0 + r->pr[6 * p + 2]);
             nsum(&re, &cre, cos(ph));
             nsum(&im, &cim, sin(ph));
         }
