@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of the rest-frame FDTD/PIC time step on GB300.
+
+One step = one field step of the whole hot path: E and B at nodes, external field + gather +
+Boris + zigzag/charge deposition for every particle, the potential update with Mur
+boundaries, the radiated-power DFT sample (and the counting sort every 20 steps).
+
+Workload: the FEL-like run, 128x128x512 nodes (8.39 M cells), 2 M macro-particles, planar
+undulator K = 1.4, lambda_u = 1.8 cm, gamma = 100, shot-noise phases (synthetic, seeded).
+Headline value: cell-updates/s of the FP32-mixed path; particle-pushes/s and the FP64 path are
+reported beside it.  With --gpus N each rank runs an independent replica (weak scaling, no
+collective on the data path).
+
+--impl reference times the FP64 CPU oracle (the plain program the kernels are checked against)
+on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-pushes/s + cell-updates/s (FP32-mixed vs FP64) at stated error; served p99"
+WORKLOAD = "fel_128x128x512"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e["source_hash"] != _source_hash(e["sources"]):
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_oracle_rate(w, lab, budget_s: float, max_steps: int):
+    """Oracle throughput on the workload: steps until the budget is spent (at least one)."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Run(oracle.params_from(w), lab)
+    t_create = time.perf_counter() - t0
+    steps = 0
+    t1 = time.perf_counter()
+    while steps < max_steps:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t1 > budget_s:
+            break
+    dt = time.perf_counter() - t1
+    return o, steps, dt, t_create
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import workloads
+    w = workloads.WORKLOADS[WORKLOAD]
+    lab = workloads.lab_bunch(w)
+    import oracle
+    o = oracle.Run(oracle.params_from(w), lab)
+    o.step(min(args.warmup, 1))   # the oracle has no cache to warm; one step settles page faults
+    budget = float(os.environ.get("MITHRA_REF_BUDGET_S", "150"))
+    t1 = time.perf_counter()
+    steps = 0
+    while steps < args.steps:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t1 > budget:
+            break
+    dt = time.perf_counter() - t1
+    cells = w.nx * w.ny * w.nz
+    val = cells * steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "steps_timed": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [w.nx, w.ny, w.nz], "particles": w.n_particles,
+                       "precision": "fp64 (CPU oracle, serial)"},
+            "particle_pushes_per_s": w.n_particles * steps / dt,
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} full field steps of {WORKLOAD} ({cells} cells, "
+                                       f"{w.n_particles} particles), serial FP64 C"},
+            "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2009_13645_gb300 as m
+    import workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    m.use_torch_allocator(True)
+    w = workloads.WORKLOADS[WORKLOAD]
+    lab = workloads.lab_bunch(w)
+    cells = w.nx * w.ny * w.nz
+    K, W = args.steps, max(args.warmup, 3)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def reduce_max(x: float) -> float:
+        if ws == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_run(precision: int, steps: int, sample_clocks: bool):
+        stream = torch.cuda.Stream()
+        run = m.Run.from_workload(w, lab, precision=precision, stream=stream.cuda_stream)
+        run.step(W)
+        run.sync()
+        run.set_profiling(True)
+        barrier()
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.start()
+        l0 = m.kernel_launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        run.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        launches = m.kernel_launches() - l0
+        barrier()
+        clocks = clk.stop() if clk else None
+        ms = ev0.elapsed_time(ev1)
+        stats = run.kernel_stats()
+        info = run.info()
+        run.close()
+        return ms, stats, launches, clocks, info
+
+    # ---- FP32-mixed (headline) and FP64 ----------------------------------------------------
+    ms32, stats32, launches, clocks, info = timed_run(1, K, True)
+    ms32 = reduce_max(ms32)
+    res64 = None
+    if not args.no_fp64:
+        K64 = max(10, K // 2)
+        ms64, stats64, _, _, _ = timed_run(0, K64, False)
+        ms64 = reduce_max(ms64)
+        res64 = {"value": ws * cells * K64 / (ms64 * 1e-3), "unit": "cell-updates/s",
+                 "particle_pushes_per_s": ws * w.n_particles * K64 / (ms64 * 1e-3), "ms_per_step": ms64 / K64,
+                 "steps": K64, "kernel_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stats64.items() if v[1]}}
+
+    # ---- end to end through the C ABI from pinned host memory -------------------------------
+    pinned = torch.empty(lab.shape, dtype=torch.float64, pin_memory=True)
+    pinned.numpy()[:] = lab
+    barrier()
+    t0 = time.perf_counter()
+    b = m.Bunch()
+    b.n = lab.shape[0]
+    b.charge_e, b.gamma, b.sig_z = w.charge_e, w.gamma, w.sig_z
+    import ctypes
+    b.lab_particles = ctypes.cast(ctypes.c_void_p(pinned.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    run = m.Run(m.grid_from(w, 1), m.undulator_from(w), b)
+    run.step(K)
+    p_ser, t_ser, _ = run.series()
+    fe, bunch = run.diag()
+    t_e2e = time.perf_counter() - t0
+    run.close()
+    t_e2e = reduce_max(t_e2e)
+    h2d = lab.nbytes
+    d2h = 2 * 8 * K + 8 * 4
+
+    # ---- roofline of the dominant kernel -----------------------------------------------------
+    hbm, peak_kind = _peaks()
+    per_launch = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stats32.items()}
+    dominant = max(stats32, key=lambda k: stats32[k][0])
+    ncell = cells
+    # algorithmic bytes per launch (FP32-mixed)
+    alg = {
+        "stencil": 4 * 4 * 4 * ncell,                       # 4 potentials x (psi^n, psi^{n-1}, source, psi^{n+1})
+        "emit_eb": (3 + 3 + 1 + 6) * 4 * ncell,             # A^n, A^{n+1}, phi^n in; 6 components out
+        "push_deposit": 2 * 48 * w.n_particles,             # particle state in and out (cell, offset, momentum)
+        "clear_sources": 4 * 4 * ncell,
+        "mur": 0,
+        "power": 0,
+        "sort": 0,
+    }
+    roof = None
+    for kern in (dominant, "stencil"):
+        if alg.get(kern):
+            achieved = alg[kern] / (per_launch[kern] * 1e-3) / 1e9
+            roof = {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": _ncu_traffic(kern),
+                    "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                    if peak_kind == "measured" else "fallback 6.8 TB/s",
+                    "alg_bytes_per_launch": alg[kern], "ms_per_launch": per_launch[kern]}
+            break
+    stencil_roof = None
+    if per_launch.get("stencil"):
+        a = alg["stencil"] / (per_launch["stencil"] * 1e-3) / 1e9
+        stencil_roof = {"achieved": a, "frac": a / hbm, "ms_per_launch": per_launch["stencil"],
+                        "traffic": _ncu_traffic("stencil")}
+
+    # ---- CPU baseline (oracle) and the error of the GPU path against it ----------------------
+    cpu = None
+    err = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        o, s_cpu, dt_cpu, _ = cpu_oracle_rate(w, lab, args.cpu_budget, 6)
+        cpu = {"value": cells * s_cpu / dt_cpu, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{s_cpu} full field steps of {WORKLOAD} after creation, serial FP64 C",
+               "particle_pushes_per_s": w.n_particles * s_cpu / dt_cpu}
+        err = {"steps": s_cpu}
+        fo, bo = o.diag()
+        for prec, tag in ((1, "fp32_mixed"), (0, "fp64")):
+            g = m.Run.from_workload(w, lab, precision=prec)
+            g.step(s_cpu)
+            fg, bg = g.diag()
+            l2 = []
+            for c in range(3):
+                a, bb = g.field(c, 1), o.field(c, 1)
+                l2.append(float(np.linalg.norm(a - bb) / max(np.linalg.norm(bb), 1e-300)))
+            err[tag] = {"field_l2_rel_A": max(l2), "field_energy_rel": abs(fg - fo) / fo,
+                        "bunching_abs": abs(bg - bo)}
+            g.close()
+
+    value = ws * cells * K / (ms32 * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [w.nx, w.ny, w.nz], "particles": w.n_particles,
+                   "precision": "fp32-mixed (fields, offsets, gather, deposit in f32; momentum, external "
+                                "field, diagnostics in f64)",
+                   "l2": "inputs larger than L2 (fields 0.74 GB + particles 0.1 GB resident)",
+                   "parallelism": f"{ws} independent replica(s)", "sort_every": 20},
+        "particle_pushes_per_s": ws * w.n_particles * K / (ms32 * 1e-3),
+        "kernel_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stats32.items() if v[1]},
+        "fp64": res64,
+        "roofline": roof,
+        "stencil_roofline": stencil_roof,
+        "cpu_baseline": cpu,
+        "error_vs_oracle": err,
+        "e2e": {"value": ws * cells * K / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K, "what": "mithra_create from pinned host particles (H2D), "
+                f"{K} steps, power series + diagnostics to host (D2H)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "hbm_bytes": info.get("hbm_bytes"),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

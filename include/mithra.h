@@ -181,6 +181,8 @@ int mithra_info(mithra_t run, double *info19, int64_t *hbm_bytes);
 #define MITHRA_K_CLEAR 6
 #define MITHRA_K_COUNT 7
 int mithra_set_profiling(mithra_t run, int on);
+/* Number of CUDA kernels this library has launched since it was loaded (all runs, all threads). */
+int64_t mithra_kernel_launches(void);
 int mithra_kernel_stats(mithra_t run, int kernel_id, double *total_ms, int64_t *launches);
 const char *mithra_kernel_name(int kernel_id);
 

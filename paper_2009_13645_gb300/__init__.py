@@ -89,12 +89,18 @@ def load(rebuild: bool = False):
     L.mithra_destroy.restype = None
     L.mithra_last_error.restype = C.c_char_p
     L.mithra_version.restype = C.c_int
+    L.mithra_kernel_launches.restype = C.c_int64
     _lib = L
     return L
 
 
 def lib():
     return load()
+
+
+def kernel_launches() -> int:
+    """CUDA kernels launched by libmithra in this process so far."""
+    return int(load().mithra_kernel_launches())
 
 
 def _check(rc):

@@ -101,6 +101,7 @@ cudaError_t power_sample_ex(const Fields6<real>& eb, const Geom& g, int kp, doub
     const int64_t plane = (int64_t)g.nx * g.ny;
     k_power_sample<real><<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(eb, g, kp, ring, slot, omega_h, t_sample,
                                                                          phase_cs);
+    count_launches(1);
     return cudaGetLastError();
 }
 template cudaError_t power_sample_ex<float>(const Fields6<float>&, const Geom&, int, double*, int, double, double,
@@ -113,6 +114,7 @@ cudaError_t launch_power_reduce(const double* ring, const double* phase_cs, int 
 {
     k_power_reduce<<<npartial, kRedThreads, 0, st>>>(ring, phase_cs, M, g, partial);
     k_final<<<1, kRedThreads, 0, st>>>(partial, npartial, 1, scale, out);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -127,6 +129,7 @@ template <typename real>
 cudaError_t launch_onaxis(const Fields6<real>& eb, int64_t id, double* out, cudaStream_t st)
 {
     k_onaxis<real><<<1, 32, 0, st>>>(eb.c[0], id, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -157,6 +160,7 @@ cudaError_t launch_energy(const Fields6<real>& eb, const Geom& g, double* partia
 {
     k_energy<real><<<npartial, kRedThreads, 0, st>>>(eb, g.ncell, partial);
     k_final<<<1, kRedThreads, 0, st>>>(partial, npartial, 1, g.dx * g.dy * g.dz, out);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -202,6 +206,7 @@ cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g,
     k_bunching<real><<<npartial, kRedThreads, 0, st>>>(P, np, g, kb, partial);
     k_final<<<1, kRedThreads, 0, st>>>(partial, npartial, 2, 1.0, out3 + 1);
     k_bunch_final<<<1, 32, 0, st>>>(out3, 1.0 / (double)np);
+    count_launches(3);
     return cudaGetLastError();
 }
 

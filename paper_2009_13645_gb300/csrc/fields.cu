@@ -326,6 +326,7 @@ cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const Sten
     const int nchunk = (g.nz - 2 + a.kchunk - 1) / a.kchunk;
     const dim3 grd((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, nchunk * ncomp);
     k_stencil<real><<<grd, blk, 0, st>>>(a, g.sy, g.sz);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -355,6 +356,7 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     k_mur_faces<real><<<dim3((unsigned)((faces + thr - 1) / thr), ncomp), thr, 0, st>>>(a, g.sy, g.sz, faces);
     k_mur_edges<real><<<dim3((unsigned)((edges + thr - 1) / thr), ncomp), thr, 0, st>>>(a, g.sy, g.sz, 2, edges);
     k_mur_edges<real><<<dim3(1, ncomp), 32, 0, st>>>(a, g.sy, g.sz, 3, 8);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -376,6 +378,7 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     const dim3 blk(32, 8);
     const dim3 grd((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, (g.nz - 2 + a.kchunk - 1) / a.kchunk);
     k_emit<real><<<grd, blk, 0, st>>>(a, g);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,9 @@
 
 namespace mithra {
 
+// Number of kernels launched by this library since it was loaded (all runs, all threads).
+void count_launches(int64_t n);
+
 // Pointers of one step's potential levels: n0 = psi^{n-1}, n1 = psi^n, out = psi^{n+1}, plus the
 // sources J_x, J_y, J_z, rho.
 template <typename real>

@@ -1,5 +1,6 @@
 // C ABI of libmithra: run set-up (rest frame, mesh checks, placement), device memory,
 // the per-step launch sequence and the accessors declared in include/mithra.h.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -46,6 +47,10 @@ extern "C" int mithra_set_allocator(mithra_alloc_fn alloc, mithra_free_fn free_f
     g_alloc.ctx = ctx;
     return MITHRA_OK;
 }
+
+static std::atomic<int64_t> g_launches{0};
+void mithra::count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern "C" int64_t mithra_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" const char* mithra_last_error(void) { return g_err.c_str(); }
 extern "C" int mithra_version(void) { return 1; }

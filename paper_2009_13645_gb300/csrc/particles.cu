@@ -243,6 +243,7 @@ cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, con
 {
     if (np <= 0) return cudaSuccess;
     k_push<real><<<nblocks(np, 128), 128, 0, st>>>(P, np, g, ef, eb, src, pc);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -252,6 +253,7 @@ cudaError_t launch_boost(const double* lab6, int64_t np, const Particles<real>& 
 {
     if (np <= 0) return cudaSuccess;
     k_boost<real><<<nblocks(np, 256), 256, 0, st>>>(lab6, np, P, g, ef.g0, ef.b0, z_ref);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -260,6 +262,7 @@ cudaError_t launch_set_rest(const double* rest6, int64_t np, const Particles<rea
 {
     if (np <= 0) return cudaSuccess;
     k_set_rest<real><<<nblocks(np, 256), 256, 0, st>>>(rest6, np, P, g);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -268,6 +271,7 @@ cudaError_t launch_get_rest(const Particles<real>& P, int64_t np, const Geom& g,
 {
     if (np <= 0) return cudaSuccess;
     k_get_rest<real><<<nblocks(np, 256), 256, 0, st>>>(P, np, g, rest6);
+    count_launches(1);
     return cudaGetLastError();
 }
 

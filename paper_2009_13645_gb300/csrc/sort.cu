@@ -94,6 +94,7 @@ static cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int64_t n, in
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles <= 1) {
         k_scan_tile<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        count_launches(1);
         return cudaGetLastError();
     }
     int32_t* partial = scratch;
@@ -101,6 +102,7 @@ static cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int64_t n, in
     cudaError_t e = scan_exclusive(partial, partial, tiles, scratch + tiles, st);
     if (e != cudaSuccess) return e;
     k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, partial);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -139,10 +141,12 @@ cudaError_t launch_sort(Particles<real>& P, Particles<real>& tmp, int64_t np, co
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((np + 255) / 256);
     k_keys<real><<<nb, 256, 0, st>>>(P, np, g, s.key, s.count, s.nbins);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(s.count, s.offset, s.nbins, s.blocksum, st)) != cudaSuccess) return e;
     k_slot<<<nb, 256, 0, st>>>(s.key, np, s.offset, s.perm);
     k_scatter<real><<<nb, 256, 0, st>>>(P, tmp, s.perm, np);
+    count_launches(2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     Particles<real> t = P;
     P = tmp;
