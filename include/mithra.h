@@ -186,6 +186,25 @@ int64_t mithra_kernel_launches(void);
 int mithra_kernel_stats(mithra_t run, int kernel_id, double *total_ms, int64_t *launches);
 const char *mithra_kernel_name(int kernel_id);
 
+/* Field energy of caller-supplied E and B arrays, computed without allocating any device memory.
+   No counterpart in the paper: it serves callers that cannot call cudaMalloc at that moment
+   (a pool that is already fully carved up, a thread that must not take allocator locks, a
+   real-time loop where an allocation's implicit synchronisation would stall every stream).
+   eb[0..5]: device pointers to E_x, E_y, E_z, B_x, B_y, B_z (n values each, FP64 when precision
+   is 0, FP32 when 1); energy_out: caller-owned device pointer to one double, written with
+   sum(eps0 E^2/2 + B^2/(2 mu0)) * cell_volume; the work is enqueued on `stream` (a cudaStream_t,
+   NULL for the legacy default stream) and the call returns without waiting.
+   Scratch: one FP64 partial per 4096 nodes in a fixed 256 KiB array inside the library's device
+   memory, present on every GPU that loads the library until the process exits; hence n may not
+   exceed MITHRA_NOALLOC_MAX_NODES (EINVAL otherwise).  The first call on a device looks up that
+   array's device address with the device current (cudaGetSymbolAddress); make that first call
+   before any stream capture.  All calls share the array: calls whose work overlaps on the GPU
+   race, so order them on one stream.  Each call writes every partial it reads; nothing needs
+   clearing between calls.  Errors: EINVAL, ECUDA. */
+#define MITHRA_NOALLOC_MAX_NODES (134217728LL)
+int mithra_field_energy_noalloc(const void *const eb[6], int precision, int64_t n, double cell_volume,
+                                double *energy_out, void *stream);
+
 /* Release everything the run holds (waits for its stream).  NULL is ignored. */
 void mithra_destroy(mithra_t run);
 

@@ -90,12 +90,27 @@ def load(rebuild: bool = False):
     L.mithra_last_error.restype = C.c_char_p
     L.mithra_version.restype = C.c_int
     L.mithra_kernel_launches.restype = C.c_int64
+    L.mithra_field_energy_noalloc.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int64, C.c_double,
+                                              C.c_void_p, C.c_void_p]
     _lib = L
     return L
 
 
 def lib():
     return load()
+
+
+NOALLOC_MAX_NODES = 134217728
+
+
+def mithra_field_energy_noalloc(eb_ptrs, precision: int, n: int, cell_volume: float, out_ptr: int,
+                                stream: int = 0) -> None:
+    """Field energy of device E/B arrays into the device double at out_ptr, with no device
+    allocation (see include/mithra.h).  eb_ptrs: six device addresses (ints)."""
+    L = load()
+    arr = (C.c_void_p * 6)(*[C.c_void_p(int(p)) for p in eb_ptrs])
+    _check(L.mithra_field_energy_noalloc(arr, int(precision), int(n), float(cell_volume),
+                                         C.c_void_p(int(out_ptr)), C.c_void_p(int(stream))))
 
 
 def kernel_launches() -> int:

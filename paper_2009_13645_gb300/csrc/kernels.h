@@ -7,6 +7,8 @@ namespace mithra {
 
 // Number of kernels launched by this library since it was loaded (all runs, all threads).
 void count_launches(int64_t n);
+// Record `msg` as the calling thread's last error (read by mithra_last_error) and return `code`.
+int set_last_error(int code, const char* msg);
 
 // Pointers of one step's potential levels: n0 = psi^{n-1}, n1 = psi^n, out = psi^{n+1}, plus the
 // sources J_x, J_y, J_z, rho.

@@ -53,6 +53,7 @@ void mithra::count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_ord
 extern "C" int64_t mithra_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" const char* mithra_last_error(void) { return g_err.c_str(); }
+int mithra::set_last_error(int code, const char* msg) { return fail(code, msg); }
 extern "C" int mithra_version(void) { return 1; }
 
 static const char* kKernelNames[MITHRA_K_COUNT] = {"emit_eb", "push_deposit", "stencil", "mur", "power", "sort",
