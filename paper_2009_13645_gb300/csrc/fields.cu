@@ -1,6 +1,8 @@
 // Field kernels: potential update (manual Eq. updateEquation; FD = NSFD with A = 0),
 // Mur absorbing boundaries (Sec. "Boundary Truncation") and E, B at nodes
 // (Sec. "Field Evaluation").
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -95,76 +97,49 @@ struct MurArgs {
     int ncomp;
     int order;
     double cdt, dt, D[3];
+    // face coefficients per normal axis, in the storage type: first order beta_0 (= beta_4),
+    // beta_1 (= beta_3); second order gamma_0, gamma_1 and the tangential gammas of the axes
+    // (a+1)%3 and (a+2)%3
+    real f0[3], f1[3], ft[3][2];
 };
 
 __device__ inline int64_t lin(int i, int j, int k, int64_t sy, int64_t sz) { return (int64_t)k * sz + (int64_t)j * sy + i; }
 
-// Decode face point `t` of a lattice (e[0], e[1], e[2]): 6 faces, each interior of the
-// other two axes.  Returns false when t is beyond the face count.
-__device__ inline bool face_point(int64_t t, const int e[3], int ijk[3], int* axis, int* side)
-{
-    for (int a = 0; a < 3; ++a) {
-        const int u = (a + 1) % 3, v = (a + 2) % 3;
-        const int64_t nf = (int64_t)(e[u] - 2) * (e[v] - 2);
-        for (int sd = 0; sd < 2; ++sd) {
-            if (t < nf) {
-                ijk[a] = sd ? e[a] - 1 : 0;
-                ijk[u] = 1 + (int)(t % (e[u] - 2));
-                ijk[v] = 1 + (int)(t / (e[u] - 2));
-                *axis = a;
-                *side = sd;
-                return true;
-            }
-            t -= nf;
-        }
-    }
-    return false;
-}
-
+// One face per blockIdx.z (axis = z / 2, side = z % 2), one component per blockIdx.y.
 template <typename real>
-__global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz, int64_t maxpts)
+__global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
 {
     const int comp = blockIdx.y;
     if (comp >= a.ncomp) return;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= maxpts) return;
+    const int ax = blockIdx.z >> 1, sd = blockIdx.z & 1;
     const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
-    int p[3], ax, sd;
-    if (!face_point(t, e, p, &ax, &sd)) return;
+    const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;   // tangential axes, u before v
+    const int nu = e[u] - 2, nv = e[v] - 2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nu * nv) return;
+    int p[3];
+    p[ax] = sd ? e[ax] - 1 : 0;
+    p[u] = 1 + t % nu;
+    p[v] = 1 + t / nu;
+    const int64_t st[3] = {1, sy, sz};
+    const int64_t ib = lin(p[0], p[1], p[2], sy, sz);
+    const int64_t iq = ib + (sd ? -st[ax] : st[ax]);   // inward neighbour
     real* __restrict__ n1 = a.n1[comp];
     const real* __restrict__ n0 = a.n0[comp];
     const real* __restrict__ nm = a.nm[comp];
-    int q[3] = {p[0], p[1], p[2]};
-    q[ax] += sd ? -1 : 1;   // inward neighbour
-    const int64_t ib = lin(p[0], p[1], p[2], sy, sz), iq = lin(q[0], q[1], q[2], sy, sz);
-    const double D = a.D[ax], cdt = a.cdt;
-    const double den = 1.0 / (cdt + D);
-    double v;
+    real vout;
     if (a.order == 1) {
-        const double b0 = (cdt - D) * den, b1 = 2.0 * D * den;
-        v = b0 * (double)nm[ib] + b1 * (double)n0[ib] - (double)nm[iq] + b1 * (double)n0[iq] + b0 * (double)n1[iq];
+        const real b0 = a.f0[ax], b1 = a.f1[ax];
+        vout = b0 * (nm[ib] + n1[iq]) + b1 * (n0[ib] + n0[iq]) - nm[iq];
     } else {
-        const int u = (ax + 1) % 3, w = (ax + 2) % 3;
-        const double ru = (cdt / a.D[u]) * (cdt / a.D[u]), rw = (cdt / a.D[w]) * (cdt / a.D[w]);
-        const double g0 = (cdt - D) * den, g1 = D * (2.0 - ru - rw) * den;
-        const double gu = 0.5 * ru * D * den, gw = 0.5 * rw * D * den;
-        int t1[3], t2[3];
-        double sb = 0.0, sq = 0.0;   // transverse neighbours on the face and on the inner plane
-        for (int s = 0; s < 2; ++s) {
-            const int ta = s ? w : u;
-            const double gt = s ? gw : gu;
-            for (int d = -1; d <= 1; d += 2) {
-                t1[0] = p[0]; t1[1] = p[1]; t1[2] = p[2];
-                t2[0] = q[0]; t2[1] = q[1]; t2[2] = q[2];
-                t1[ta] += d;
-                t2[ta] += d;
-                sb += gt * (double)n0[lin(t1[0], t1[1], t1[2], sy, sz)];
-                sq += gt * (double)n0[lin(t2[0], t2[1], t2[2], sy, sz)];
-            }
-        }
-        v = g0 * (double)nm[ib] + g1 * (double)n0[ib] - (double)nm[iq] + g1 * (double)n0[iq] + g0 * (double)n1[iq] + sb + sq;
+        // tangential neighbours at level n on the face and on the inner plane
+        const int ta = (ax + 1) % 3, tb = (ax + 2) % 3;
+        const real ga = a.ft[ax][0], gb = a.ft[ax][1];
+        const real sa = n0[ib + st[ta]] + n0[ib - st[ta]] + n0[iq + st[ta]] + n0[iq - st[ta]];
+        const real sb = n0[ib + st[tb]] + n0[ib - st[tb]] + n0[iq + st[tb]] + n0[iq - st[tb]];
+        vout = a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + ga * sa + gb * sb;
     }
-    n1[ib] = (real)v;
+    n1[ib] = vout;
 }
 
 // Edges (cls = 2) and corners (cls = 3).
@@ -239,8 +214,11 @@ __global__ void k_mur_edges(MurArgs<real> a, int64_t sy, int64_t sz, int cls, in
 
 // ---------------------------------------------------------------------------------------
 // E and B at interior nodes from node averages of the staggered potentials (levels n and
-// n+1) and phi^n:  E = -(A^{n+1} - A^n)/dt - grad_c phi,  B = (curl_c A^n + curl_c A^{n+1}) / 2.
-// Each thread walks a chunk of z for one (i, j) node column.
+// n+1) and phi^n:  E = -(A^{n+1} - A^n)/dt - grad_c phi,  B = (curl_c A^n + curl_c A^{n+1}) / 2,
+// in the storage type.  Per step only the nodes the particles will gather from (the box the
+// push kernel reduced from the cells it deposited into) and the power plane are needed; inside
+// that box the sources of the previous step are cleared in the same pass.  With box == null the
+// whole interior is emitted (diagnostics) and nothing is cleared.
 // ---------------------------------------------------------------------------------------
 template <typename real>
 struct EmitArgs {
@@ -248,51 +226,76 @@ struct EmitArgs {
     const real* a1[3];   // A^{n+1}
     const real* phi;     // phi^n (node), may be null when space charge is off
     real* eb[6];
-    double idt, i2dx, i2dy, i2dz;
+    real* src[4];        // sources to clear inside the box (entries may be null)
+    real idt, i2dx, i2dy, i2dz;
     int kchunk;
+    int kp;              // plane emitted in full (< 0: none)
+    const int* box;      // cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit; null: whole grid
+    int* box_reset;      // box the next push reduces into: reset to empty here (may be null)
 };
 
 template <typename real>
-__device__ inline double anode(const real* __restrict__ A, int64_t id, int64_t back)
+__device__ __forceinline__ real navg(const real* __restrict__ A, int64_t id, int64_t back)
 {
-    return 0.5 * ((double)__ldg(A + id) + (double)__ldg(A + id - back));
+    return (real)0.5 * (__ldg(A + id) + __ldg(A + id - back));
 }
 
 template <typename real>
 __global__ void __launch_bounds__(256) k_emit(EmitArgs<real> a, Geom g)
 {
-    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
+    const int i0 = 1 + blockIdx.x * blockDim.x, j0 = 1 + blockIdx.y * blockDim.y;
     const int k0 = 1 + blockIdx.z * a.kchunk;
     const int k1 = min(g.nz - 2, k0 + a.kchunk - 1);
+    if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < 6 && threadIdx.y == 0)
+        a.box_reset[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+    // nodes [lo - 1, hi + 2] around the cells of the last deposit: the particles gather at their
+    // cells' nodes next step, and with sub-steps they move up to one cell during that step
+    int bl[3] = {1, 1, 1}, bh[3] = {g.nx - 2, g.ny - 2, g.nz - 2};
+    if (a.box) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            bl[d] = __ldg(a.box + d) - 1;
+            bh[d] = __ldg(a.box + 3 + d) + 2;
+        }
+    }
+    const bool plane_here = a.kp >= k0 && a.kp <= k1;
+    const bool box_here = bl[0] <= min(bh[0], i0 + (int)blockDim.x - 1) && bh[0] >= i0 &&
+                          bl[1] <= min(bh[1], j0 + (int)blockDim.y - 1) && bh[1] >= j0 && bl[2] <= min(bh[2], k1) &&
+                          bh[2] >= k0;
+    if (!plane_here && !box_here) return;
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (i > g.nx - 2 || j > g.ny - 2) return;
+    const bool col_in = i >= bl[0] && i <= bh[0] && j >= bl[1] && j <= bh[1];
     const int64_t sy = g.sy, sz = g.sz;
+    const int64_t back[3] = {1, sy, sz};
     for (int k = k0; k <= k1; ++k) {
+        const bool in = col_in && k >= bl[2] && k <= bh[2];
+        if (!in && k != a.kp) continue;
         const int64_t id = (int64_t)k * sz + (int64_t)j * sy + i;
-        double E[3], B[3] = {0.0, 0.0, 0.0};
-        const int64_t back[3] = {1, sy, sz};
-        for (int c = 0; c < 3; ++c)
-            E[c] = -(anode(a.a1[c], id, back[c]) - anode(a.a0[c], id, back[c])) * a.idt;
+        if (in && a.box) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (a.src[c]) a.src[c][id] = (real)0;
+        }
+        real E[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) E[c] = (navg(a.a0[c], id, back[c]) - navg(a.a1[c], id, back[c])) * a.idt;
         if (a.phi) {
-            E[0] -= ((double)__ldg(a.phi + id + 1) - (double)__ldg(a.phi + id - 1)) * a.i2dx;
-            E[1] -= ((double)__ldg(a.phi + id + sy) - (double)__ldg(a.phi + id - sy)) * a.i2dy;
-            E[2] -= ((double)__ldg(a.phi + id + sz) - (double)__ldg(a.phi + id - sz)) * a.i2dz;
+            E[0] -= (__ldg(a.phi + id + 1) - __ldg(a.phi + id - 1)) * a.i2dx;
+            E[1] -= (__ldg(a.phi + id + sy) - __ldg(a.phi + id - sy)) * a.i2dy;
+            E[2] -= (__ldg(a.phi + id + sz) - __ldg(a.phi + id - sz)) * a.i2dz;
         }
-        for (int l = 0; l < 2; ++l) {
-            const real* const* A = l ? a.a1 : a.a0;
-            B[0] += (anode(A[2], id + sy, sz) - anode(A[2], id - sy, sz)) * a.i2dy
-                  - (anode(A[1], id + sz, sy) - anode(A[1], id - sz, sy)) * a.i2dz;
-            B[1] += (anode(A[0], id + sz, 1) - anode(A[0], id - sz, 1)) * a.i2dz
-                  - (anode(A[2], id + 1, sz) - anode(A[2], id - 1, sz)) * a.i2dx;
-            B[2] += (anode(A[1], id + 1, sy) - anode(A[1], id - 1, sy)) * a.i2dx
-                  - (anode(A[0], id + sy, 1) - anode(A[0], id - sy, 1)) * a.i2dy;
-        }
-        a.eb[0][id] = (real)E[0];
-        a.eb[1][id] = (real)E[1];
-        a.eb[2][id] = (real)E[2];
-        a.eb[3][id] = (real)(0.5 * B[0]);
-        a.eb[4][id] = (real)(0.5 * B[1]);
-        a.eb[5][id] = (real)(0.5 * B[2]);
+        // node-averaged sums of the two levels, S_c = A_c^n + A_c^{n+1}, at the six neighbours
+        auto S = [&](int c, int64_t at) { return navg(a.a0[c], at, back[c]) + navg(a.a1[c], at, back[c]); };
+        const real bx = (S(2, id + sy) - S(2, id - sy)) * a.i2dy - (S(1, id + sz) - S(1, id - sz)) * a.i2dz;
+        const real by = (S(0, id + sz) - S(0, id - sz)) * a.i2dz - (S(2, id + 1) - S(2, id - 1)) * a.i2dx;
+        const real bz = (S(1, id + 1) - S(1, id - 1)) * a.i2dx - (S(0, id + sy) - S(0, id - sy)) * a.i2dy;
+        a.eb[0][id] = E[0];
+        a.eb[1][id] = E[1];
+        a.eb[2][id] = E[2];
+        a.eb[3][id] = (real)0.5 * bx;
+        a.eb[4][id] = (real)0.5 * by;
+        a.eb[5][id] = (real)0.5 * bz;
     }
 }
 
@@ -349,11 +352,33 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     a.D[0] = g.dx;
     a.D[1] = g.dy;
     a.D[2] = g.dz;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double D = a.D[ax], cdt = a.cdt, den = 1.0 / (cdt + D);
+        if (order == 1) {
+            a.f0[ax] = (real)((cdt - D) * den);            // beta_0 = beta_4
+            a.f1[ax] = (real)(2.0 * D * den);              // beta_1 = beta_3
+            a.ft[ax][0] = a.ft[ax][1] = (real)0;
+        } else {
+            const int ta = (ax + 1) % 3, tb = (ax + 2) % 3;
+            const double ra = (cdt / a.D[ta]) * (cdt / a.D[ta]), rb = (cdt / a.D[tb]) * (cdt / a.D[tb]);
+            a.f0[ax] = (real)((cdt - D) * den);            // gamma_0 = gamma_4
+            a.f1[ax] = (real)(D * (2.0 - ra - rb) * den);  // gamma_1 = gamma_3
+            a.ft[ax][0] = (real)(0.5 * ra * D * den);      // gamma of the (ax+1) neighbours
+            a.ft[ax][1] = (real)(0.5 * rb * D * den);      // gamma of the (ax+2) neighbours
+        }
+    }
+    int64_t maxface = 0;
+    for (int c = 0; c < ncomp; ++c) {
+        const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
+        for (int ax = 0; ax < 3; ++ax) {
+            const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
+            maxface = std::max<int64_t>(maxface, (e[u] - 2) * (e[v] - 2));
+        }
+    }
     const int64_t nx = g.nx, ny = g.ny, nz = g.nz;
-    const int64_t faces = 2 * ((ny - 2) * (nz - 2) + (nx - 2) * (nz - 2) + (nx - 2) * (ny - 2));
     const int64_t edges = 4 * ((nx - 2) + (ny - 2) + (nz - 2));
     const int thr = 256;
-    k_mur_faces<real><<<dim3((unsigned)((faces + thr - 1) / thr), ncomp), thr, 0, st>>>(a, g.sy, g.sz, faces);
+    k_mur_faces<real><<<dim3((unsigned)((maxface + thr - 1) / thr), ncomp, 6), thr, 0, st>>>(a, g.sy, g.sz);
     k_mur_edges<real><<<dim3((unsigned)((edges + thr - 1) / thr), ncomp), thr, 0, st>>>(a, g.sy, g.sz, 2, edges);
     k_mur_edges<real><<<dim3(1, ncomp), 32, 0, st>>>(a, g.sy, g.sz, 3, 8);
     count_launches(3);
@@ -361,7 +386,8 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
 }
 
 template <typename real>
-cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, cudaStream_t st)
+cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, const EmitBox& bx,
+                        cudaStream_t st)
 {
     EmitArgs<real> a;
     for (int c = 0; c < 3; ++c) {
@@ -370,11 +396,16 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     }
     a.phi = g.space_charge ? L.n0[3] : nullptr;
     for (int c = 0; c < 6; ++c) a.eb[c] = eb.c[c];
-    a.idt = 1.0 / g.dt;
-    a.i2dx = 0.5 / g.dx;
-    a.i2dy = 0.5 / g.dy;
-    a.i2dz = 0.5 / g.dz;
+    for (int c = 0; c < 4; ++c) a.src[c] = (bx.box && bx.clear) ? (real*)L.src[c] : nullptr;
+    if (!g.space_charge) a.src[3] = nullptr;
+    a.idt = (real)(1.0 / g.dt);
+    a.i2dx = (real)(0.5 / g.dx);
+    a.i2dy = (real)(0.5 / g.dy);
+    a.i2dz = (real)(0.5 / g.dz);
     a.kchunk = 16;
+    a.kp = bx.kp;
+    a.box = bx.box;
+    a.box_reset = bx.box_reset;
     const dim3 blk(32, 8);
     const dim3 grd((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, (g.nz - 2 + a.kchunk - 1) / a.kchunk);
     k_emit<real><<<grd, blk, 0, st>>>(a, g);
@@ -386,7 +417,9 @@ template cudaError_t launch_stencil<float>(const FieldLevels<float>&, const Geom
 template cudaError_t launch_stencil<double>(const FieldLevels<double>&, const Geom&, const StencilCoef&, int, cudaStream_t);
 template cudaError_t launch_mur<float>(const FieldLevels<float>&, const Geom&, int, int, cudaStream_t);
 template cudaError_t launch_mur<double>(const FieldLevels<double>&, const Geom&, int, int, cudaStream_t);
-template cudaError_t launch_emit<float>(const FieldLevels<float>&, const Fields6<float>&, const Geom&, cudaStream_t);
-template cudaError_t launch_emit<double>(const FieldLevels<double>&, const Fields6<double>&, const Geom&, cudaStream_t);
+template cudaError_t launch_emit<float>(const FieldLevels<float>&, const Fields6<float>&, const Geom&, const EmitBox&,
+                                        cudaStream_t);
+template cudaError_t launch_emit<double>(const FieldLevels<double>&, const Fields6<double>&, const Geom&,
+                                         const EmitBox&, cudaStream_t);
 
 }  // namespace mithra

@@ -30,8 +30,16 @@ cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const Sten
                            cudaStream_t st);
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, cudaStream_t st);
+// Region of one E/B emission: box == null emits the whole interior and clears nothing.
+struct EmitBox {
+    const int* box;      // device: cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit
+    int* box_reset;      // device: box the next push reduces into, reset to empty by the emission
+    int kp;              // plane always emitted in full (< 0: none)
+    bool clear;          // clear the sources inside the box
+};
 template <typename real>
-cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, cudaStream_t st);
+cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, const EmitBox& bx,
+                        cudaStream_t st);
 
 // Particles.
 struct PushConst {
@@ -43,7 +51,7 @@ struct PushConst {
 
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,
-                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc,
+                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, int* box_out,
                         cudaStream_t st);
 
 template <typename real>

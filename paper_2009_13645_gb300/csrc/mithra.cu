@@ -198,8 +198,37 @@ struct RunT final : mithra_run {
     double* small = nullptr;   // 8 doubles of diagnostic output
     double* rest_buf = nullptr;
     int64_t onaxis_id = 0;
+    int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
 
     int lev(int k) const { return (base + k) % 3; }
+
+    // Make the box read by the next emission cover every active cell (start, new particles).
+    int full_box(int which)
+    {
+        const int h[6] = {1, 1, 1, g.nx - 3, g.ny - 3, g.nz - 3};
+        CU(cudaMemcpyAsync(box[which], h, sizeof h, cudaMemcpyHostToDevice, stream));
+        CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
+    // E and B of the last step over the whole interior: after a step the ring holds
+    // A^{n+1} at lev(0) and the step's A^n still at lev(2).
+    int emit_full()
+    {
+        if (nstep == 0) return MITHRA_OK;
+        FieldLevels<real> L;
+        for (int c = 0; c < 4; ++c) {
+            L.n0[c] = pot[lev(2)][c];
+            L.n1[c] = pot[lev(0)][c];
+            L.out[c] = nullptr;
+            L.src[c] = src[c];
+        }
+        Fields6<real> E6;
+        for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
+        EmitBox bx{nullptr, nullptr, -1, false};
+        CU(launch_emit<real>(L, E6, g, bx, stream));
+        return MITHRA_OK;
+    }
 
     int alloc_all()
     {
@@ -246,6 +275,10 @@ struct RunT final : mithra_run {
         small = (double*)mem.get(8 * 8);
         if (!ring || !phase_cs || !partial || !small) return fail(MITHRA_ENOMEM, "device allocation failed (diagnostics)");
         CU(cudaMemsetAsync(ring, 0, (size_t)M * 4 * plane * 8, stream));
+        for (int b = 0; b < 2; ++b)
+            if (!(box[b] = (int*)mem.get(6 * sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (box)");
+        int rc = full_box(nstep % 2);
+        if (rc) return rc;
         return grow_series(1024);
     }
 
@@ -312,7 +345,6 @@ struct RunT final : mithra_run {
     {
         int rc = grow_series(nstep + nsteps);
         if (rc) return rc;
-        const size_t cell = (size_t)g.ncell * sizeof(real);
         const int ncomp = g.space_charge ? 4 : 3;
         Fields6<real> E6;
         for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
@@ -325,12 +357,11 @@ struct RunT final : mithra_run {
             }
             FieldLevels<real> L = levels();
             cudaEvent_t e0 = nullptr;
+            // E/B where the particles are (and on the power plane); clears the previous sources
+            const EmitBox bx{box[n % 2], box[(n + 1) % 2], (int)d.kp, true};
             pbeg(MITHRA_K_EMIT, &e0);
-            CU(launch_emit<real>(L, E6, g, stream));
+            CU(launch_emit<real>(L, E6, g, bx, stream));
             pend(MITHRA_K_EMIT, e0);
-            pbeg(MITHRA_K_CLEAR, &e0);
-            for (int c = 0; c < ncomp; ++c) CU(cudaMemsetAsync(src[c], 0, cell, stream));
-            pend(MITHRA_K_CLEAR, e0);
             PushConst pc;
             pc.t_half = d.T0 + ((double)n + 0.5) * d.dt;
             pc.qJ[0] = d.q / (d.dy * d.dz * d.dt);
@@ -341,7 +372,7 @@ struct RunT final : mithra_run {
             pc.cdtb[1] = kC * d.dtb / d.dy;
             pc.cdtb[2] = kC * d.dtb / d.dz;
             pbeg(MITHRA_K_PUSH, &e0);
-            CU(launch_push<real>(P, np, g, ef, E6, S4, pc, stream));
+            CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
             pend(MITHRA_K_PUSH, e0);
             pbeg(MITHRA_K_STENCIL, &e0);
             CU(launch_stencil<real>(L, g, cf, ncomp, stream));
@@ -382,6 +413,10 @@ struct RunT final : mithra_run {
     {
         if (which < 0 || which > 13 || level < 0 || level > 1) return fail(MITHRA_EINVAL, "fields: bad index/level");
         if (cap < (size_t)g.ncell) return fail(MITHRA_ERANGE, "fields: buffer too small");
+        if (which >= 8) {
+            const int rc = emit_full();
+            if (rc) return rc;
+        }
         std::vector<real> h((size_t)g.ncell);
         CU(cudaMemcpyAsync(h.data(), field_ptr(which, level), (size_t)g.ncell * sizeof(real), cudaMemcpyDeviceToHost,
                            stream));
@@ -429,7 +464,7 @@ struct RunT final : mithra_run {
         CU(cudaMemcpyAsync(rest_buf, in, (size_t)np * 6 * 8, cudaMemcpyHostToDevice, stream));
         CU(launch_set_rest<real>(rest_buf, np, P, g, stream));
         CU(cudaStreamSynchronize(stream));
-        return MITHRA_OK;
+        return full_box(nstep % 2);
     }
 
     int diag(double* fe, double* b3) override
@@ -437,7 +472,11 @@ struct RunT final : mithra_run {
         Fields6<real> E6;
         for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
         double h[4] = {0, 0, 0, 0};
-        if (fe) CU(launch_energy<real>(E6, g, partial, npartial, small, stream));
+        if (fe) {
+            const int rc = emit_full();
+            if (rc) return rc;
+            CU(launch_energy<real>(E6, g, partial, npartial, small, stream));
+        }
         if (b3) CU(launch_bunching<real>(P, np, g, d.kb, partial + npartial, npartial, small + 4, stream));
         CU(cudaMemcpyAsync(h, small, 8, cudaMemcpyDeviceToHost, stream));
         double hb[3] = {0, 0, 0};

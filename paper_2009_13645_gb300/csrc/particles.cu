@@ -75,108 +75,153 @@ __device__ __forceinline__ void zigzag(const real A[3], const real B[3], const i
     deposit_piece(R, B, c2, base, src, g, pc);
 }
 
+// Block-wide min/max of the cells this block deposited into (or will gather from next step),
+// merged into box_out with one atomic per bound and block.
+__device__ __forceinline__ void box_merge(int lo[3], int hi[3], int* box_out)
+{
+    __shared__ int sh[6][4];   // 128 threads = 4 warps
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int a = __reduce_min_sync(0xffffffffu, lo[d]);
+        const int b = __reduce_max_sync(0xffffffffu, hi[d]);
+        if (lane == 0) {
+            sh[d][w] = a;
+            sh[3 + d][w] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int q = threadIdx.x;
+        int v = sh[q][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = q < 3 ? min(v, sh[q][k]) : max(v, sh[q][k]);
+        if (q < 3) {
+            if (v != 0x7fffffff) atomicMin(box_out + q, v);
+        } else if (v != (int)0x80000000) {
+            atomicMax(box_out + q, v);
+        }
+    }
+}
+
 template <typename real>
 __global__ void __launch_bounds__(128) k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb,
-                                              Fields4<real> src, PushConst pc)
+                                              Fields4<real> src, PushConst pc, int* box_out)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    int ci[3] = {P.ix[p], P.iy[p], P.iz[p]};
-    real f[3] = {P.fx[p], P.fy[p], P.fz[p]};
-    double u[3] = {P.ux[p], P.uy[p], P.uz[p]};
-    for (int m = 0; m < g.substeps; ++m) {
-        const double t = pc.t_half + (double)m * g.dtb;
-        const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
-        const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
-        const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
-        double E[3], B[3];
-        external_field(ef, x, y, z, t, E, B);
-        const bool a1 = active_cell(ci[0], ci[1], ci[2], g);
-        if (a1) {
-            const real wx[2] = {(real)1 - f[0], f[0]};
-            const real wy[2] = {(real)1 - f[1], f[1]};
-            const real wz[2] = {(real)1 - f[2], f[2]};
-            real s[6] = {0, 0, 0, 0, 0, 0};
-            const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
+    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff};
+    int hi[3] = {(int)0x80000000, (int)0x80000000, (int)0x80000000};
+    if (p < np) {
+        int ci[3] = {P.ix[p], P.iy[p], P.iz[p]};
+        real f[3] = {P.fx[p], P.fy[p], P.fz[p]};
+        double u[3] = {P.ux[p], P.uy[p], P.uz[p]};
+        for (int m = 0; m < g.substeps; ++m) {
+            const double t = pc.t_half + (double)m * g.dtb;
+            const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
+            const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
+            const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
+            double E[3], B[3];
+            external_field(ef, x, y, z, t, E, B);
+            const bool a1 = active_cell(ci[0], ci[1], ci[2], g);
+            if (a1) {
+                const real wx[2] = {(real)1 - f[0], f[0]};
+                const real wy[2] = {(real)1 - f[1], f[1]};
+                const real wz[2] = {(real)1 - f[2], f[2]};
+                real s[6] = {0, 0, 0, 0, 0, 0};
+                const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
 #pragma unroll
-            for (int K = 0; K < 2; ++K)
+                for (int K = 0; K < 2; ++K)
 #pragma unroll
-                for (int J = 0; J < 2; ++J)
+                    for (int J = 0; J < 2; ++J)
 #pragma unroll
-                    for (int I = 0; I < 2; ++I) {
-                        const real w = wx[I] * wy[J] * wz[K];
-                        const int64_t id = o + K * g.sz + J * g.sy + I;
+                        for (int I = 0; I < 2; ++I) {
+                            const real w = wx[I] * wy[J] * wz[K];
+                            const int64_t id = o + K * g.sz + J * g.sy + I;
 #pragma unroll
-                        for (int c = 0; c < 6; ++c) s[c] += w * __ldg(eb.c[c] + id);
-                    }
+                            for (int c = 0; c < 6; ++c) s[c] += w * __ldg(eb.c[c] + id);
+                        }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                E[c] += (double)s[c];
-                B[c] += (double)s[3 + c];
-            }
-        }
-        boris(u, E, B, g.dtb);
-        const double ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        real b[3];
-        int nc[3];
-        real nf[3];
-#pragma unroll
-        for (int l = 0; l < 3; ++l) {
-            b[l] = f[l] + (real)(pc.cdtb[l] * u[l] * ig);
-            const real fl = floor(b[l]);
-            int c = (int)fl;
-            real o = b[l] - fl;
-            if (o >= (real)1) { o -= (real)1; c += 1; }
-            nc[l] = ci[l] + c;
-            nf[l] = o;
-        }
-        if (a1 && active_cell(nc[0], nc[1], nc[2], g)) {
-            real mx = fmax(fabs(b[0] - f[0]), fmax(fabs(b[1] - f[1]), fabs(b[2] - f[2])));
-            if (mx <= (real)1) {
-                zigzag(f, b, ci, src, g, pc);
-            } else {
-                const int ns = (int)ceil((double)mx);
-                real A[3], Bq[3];
-                for (int s = 0; s < ns; ++s) {
-#pragma unroll
-                    for (int l = 0; l < 3; ++l) {
-                        const real dl = b[l] - f[l];
-                        A[l] = (s == 0) ? f[l] : f[l] + dl * ((real)s / (real)ns);
-                        Bq[l] = (s == ns - 1) ? b[l] : f[l] + dl * ((real)(s + 1) / (real)ns);
-                    }
-                    zigzag(A, Bq, ci, src, g, pc);
+                for (int c = 0; c < 3; ++c) {
+                    E[c] += (double)s[c];
+                    B[c] += (double)s[3 + c];
                 }
             }
+            boris(u, E, B, g.dtb);
+            const double ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            real b[3];
+            int nc[3];
+            real nf[3];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                b[l] = f[l] + (real)(pc.cdtb[l] * u[l] * ig);
+                const real fl = floor(b[l]);
+                int c = (int)fl;
+                real o = b[l] - fl;
+                if (o >= (real)1) { o -= (real)1; c += 1; }
+                b[l] = (real)c + o;   // the deposit ends exactly at the stored (cell, offset) point
+                nc[l] = ci[l] + c;
+                nf[l] = o;
+            }
+            if (a1 && active_cell(nc[0], nc[1], nc[2], g)) {
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    lo[l] = min(lo[l], min(ci[l], nc[l]));
+                    hi[l] = max(hi[l], max(ci[l], nc[l]));
+                }
+                real mx = fmax(fabs(b[0] - f[0]), fmax(fabs(b[1] - f[1]), fabs(b[2] - f[2])));
+                if (mx <= (real)1) {
+                    zigzag(f, b, ci, src, g, pc);
+                } else {
+                    const int ns = (int)ceil((double)mx);
+                    real A[3], Bq[3];
+                    for (int s = 0; s < ns; ++s) {
+#pragma unroll
+                        for (int l = 0; l < 3; ++l) {
+                            const real dl = b[l] - f[l];
+                            A[l] = (s == 0) ? f[l] : f[l] + dl * ((real)s / (real)ns);
+                            Bq[l] = (s == ns - 1) ? b[l] : f[l] + dl * ((real)(s + 1) / (real)ns);
+                        }
+                        zigzag(A, Bq, ci, src, g, pc);
+                    }
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                ci[l] = nc[l];
+                f[l] = nf[l];
+            }
         }
+        if (active_cell(ci[0], ci[1], ci[2], g)) {
 #pragma unroll
-        for (int l = 0; l < 3; ++l) {
-            ci[l] = nc[l];
-            f[l] = nf[l];
+            for (int l = 0; l < 3; ++l) {
+                lo[l] = min(lo[l], ci[l]);
+                hi[l] = max(hi[l], ci[l]);
+            }
+            if (g.space_charge) {
+                const real wx[2] = {(real)1 - f[0], f[0]};
+                const real wy[2] = {(real)1 - f[1], f[1]};
+                const real wz[2] = {(real)1 - f[2], f[2]};
+                const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
+                const real q = (real)pc.qrho;
+#pragma unroll
+                for (int K = 0; K < 2; ++K)
+#pragma unroll
+                    for (int J = 0; J < 2; ++J)
+#pragma unroll
+                        for (int I = 0; I < 2; ++I)
+                            atomicAdd(src.c[3] + o + K * g.sz + J * g.sy + I, q * wx[I] * wy[J] * wz[K]);
+            }
         }
+        P.ix[p] = ci[0];
+        P.iy[p] = ci[1];
+        P.iz[p] = ci[2];
+        P.fx[p] = f[0];
+        P.fy[p] = f[1];
+        P.fz[p] = f[2];
+        P.ux[p] = u[0];
+        P.uy[p] = u[1];
+        P.uz[p] = u[2];
     }
-    if (g.space_charge && active_cell(ci[0], ci[1], ci[2], g)) {
-        const real wx[2] = {(real)1 - f[0], f[0]};
-        const real wy[2] = {(real)1 - f[1], f[1]};
-        const real wz[2] = {(real)1 - f[2], f[2]};
-        const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
-        const real q = (real)pc.qrho;
-#pragma unroll
-        for (int K = 0; K < 2; ++K)
-#pragma unroll
-            for (int J = 0; J < 2; ++J)
-#pragma unroll
-                for (int I = 0; I < 2; ++I)
-                    atomicAdd(src.c[3] + o + K * g.sz + J * g.sy + I, q * wx[I] * wy[J] * wz[K]);
-    }
-    P.ix[p] = ci[0];
-    P.iy[p] = ci[1];
-    P.iz[p] = ci[2];
-    P.fx[p] = f[0];
-    P.fy[p] = f[1];
-    P.fz[p] = f[2];
-    P.ux[p] = u[0];
-    P.uy[p] = u[1];
-    P.uz[p] = u[2];
+    box_merge(lo, hi, box_out);
 }
 
 // Lab-frame macro-particles (x, y, z relative to the bunch reference at t' = 0, gamma*beta) to
@@ -239,10 +284,11 @@ static inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1)
 
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,
-                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, cudaStream_t st)
+                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, int* box_out,
+                        cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    k_push<real><<<nblocks(np, 128), 128, 0, st>>>(P, np, g, ef, eb, src, pc);
+    k_push<real><<<nblocks(np, 128), 128, 0, st>>>(P, np, g, ef, eb, src, pc, box_out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -277,7 +323,7 @@ cudaError_t launch_get_rest(const Particles<real>& P, int64_t np, const Geom& g,
 
 #define MITHRA_INST(real)                                                                                              \
     template cudaError_t launch_push<real>(const Particles<real>&, int64_t, const Geom&, const ExtField&,             \
-                                           const Fields6<real>&, const Fields4<real>&, const PushConst&,             \
+                                           const Fields6<real>&, const Fields4<real>&, const PushConst&, int*,       \
                                            cudaStream_t);                                                              \
     template cudaError_t launch_boost<real>(const double*, int64_t, const Particles<real>&, const Geom&,              \
                                             const ExtField&, double, cudaStream_t);                                   \
