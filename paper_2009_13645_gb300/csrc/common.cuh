@@ -142,6 +142,60 @@ __host__ __device__ inline void external_field(const ExtField& f, double x, doub
     B[2] = Bp[2];
 }
 
+// sin and cos of a small angle |d| <= 1 in FP64 from their Taylor series (terms through d^19 /
+// d^20; the first omitted term is below 1e-19 for |d| <= 1).
+__host__ __device__ inline void sincos_small(double d, double* s, double* c)
+{
+    const double x = d * d;
+    double ps = 1.0 / 121645100408832000.0;                  // 1/19!
+    ps = fma(ps, -x, 1.0 / 355687428096000.0);               // 1/17!
+    ps = fma(ps, -x, 1.0 / 1307674368000.0);                 // 1/15!
+    ps = fma(ps, -x, 1.0 / 6227020800.0);                    // 1/13!
+    ps = fma(ps, -x, 1.0 / 39916800.0);                      // 1/11!
+    ps = fma(ps, -x, 1.0 / 362880.0);                        // 1/9!
+    ps = fma(ps, -x, 1.0 / 5040.0);                          // 1/7!
+    ps = fma(ps, -x, 1.0 / 120.0);                           // 1/5!
+    ps = fma(ps, -x, 1.0 / 6.0);                             // 1/3!
+    ps = fma(ps, -x, 1.0);
+    *s = d * ps;
+    double pc = 1.0 / 2432902008176640000.0;                 // 1/20!
+    pc = fma(pc, -x, 1.0 / 6402373705728000.0);              // 1/18!
+    pc = fma(pc, -x, 1.0 / 20922789888000.0);                // 1/16!
+    pc = fma(pc, -x, 1.0 / 87178291200.0);                   // 1/14!
+    pc = fma(pc, -x, 1.0 / 479001600.0);                     // 1/12!
+    pc = fma(pc, -x, 1.0 / 3628800.0);                       // 1/10!
+    pc = fma(pc, -x, 1.0 / 40320.0);                         // 1/8!
+    pc = fma(pc, -x, 1.0 / 720.0);                           // 1/6!
+    pc = fma(pc, -x, 1.0 / 24.0);                            // 1/4!
+    pc = fma(pc, -x, 0.5);                                   // 1/2!
+    *c = fma(pc, -x, 1.0);
+}
+
+// cosh and sinh of |x| <= 0.5 in FP64 from their Taylor series (through x^16 / x^17).
+__host__ __device__ inline void coshsinh_small(double x, double* ch, double* sh)
+{
+    const double y = x * x;
+    double pc = 1.0 / 20922789888000.0;                      // 1/16!
+    pc = fma(pc, y, 1.0 / 87178291200.0);
+    pc = fma(pc, y, 1.0 / 479001600.0);
+    pc = fma(pc, y, 1.0 / 3628800.0);
+    pc = fma(pc, y, 1.0 / 40320.0);
+    pc = fma(pc, y, 1.0 / 720.0);
+    pc = fma(pc, y, 1.0 / 24.0);
+    pc = fma(pc, y, 0.5);
+    *ch = fma(pc, y, 1.0);
+    double ps = 1.0 / 355687428096000.0;                     // 1/17!
+    ps = fma(ps, y, 1.0 / 1307674368000.0);
+    ps = fma(ps, y, 1.0 / 6227020800.0);
+    ps = fma(ps, y, 1.0 / 39916800.0);
+    ps = fma(ps, y, 1.0 / 362880.0);
+    ps = fma(ps, y, 1.0 / 5040.0);
+    ps = fma(ps, y, 1.0 / 120.0);
+    ps = fma(ps, y, 1.0 / 6.0);
+    ps = fma(ps, y, 1.0);
+    *sh = x * ps;
+}
+
 // Boris rotation of the normalised momentum u of an electron (Eq. BorisScheme), FP64.
 __host__ __device__ inline void boris(double u[3], const double E[3], const double B[3], double dtb)
 {
@@ -152,6 +206,22 @@ __host__ __device__ inline void boris(double u[3], const double E[3], const doub
     const double t2y = t1y + a * (t1z * B[0] - t1x * B[2]);
     const double t2z = t1z + a * (t1x * B[1] - t1y * B[0]);
     const double s = 2.0 * a / (1.0 + a * a * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+    u[0] = t1x + s * (t2y * B[2] - t2z * B[1]) - h * E[0];
+    u[1] = t1y + s * (t2z * B[0] - t2x * B[2]) - h * E[1];
+    u[2] = t1z + s * (t2x * B[1] - t2y * B[0]) - h * E[2];
+}
+
+// The same Boris rotation in FP32 (Eq. BorisScheme); used by the FP32-mixed push, which adds
+// the resulting increment to the FP64 momentum.
+__host__ __device__ inline void boris_f32(float u[3], const float E[3], const float B[3], float dtb)
+{
+    const float h = (float)(kQe / (2.0 * kMe * kC)) * dtb;
+    const float t1x = u[0] - h * E[0], t1y = u[1] - h * E[1], t1z = u[2] - h * E[2];
+    const float a = -(float)(kQe / (2.0 * kMe)) * dtb / sqrtf(1.0f + t1x * t1x + t1y * t1y + t1z * t1z);
+    const float t2x = t1x + a * (t1y * B[2] - t1z * B[1]);
+    const float t2y = t1y + a * (t1z * B[0] - t1x * B[2]);
+    const float t2z = t1z + a * (t1x * B[1] - t1y * B[0]);
+    const float s = 2.0f * a / (1.0f + a * a * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
     u[0] = t1x + s * (t2y * B[2] - t2z * B[1]) - h * E[0];
     u[1] = t1y + s * (t2z * B[0] - t2x * B[2]) - h * E[1];
     u[2] = t1z + s * (t2x * B[1] - t2y * B[0]) - h * E[2];

@@ -47,7 +47,16 @@ struct PushConst {
     double qJ[3];         // q / (D_m D_n dt): current density per unit displacement (cells) along each axis
     double qrho;          // q / (dx dy dz)
     double cdtb[3];       // c dt_b / D_l
+    // static undulator: per-step table of (sin, cos) of k_u (zeta - offset) at every z node plane
+    // (one table per planar field; null: evaluate directly)
+    const double2* ptab[2];
+    double Z0;            // lab coordinate zeta of node plane 0 at t_half: gamma0 (z0 + beta0 c t_half)
+    double kz;            // gamma0 dz: zeta per cell along z
+    double zstep;         // gamma0 beta0 c dt_b: zeta per sub-step
 };
+
+cudaError_t launch_phase_table(const ExtField& ef, double Z0, double kz, int nz, double2* t0, double2* t1,
+                               cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,

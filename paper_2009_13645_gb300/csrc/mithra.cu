@@ -199,6 +199,7 @@ struct RunT final : mithra_run {
     double* rest_buf = nullptr;
     int64_t onaxis_id = 0;
     int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
+    double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables (one per planar field)
 
     int lev(int k) const { return (base + k) % 3; }
 
@@ -277,6 +278,11 @@ struct RunT final : mithra_run {
         CU(cudaMemsetAsync(ring, 0, (size_t)M * 4 * plane * 8, stream));
         for (int b = 0; b < 2; ++b)
             if (!(box[b] = (int*)mem.get(6 * sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (box)");
+        if (ef.kind == 0 || ef.kind == 1) {
+            for (int b = 0; b < (ef.kind == 1 ? 2 : 1); ++b)
+                if (!(ptab[b] = (double2*)mem.get((size_t)g.nz * sizeof(double2))))
+                    return fail(MITHRA_ENOMEM, "device allocation failed (phase table)");
+        }
         int rc = full_box(nstep % 2);
         if (rc) return rc;
         return grow_series(1024);
@@ -371,7 +377,13 @@ struct RunT final : mithra_run {
             pc.cdtb[0] = kC * d.dtb / d.dx;
             pc.cdtb[1] = kC * d.dtb / d.dy;
             pc.cdtb[2] = kC * d.dtb / d.dz;
+            pc.ptab[0] = ptab[0];
+            pc.ptab[1] = ptab[1];
+            pc.Z0 = d.g0 * (d.z0 + d.b0 * kC * pc.t_half);
+            pc.kz = d.g0 * d.dz;
+            pc.zstep = d.g0 * d.b0 * kC * d.dtb;
             pbeg(MITHRA_K_PUSH, &e0);
+            if (ptab[0]) CU(launch_phase_table(ef, pc.Z0, pc.kz, g.nz, ptab[0], ptab[1], stream));
             CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
             pend(MITHRA_K_PUSH, e0);
             pbeg(MITHRA_K_STENCIL, &e0);

@@ -3,10 +3,142 @@
 // field in FP64, gathers the self-field with linear weights (Eq. fieldInterpolation), advances
 // the momentum with the Boris scheme (Eq. BorisScheme, FP64) and deposits the Umeda zigzag
 // current and the linear-weight charge (Sec. "Current Deposition") with atomics.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace mithra {
+
+// Static undulator field at a particle with the phase of every planar field taken from the
+// step's table (entry of the particle's z cell, in FP64) and rotated by the small angle of the
+// offset within the cell and of the sub-step; cosh / sinh of the small transverse argument from
+// their series.  Same fields as external_field(), evaluated with fewer FP64 operations.
+__device__ __forceinline__ void static_field_fast(const ExtField& f, const PushConst& pc, int iz, double fz, int m,
+                                                  double x, double y, double E[3], double B[3])
+{
+    double Bp[3] = {0.0, 0.0, 0.0};
+    const double dzl = fma(pc.kz, fz, (double)m * pc.zstep);   // zeta beyond the cell's node plane
+    const double zn = fma(pc.kz, (double)iz, pc.Z0);           // zeta of the node plane
+    const int nplanar = f.kind == 1 ? 2 : 1;
+    for (int j = 0; j < nplanar; ++j) {
+        const double c = j ? -f.spol : f.cpol, s = j ? f.cpol : f.spol;
+        const double u = (zn - (j ? f.qlam : 0.0)) + dzl;
+        double sn, cs;
+        if (u >= 0.0 && u <= f.Lu) {
+            const double d = f.ku * dzl;
+            if (fabs(d) <= 1.0) {
+                const double2 t = __ldg(pc.ptab[j] + iz);
+                double sd, cd;
+                sincos_small(d, &sd, &cd);
+                sn = fma(t.x, cd, t.y * sd);
+                cs = fma(t.y, cd, -t.x * sd);
+            } else {
+                sincos(f.ku * u, &sn, &cs);
+            }
+        } else {
+            const double kd = f.ku * ((u < 0.0) ? u : (u - f.Lu));
+            const double g = exp(-0.5 * kd * kd);
+            sn = kd * g;
+            cs = g;
+        }
+        const double ky = f.ku * (c * y - s * x);
+        double ch, sh;
+        if (fabs(ky) <= 0.5) {
+            coshsinh_small(ky, &ch, &sh);
+        } else {
+            ch = cosh(ky);
+            sh = sinh(ky);
+        }
+        const double Bt = f.B0 * ch * sn;
+        Bp[0] -= Bt * s;
+        Bp[1] += Bt * c;
+        Bp[2] += f.B0 * sh * cs;
+    }
+    // a purely magnetic lab field seen from the frame moving with beta0 along z
+    const double gbc = f.g0 * f.b0 * kC;
+    E[0] = -gbc * Bp[1];
+    E[1] = gbc * Bp[0];
+    E[2] = 0.0;
+    B[0] = f.g0 * Bp[0];
+    B[1] = f.g0 * Bp[1];
+    B[2] = Bp[2];
+}
+
+// FP32-mixed variant: the lab coordinate of the particle (the undulator phase) and the
+// Lorentz transform stay in FP64; the field shape evaluated from that phase - the rotation of
+// the tabulated sin/cos by the sub-cell angle (< 1 rad) and cosh/sinh of k_u y - is computed in
+// FP32, the precision of the fields it is added to.
+__device__ __forceinline__ void static_field_mixed(const ExtField& f, const PushConst& pc, int iz, float fz, int m,
+                                                   float x, float y, double E[3], double B[3])
+{
+    float Bp[3] = {0.f, 0.f, 0.f};
+    const double dzl = fma(pc.kz, (double)fz, (double)m * pc.zstep);
+    const double zn = fma(pc.kz, (double)iz, pc.Z0);
+    const int nplanar = f.kind == 1 ? 2 : 1;
+    const float ku = (float)f.ku, B0 = (float)f.B0;
+    for (int j = 0; j < nplanar; ++j) {
+        const float c = j ? -(float)f.spol : (float)f.cpol, s = j ? (float)f.cpol : (float)f.spol;
+        const double u = (zn - (j ? f.qlam : 0.0)) + dzl;
+        float sn, cs;
+        const double d = f.ku * dzl;
+        if (u >= 0.0 && u <= f.Lu && fabs(d) <= 1.0) {
+            const double2 t = __ldg(pc.ptab[j] + iz);
+            float sd, cd;
+            sincosf((float)d, &sd, &cd);
+            const float ts = (float)t.x, tc = (float)t.y;
+            sn = fmaf(ts, cd, tc * sd);
+            cs = fmaf(tc, cd, -ts * sd);
+        } else {
+            double sd, cd;
+            if (u >= 0.0 && u <= f.Lu) {
+                sincos(f.ku * u, &sd, &cd);
+            } else {
+                const double kd = f.ku * ((u < 0.0) ? u : (u - f.Lu));
+                const double g = exp(-0.5 * kd * kd);
+                sd = kd * g;
+                cd = g;
+            }
+            sn = (float)sd;
+            cs = (float)cd;
+        }
+        const float ky = ku * (c * y - s * x);
+        const float ch = coshf(ky), sh = sinhf(ky);
+        const float Bt = B0 * ch * sn;
+        Bp[0] -= Bt * s;
+        Bp[1] += Bt * c;
+        Bp[2] += B0 * sh * cs;
+    }
+    const double gbc = f.g0 * f.b0 * kC;
+    E[0] = -gbc * (double)Bp[1];
+    E[1] = gbc * (double)Bp[0];
+    E[2] = 0.0;
+    B[0] = f.g0 * (double)Bp[0];
+    B[1] = f.g0 * (double)Bp[1];
+    B[2] = (double)Bp[2];
+}
+
+__global__ void k_phase_table(ExtField f, double Z0, double kz, int nz, double2* t0, double2* t1)
+{
+    const int iz = blockIdx.x * blockDim.x + threadIdx.x;
+    if (iz >= nz) return;
+    const double zn = fma(kz, (double)iz, Z0);
+    double s, c;
+    sincos(f.ku * zn, &s, &c);
+    t0[iz] = make_double2(s, c);
+    if (t1) {
+        sincos(f.ku * (zn - f.qlam), &s, &c);
+        t1[iz] = make_double2(s, c);
+    }
+}
+
+cudaError_t launch_phase_table(const ExtField& ef, double Z0, double kz, int nz, double2* t0, double2* t1,
+                               cudaStream_t st)
+{
+    k_phase_table<<<(nz + 127) / 128, 128, 0, st>>>(ef, Z0, kz, nz, t0, t1);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 __device__ __forceinline__ bool active_cell(int i, int j, int k, const Geom& g)
 {
@@ -115,18 +247,30 @@ __global__ void __launch_bounds__(128) k_push(Particles<real> P, int64_t np, Geo
         real f[3] = {P.fx[p], P.fy[p], P.fz[p]};
         double u[3] = {P.ux[p], P.uy[p], P.uz[p]};
         for (int m = 0; m < g.substeps; ++m) {
-            const double t = pc.t_half + (double)m * g.dtb;
-            const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
-            const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
-            const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
             double E[3], B[3];
-            external_field(ef, x, y, z, t, E, B);
+            if (pc.ptab[0] && ci[2] >= 0 && ci[2] < g.nz) {
+                if constexpr (std::is_same<real, float>::value) {
+                    const float x = (float)g.x0 + ((float)ci[0] + f[0]) * (float)g.dx;
+                    const float y = (float)g.y0 + ((float)ci[1] + f[1]) * (float)g.dy;
+                    static_field_mixed(ef, pc, ci[2], f[2], m, x, y, E, B);
+                } else {
+                    const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
+                    const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
+                    static_field_fast(ef, pc, ci[2], (double)f[2], m, x, y, E, B);
+                }
+            } else {
+                const double t = pc.t_half + (double)m * g.dtb;
+                const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
+                const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
+                const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
+                external_field(ef, x, y, z, t, E, B);
+            }
             const bool a1 = active_cell(ci[0], ci[1], ci[2], g);
+            real s[6] = {0, 0, 0, 0, 0, 0};
             if (a1) {
                 const real wx[2] = {(real)1 - f[0], f[0]};
                 const real wy[2] = {(real)1 - f[1], f[1]};
                 const real wz[2] = {(real)1 - f[2], f[2]};
-                real s[6] = {0, 0, 0, 0, 0, 0};
                 const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
 #pragma unroll
                 for (int K = 0; K < 2; ++K)
@@ -139,20 +283,34 @@ __global__ void __launch_bounds__(128) k_push(Particles<real> P, int64_t np, Geo
 #pragma unroll
                             for (int c = 0; c < 6; ++c) s[c] += w * __ldg(eb.c[c] + id);
                         }
+            }
+            real ig;
+            if constexpr (std::is_same<real, float>::value) {
+                // Boris rotation in FP32 on the momentum rounded to FP32; its increment is added
+                // to the FP64 momentum, and 1/gamma of the move comes from the FP64 momentum
+                float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
+                const float Et[3] = {(float)E[0] + s[0], (float)E[1] + s[1], (float)E[2] + s[2]};
+                const float Bt[3] = {(float)B[0] + s[3], (float)B[1] + s[4], (float)B[2] + s[5]};
+                const float u0[3] = {uf[0], uf[1], uf[2]};
+                boris_f32(uf, Et, Bt, (float)g.dtb);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) u[l] += (double)(uf[l] - u0[l]);
+                ig = (float)rsqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     E[c] += (double)s[c];
                     B[c] += (double)s[3 + c];
                 }
+                boris(u, E, B, g.dtb);
+                ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             }
-            boris(u, E, B, g.dtb);
-            const double ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             real b[3];
             int nc[3];
             real nf[3];
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
-                b[l] = f[l] + (real)(pc.cdtb[l] * u[l] * ig);
+                b[l] = f[l] + (real)pc.cdtb[l] * ((real)u[l] * ig);
                 const real fl = floor(b[l]);
                 int c = (int)fl;
                 real o = b[l] - fl;
