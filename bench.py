@@ -53,7 +53,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -67,7 +67,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -180,15 +180,55 @@ def run_reference(args):
     return 0
 
 
+def serving_run(m, workloads, all_fp64: bool, n_requests: int, rate_hz: float):
+    """The serving stream: Poisson arrivals, mixed grids, bunches and precision flags."""
+    reqs = workloads.serving_requests(n_requests, rate_hz)
+    if all_fp64:
+        reqs = [(t, workloads.scaled(w, precision=0)) for t, w in reqs]
+    labs = [workloads.lab_bunch(w) for _, w in reqs]
+    m.serve_start(64 << 30, max_active=16, queue_capacity=4 * n_requests, steps_per_chunk=16)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for (arr, w), lab in zip(reqs, labs):
+            d = t0 + arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(m.submit(w, lab))
+        while True:
+            res = [m.poll(t) for t in tickets]
+            if all(d for d, _ in res):
+                break
+            time.sleep(0.005)
+        res = [r for _, r in res]
+        peak = m.serve_stats()["pool_peak"]
+        for t in tickets:
+            m.release(t)
+    finally:
+        m.serve_stop()
+    ok = [r for r in res if r.status == 0]
+    lat = sorted(r.t_done - r.t_submit for r in ok)
+    span = max(r.t_done for r in ok) - min(r.t_submit for r in ok)
+    cells = sum(w.nx * w.ny * w.nz * w.steps for (_, w), r in zip(reqs, res) if r.status == 0)
+    pushes = sum(w.n_particles * w.steps for (_, w), r in zip(reqs, res) if r.status == 0)
+    q = lambda f: lat[min(len(lat) - 1, int(math.ceil(f * len(lat))) - 1)]
+    return {"requests": n_requests, "completed": len(ok), "arrival_rate_hz": rate_hz,
+            "p50_s": q(0.50), "p99_s": q(0.99), "max_s": lat[-1], "makespan_s": span,
+            "cell_updates_per_s": cells / span, "particle_pushes_per_s": pushes / span,
+            "pool_peak_bytes": peak, "precision": "fp64 for every request" if all_fp64 else "50/50 FP32-mixed/FP64"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -332,6 +372,11 @@ def main():
                         "bunching_abs": abs(bg - bo)}
             g.close()
 
+    served = None
+    if not args.no_serving:
+        served = serving_run(m, workloads, False, args.serving_requests, 4.0)
+        served["fp64_path"] = serving_run(m, workloads, True, args.serving_requests, 4.0)
+
     value = ws * cells * K / (ms32 * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": K, "warmup": W,
@@ -352,6 +397,7 @@ def main():
         "e2e": {"value": ws * cells * K / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K, "what": "mithra_create from pinned host particles (H2D), "
                 f"{K} steps, power series + diagnostics to host (D2H)"},
+        "served": served,
         "gpu_launches": launches,
         "clocks": clocks,
         "hbm_bytes": info.get("hbm_bytes"),

@@ -186,6 +186,46 @@ int64_t mithra_kernel_launches(void);
 int mithra_kernel_stats(mithra_t run, int kernel_id, double *total_ms, int64_t *launches);
 const char *mithra_kernel_name(int kernel_id);
 
+/* Serving (continuous batching).  Requests - each one run of its own grid, bunch, undulator,
+   precision and step count - are queued by mithra_submit and admitted first come, first served
+   as soon as their device-memory footprint fits in the serving pool; every admitted request is
+   a run on its own CUDA stream, advanced in chunks of steps by one scheduler thread, so the
+   kernels of concurrent requests overlap on the GPU.  A finished request returns its memory to
+   the pool and its results wait in host memory until mithra_release.  Results do not depend on
+   what else is being served (each run owns its buffers).  Times are seconds on the server's
+   monotonic clock. */
+typedef struct mithra_result {
+    int32_t status;            /* MITHRA_OK, or the request's error (ENOMEM: larger than the pool) */
+    int32_t state;             /* 0 queued, 1 running, 2 done */
+    int64_t steps;             /* steps taken (done) or enqueued so far (running) */
+    double t_submit, t_admit, t_done;
+    double field_energy;       /* J, rest frame, after the last step */
+    double bunching;           /* |<exp(j kb z)>| after the last step */
+    double power_last;         /* lab radiated power at the last step (W) */
+    double power_peak;         /* largest lab radiated power of the series (W) */
+    int64_t hbm_bytes;         /* device bytes the run held */
+    int64_t reserved_bytes;    /* footprint reserved at admission */
+} mithra_result;
+
+/* Start the server on the current device with a pool of hbm_budget_bytes (allocated once, from
+   the installed allocator), at most max_active requests on the device, a queue of at most
+   queue_capacity waiting requests, and steps_per_chunk steps enqueued per request at a time. */
+int mithra_serve_start(size_t hbm_budget_bytes, int max_active, int queue_capacity, int steps_per_chunk);
+/* Queue one request (inputs copied; never blocks).  EAGAIN when the queue is full, EINVAL as
+   mithra_create, and when no server is running. */
+int mithra_submit(const mithra_grid *grid, const mithra_undulator *und, const mithra_bunch *bunch, int64_t nsteps,
+                  uint64_t *ticket);
+/* State and scalar results of a request; done = 1 once it has finished.  ENOTFOUND: unknown ticket. */
+int mithra_poll(uint64_t ticket, int *done, mithra_result *out);
+/* Radiated-power series of a finished request (as mithra_radiated_power).  EAGAIN if not finished. */
+int mithra_result_series(uint64_t ticket, double *p_lab, double *t_lab, size_t cap, size_t *n_out);
+/* Forget a finished request and its results. */
+int mithra_release(uint64_t ticket);
+/* stats = {completed, active, queued, reserved bytes, pool bytes in use, pool peak bytes}. */
+int mithra_serve_stats(int64_t stats[6]);
+/* Stop the scheduler (unfinished requests end with ETIMEDOUT) and free the pool. */
+int mithra_serve_stop(void);
+
 /* Field energy of caller-supplied E and B arrays, computed without allocating any device memory.
    No counterpart in the paper: it serves callers that cannot call cudaMalloc at that moment
    (a pool that is already fully carved up, a thread that must not take allocator locks, a

@@ -90,6 +90,14 @@ def load(rebuild: bool = False):
     L.mithra_last_error.restype = C.c_char_p
     L.mithra_version.restype = C.c_int
     L.mithra_kernel_launches.restype = C.c_int64
+    L.mithra_serve_start.argtypes = [C.c_size_t, C.c_int, C.c_int, C.c_int]
+    L.mithra_submit.argtypes = [C.POINTER(Grid), C.POINTER(Undulator), C.POINTER(Bunch), C.c_int64,
+                                C.POINTER(C.c_uint64)]
+    L.mithra_poll.argtypes = [C.c_uint64, C.POINTER(C.c_int), C.c_void_p]
+    L.mithra_result_series.argtypes = [C.c_uint64, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.mithra_release.argtypes = [C.c_uint64]
+    L.mithra_serve_stats.argtypes = [C.POINTER(C.c_int64)]
+    L.mithra_serve_stop.argtypes = []
     L.mithra_field_energy_noalloc.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int64, C.c_double,
                                               C.c_void_p, C.c_void_p]
     _lib = L
@@ -111,6 +119,64 @@ def mithra_field_energy_noalloc(eb_ptrs, precision: int, n: int, cell_volume: fl
     arr = (C.c_void_p * 6)(*[C.c_void_p(int(p)) for p in eb_ptrs])
     _check(L.mithra_field_energy_noalloc(arr, int(precision), int(n), float(cell_volume),
                                          C.c_void_p(int(out_ptr)), C.c_void_p(int(stream))))
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("state", C.c_int32), ("steps", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("field_energy", C.c_double), ("bunching", C.c_double), ("power_last", C.c_double),
+                ("power_peak", C.c_double), ("hbm_bytes", C.c_int64), ("reserved_bytes", C.c_int64)]
+
+
+def serve_start(hbm_budget_bytes: int, max_active: int = 8, queue_capacity: int = 256, steps_per_chunk: int = 16):
+    """Start the serving loop on the current device (see include/mithra.h)."""
+    _check(load().mithra_serve_start(C.c_size_t(int(hbm_budget_bytes)), int(max_active), int(queue_capacity),
+                                     int(steps_per_chunk)))
+
+
+def submit(w, lab6=None, nsteps=None, precision=None) -> int:
+    """Queue one run of workload w (lab particles lab6, default: its seeded bunch)."""
+    import workloads
+    L = load()
+    lab6 = workloads.lab_bunch(w) if lab6 is None else lab6
+    b, keep = bunch_from(w, lab6)
+    g, u = grid_from(w, precision), undulator_from(w)
+    t = C.c_uint64()
+    _check(L.mithra_submit(C.byref(g), C.byref(u), C.byref(b), int(w.steps if nsteps is None else nsteps),
+                           C.byref(t)))
+    return t.value
+
+
+def poll(ticket: int):
+    """(done, Result) of a request."""
+    d = C.c_int()
+    r = Result()
+    _check(load().mithra_poll(C.c_uint64(ticket), C.byref(d), C.byref(r)))
+    return bool(d.value), r
+
+
+def result_series(ticket: int):
+    L = load()
+    n = C.c_size_t()
+    _check(L.mithra_result_series(C.c_uint64(ticket), None, None, 0, C.byref(n)))
+    p, t = np.zeros(n.value), np.zeros(n.value)
+    if n.value:
+        _check(L.mithra_result_series(C.c_uint64(ticket), _dp(p), _dp(t), n.value, C.byref(n)))
+    return p, t
+
+
+def release(ticket: int):
+    _check(load().mithra_release(C.c_uint64(ticket)))
+
+
+def serve_stats() -> dict:
+    s = (C.c_int64 * 6)()
+    _check(load().mithra_serve_stats(s))
+    return dict(zip(("completed", "active", "queued", "reserved", "pool_in_use", "pool_peak"), list(s)))
+
+
+def serve_stop():
+    _check(load().mithra_serve_stop())
 
 
 def kernel_launches() -> int:

@@ -1,5 +1,6 @@
 // C ABI of libmithra: run set-up (rest frame, mesh checks, placement), device memory,
 // the per-step launch sequence and the accessors declared in include/mithra.h.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,7 @@
 #include "../../include/mithra.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "run.h"
 
 using namespace mithra;
 
@@ -53,6 +55,14 @@ void mithra::count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_ord
 extern "C" int64_t mithra_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" const char* mithra_last_error(void) { return g_err.c_str(); }
+
+void mithra::get_allocator(mithra_alloc_fn* alloc, mithra_free_fn* free_fn, void** ctx)
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    *alloc = g_alloc.alloc;
+    *free_fn = g_alloc.free_fn;
+    *ctx = g_alloc.ctx;
+}
 int mithra::set_last_error(int code, const char* msg) { return fail(code, msg); }
 extern "C" int mithra_version(void) { return 1; }
 
@@ -640,13 +650,11 @@ int derive(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, cons
 }
 
 template <typename real>
-int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, const mithra_bunch& b, mithra_t* out)
+int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, const mithra_bunch& b,
+             const Allocator& alloc, mithra_t* out)
 {
     RunT<real>* r = new RunT<real>();
-    {
-        std::lock_guard<std::mutex> lk(g_alloc_mu);
-        r->mem.a = g_alloc;
-    }
+    r->mem.a = alloc;
     int rc = derive(gr, dt_lab, u, b, r->d, r->ef);
     if (rc) {
         delete r;
@@ -730,11 +738,10 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
 
 }  // namespace
 
-extern "C" int mithra_create(const mithra_grid* gr, double dt_lab, const mithra_undulator* u, const mithra_bunch* b,
-                             mithra_t* out)
+// Checks of mithra_create that need no device (shared with the serving queue).
+int mithra::validate_request(const mithra_grid* gr, double dt_lab, const mithra_undulator* u, const mithra_bunch* b)
 {
-    if (!gr || !u || !b || !out) return fail(MITHRA_EINVAL, "create: null argument");
-    *out = nullptr;
+    if (!gr || !u || !b) return fail(MITHRA_EINVAL, "create: null argument");
     if (gr->nx < 6 || gr->ny < 6 || gr->nz < 6) return fail(MITHRA_EINVAL, "create: each axis needs >= 6 nodes");
     if ((int64_t)gr->nx * gr->ny * gr->nz >= (int64_t(1) << 31) - 1)
         return fail(MITHRA_EINVAL, "create: more than 2^31 - 2 nodes");
@@ -758,8 +765,54 @@ extern "C" int mithra_create(const mithra_grid* gr, double dt_lab, const mithra_
         for (int64_t i = 0; i < 6 * b->n; ++i)
             if (!std::isfinite(b->lab_particles[i])) return fail(MITHRA_EINVAL, "create: non-finite particle value");
     }
-    if (gr->precision == 0) return create_t<double>(*gr, dt_lab, *u, *b, out);
-    return create_t<float>(*gr, dt_lab, *u, *b, out);
+    return MITHRA_OK;
+}
+
+int mithra::create_with(const mithra_grid* gr, double dt_lab, const mithra_undulator* u, const mithra_bunch* b,
+                        mithra_alloc_fn alloc, mithra_free_fn free_fn, void* ctx, mithra_t* out)
+{
+    if (!out) return fail(MITHRA_EINVAL, "create: null argument");
+    *out = nullptr;
+    const int rc = validate_request(gr, dt_lab, u, b);
+    if (rc) return rc;
+    Allocator a;
+    a.alloc = alloc;
+    a.free_fn = free_fn;
+    a.ctx = ctx;
+    if (gr->precision == 0) return create_t<double>(*gr, dt_lab, *u, *b, a, out);
+    return create_t<float>(*gr, dt_lab, *u, *b, a, out);
+}
+
+extern "C" int mithra_create(const mithra_grid* gr, double dt_lab, const mithra_undulator* u, const mithra_bunch* b,
+                             mithra_t* out)
+{
+    Allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    return mithra::create_with(gr, dt_lab, u, b, a.alloc, a.free_fn, a.ctx, out);
+}
+
+int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, const mithra_bunch* b, int64_t nsteps)
+{
+    auto up = [](int64_t x) { return (x + 255) & ~(int64_t)255; };
+    const int64_t ncell = (int64_t)gr->nx * gr->ny * gr->nz;
+    const int64_t rs = gr->precision == 0 ? 8 : 4;
+    const int64_t n = b->n > 0 ? b->n : 1;
+    int64_t t = 22 * up(ncell * rs);                                          // potentials, sources, E/B
+    t += 2 * (4 * up(n * 4) + 3 * up(n * rs) + 3 * up(n * 8));               // particles and sort copy
+    t += 2 * up(n * 4) + 2 * up((ncell + 1) * 4) + up((ncell / 4096 + 16) * 4);   // sort scratch
+    // the power window M is only known after the rest frame is fixed; bound it by the run's steps
+    const int64_t plane = (int64_t)gr->nx * gr->ny;
+    const int64_t M = std::min<int64_t>(std::max<int64_t>(nsteps, 1), 4096);
+    t += up(M * 4 * plane * 8) + up(2 * M * 8) + 2 * up(4 * 304 * 8) + up(64);
+    int64_t cap = 1024;
+    while (cap < nsteps) cap *= 2;
+    t += 4 * up(cap * 8);                                                     // series (old and new while growing)
+    t += 2 * up(6 * 4) + 2 * up(gr->nz * 16);                                 // boxes, phase tables
+    t += up(n * 48);                                                          // lab particles during the boost
+    return t;
 }
 
 extern "C" int mithra_set_stream(mithra_t r, void* stream)
