@@ -43,95 +43,68 @@ __global__ void k_final(const double* __restrict__ partial, int npartial, int nc
 }
 
 // ---- radiated power -------------------------------------------------------------------
+// One step of the running DFT on the power plane: every plane point adds its new sample of
+// E_x, E_y, B_x, B_y times exp(-j w t_n) to its accumulators and, once the window is full,
+// subtracts the sample of step n - M kept in the ring (the DFT over the last M steps, updated
+// instead of recomputed); the interior points then add Re(Ex By* - Ey Bx*) of their
+// accumulators to a per-block partial.  The on-axis E_x of the step is recorded by one thread.
 template <typename real>
-__global__ void k_power_sample(Fields6<real> eb, Geom g, int kp, double* __restrict__ ring, int slot, double omega_h,
-                               double t_sample, double* __restrict__ phase_cs)
-{
-    const int64_t plane = (int64_t)g.nx * g.ny;
-    const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pl == 0) {
-        double s, c;
-        sincos(omega_h * t_sample, &s, &c);
-        phase_cs[2 * slot] = c;
-        phase_cs[2 * slot + 1] = s;
-    }
-    if (pl >= plane) return;
-    const int64_t id = (int64_t)kp * g.sz + pl;
-    double* r = ring + (int64_t)slot * 4 * plane;
-    r[pl] = (double)eb.c[0][id];
-    r[plane + pl] = (double)eb.c[1][id];
-    r[2 * plane + pl] = (double)eb.c[3][id];
-    r[3 * plane + pl] = (double)eb.c[4][id];
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_power_reduce(const double* __restrict__ ring,
-                                                              const double* __restrict__ phase_cs, int M, Geom g,
-                                                              double* __restrict__ partial)
+__global__ void __launch_bounds__(kRedThreads) k_power_step(Fields6<real> eb, Geom g, PowerStep ps,
+                                                            double* __restrict__ partial)
 {
     __shared__ double sh[32];
     const int64_t plane = (int64_t)g.nx * g.ny;
-    const int64_t nin = (int64_t)(g.nx - 2) * (g.ny - 2);
-    double acc = 0.0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nin; t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = 1 + (int)(t % (g.nx - 2));
-        const int j = 1 + (int)(t / (g.nx - 2));
-        const int64_t pl = (int64_t)j * g.nx + i;
-        double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
-        for (int m = 0; m < M; ++m) {
-            const double c = phase_cs[2 * m], s = phase_cs[2 * m + 1];
-            const double* r = ring + (int64_t)m * 4 * plane + pl;
+    const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double contrib = 0.0;
+    if (pl < plane) {
+        const int64_t id = (int64_t)ps.kp * g.sz + pl;
+        if (id == ps.onaxis_id) *ps.onaxis_out = (double)eb.c[0][id];
+        const double x[4] = {(double)eb.c[0][id], (double)eb.c[1][id], (double)eb.c[3][id], (double)eb.c[4][id]};
+        double* r = ps.ring + (int64_t)ps.slot * 4 * plane + pl;
+        double re[4], im[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const double v = r[q * plane];
-                re[q] += v * c;
-                im[q] -= v * s;
+        for (int q = 0; q < 4; ++q) {
+            double a = ps.acc[(2 * q) * plane + pl], b = ps.acc[(2 * q + 1) * plane + pl];
+            a += x[q] * ps.cn;
+            b -= x[q] * ps.sn;
+            if (ps.full) {
+                const double o = r[q * plane];
+                a -= o * ps.co;
+                b += o * ps.so;
             }
+            ps.acc[(2 * q) * plane + pl] = a;
+            ps.acc[(2 * q + 1) * plane + pl] = b;
+            r[q * plane] = x[q];
+            re[q] = a;
+            im[q] = b;
         }
-        // Re(Ex By* - Ey Bx*) of the unnormalised DFT sums; the (2/M)^2 goes into `scale`
-        acc += (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
+        const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
+        if (ps.emit && i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2)
+            contrib = (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
     }
-    const double tot = block_sum(acc, sh);
+    const double tot = block_sum(contrib, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
 template <typename real>
-cudaError_t power_sample_ex(const Fields6<real>& eb, const Geom& g, int kp, double* ring, int slot, double omega_h,
-                            double t_sample, double* phase_cs, cudaStream_t st)
+cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const PowerStep& ps, double scale,
+                              double* partial, int npartial, double* out, cudaStream_t st)
 {
     const int64_t plane = (int64_t)g.nx * g.ny;
-    k_power_sample<real><<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(eb, g, kp, ring, slot, omega_h, t_sample,
-                                                                         phase_cs);
+    const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
+    if ((int)nb > npartial) return cudaErrorInvalidValue;
+    k_power_step<real><<<nb, kRedThreads, 0, st>>>(eb, g, ps, partial);
     count_launches(1);
+    if (ps.emit) {
+        k_final<<<1, kRedThreads, 0, st>>>(partial, (int)nb, 1, scale, out);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
-template cudaError_t power_sample_ex<float>(const Fields6<float>&, const Geom&, int, double*, int, double, double,
-                                            double*, cudaStream_t);
-template cudaError_t power_sample_ex<double>(const Fields6<double>&, const Geom&, int, double*, int, double, double,
-                                             double*, cudaStream_t);
-
-cudaError_t launch_power_reduce(const double* ring, const double* phase_cs, int M, const Geom& g, double scale,
-                                double* partial, int npartial, double* out, cudaStream_t st)
-{
-    k_power_reduce<<<npartial, kRedThreads, 0, st>>>(ring, phase_cs, M, g, partial);
-    k_final<<<1, kRedThreads, 0, st>>>(partial, npartial, 1, scale, out);
-    count_launches(2);
-    return cudaGetLastError();
-}
-
-// ---- on-axis sample -------------------------------------------------------------------
-template <typename real>
-__global__ void k_onaxis(const real* __restrict__ ex, int64_t id, double* __restrict__ out)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *out = (double)ex[id];
-}
-
-template <typename real>
-cudaError_t launch_onaxis(const Fields6<real>& eb, int64_t id, double* out, cudaStream_t st)
-{
-    k_onaxis<real><<<1, 32, 0, st>>>(eb.c[0], id, out);
-    count_launches(1);
-    return cudaGetLastError();
-}
+template cudaError_t launch_power_step<float>(const Fields6<float>&, const Geom&, const PowerStep&, double, double*,
+                                              int, double*, cudaStream_t);
+template cudaError_t launch_power_step<double>(const Fields6<double>&, const Geom&, const PowerStep&, double, double*,
+                                               int, double*, cudaStream_t);
 
 // ---- field energy ----------------------------------------------------------------------
 template <typename real>
@@ -211,7 +184,6 @@ cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g,
 }
 
 #define MITHRA_INST(real)                                                                                              \
-    template cudaError_t launch_onaxis<real>(const Fields6<real>&, int64_t, double*, cudaStream_t);                    \
     template cudaError_t launch_energy<real>(const Fields6<real>&, const Geom&, double*, int, double*, cudaStream_t); \
     template cudaError_t launch_bunching<real>(const Particles<real>&, int64_t, const Geom&, double, double*, int,    \
                                                double*, cudaStream_t);

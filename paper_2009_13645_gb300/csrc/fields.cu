@@ -406,6 +406,7 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     a.kp = bx.kp;
     a.box = bx.box;
     a.box_reset = bx.box_reset;
+    a.kchunk = bx.box ? 4 : 16;   // short z chunks spread the box over more blocks
     const dim3 blk(32, 8);
     const dim3 grd((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, (g.nz - 2 + a.kchunk - 1) / a.kchunk);
     k_emit<real><<<grd, blk, 0, st>>>(a, g);

@@ -89,13 +89,21 @@ cudaError_t launch_sort(Particles<real>& P, Particles<real>& tmp, int64_t np, co
 size_t sort_scan_partials(int64_t nbins);
 
 // Diagnostics.
+struct PowerStep {
+    int kp;                 // plane index
+    int slot;               // ring slot of step n (the slot of step n - M is the same)
+    int full;               // the ring holds step n - M: subtract it
+    int emit;               // window complete: reduce the power
+    double cn, sn;          // cos, sin of w t_n
+    double co, so;          // cos, sin of w t_{n-M}
+    double* ring;           // M x 4 x plane samples
+    double* acc;            // 8 x plane accumulators (re, im of Ex, Ey, Bx, By)
+    int64_t onaxis_id;
+    double* onaxis_out;
+};
 template <typename real>
-cudaError_t power_sample_ex(const Fields6<real>& eb, const Geom& g, int kp, double* ring, int slot, double omega_h,
-                            double t_sample, double* phase_cs, cudaStream_t st);
-cudaError_t launch_power_reduce(const double* ring, const double* ring_phase_cs, int M, const Geom& g,
-                                double scale, double* partial, int npartial, double* out, cudaStream_t st);
-template <typename real>
-cudaError_t launch_onaxis(const Fields6<real>& eb, int64_t id, double* out, cudaStream_t st);
+cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const PowerStep& ps, double scale,
+                              double* partial, int npartial, double* out, cudaStream_t st);
 template <typename real>
 cudaError_t launch_energy(const Fields6<real>& eb, const Geom& g, double* partial, int npartial, double* out,
                           cudaStream_t st);

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -200,6 +201,7 @@ struct RunT final : mithra_run {
     SortScratch ss{};
     double* ring = nullptr;
     double* phase_cs = nullptr;
+    double* acc = nullptr;      // running DFT accumulators of the power plane
     double* partial = nullptr;
     int npartial = 304;
     double* ser_p = nullptr;
@@ -280,12 +282,16 @@ struct RunT final : mithra_run {
             return fail(MITHRA_ENOMEM, "device allocation failed (sort scratch)");
         const int M = (int)d.M;
         const size_t plane = (size_t)g.nx * g.ny;
+        npartial = std::max<int>(304, (int)((plane + 255) / 256));
         ring = (double*)mem.get((size_t)M * 4 * plane * 8);
         phase_cs = (double*)mem.get((size_t)2 * M * 8);
+        acc = (double*)mem.get((size_t)8 * plane * 8);
         partial = (double*)mem.get((size_t)4 * npartial * 8);   // energy: [0, n); bunching: [n, 3n)
         small = (double*)mem.get(8 * 8);
-        if (!ring || !phase_cs || !partial || !small) return fail(MITHRA_ENOMEM, "device allocation failed (diagnostics)");
+        if (!ring || !phase_cs || !acc || !partial || !small)
+            return fail(MITHRA_ENOMEM, "device allocation failed (diagnostics)");
         CU(cudaMemsetAsync(ring, 0, (size_t)M * 4 * plane * 8, stream));
+        CU(cudaMemsetAsync(acc, 0, (size_t)8 * plane * 8, stream));
         for (int b = 0; b < 2; ++b)
             if (!(box[b] = (int*)mem.get(6 * sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (box)");
         if (ef.kind == 0 || ef.kind == 1) {
@@ -403,16 +409,28 @@ struct RunT final : mithra_run {
             CU(launch_mur<real>(L, g, mur_order, ncomp, stream));
             pend(MITHRA_K_MUR, e0);
             pbeg(MITHRA_K_POWER, &e0);
-            const int M = (int)d.M;
-            const int slot = (int)(n % M);
-            CU(power_sample_ex<real>(E6, g, (int)d.kp, ring, slot, d.omega_h, ((double)n + 0.5) * d.dt, phase_cs,
-                                     stream));
-            if (n + 1 >= M) {
+            {
+                const int M = (int)d.M;
+                PowerStep ps;
+                ps.kp = (int)d.kp;
+                ps.slot = (int)(n % M);
+                ps.full = n >= M ? 1 : 0;
+                ps.emit = n + 1 >= M ? 1 : 0;
+                const double th = d.omega_h * ((double)n + 0.5) * d.dt;
+                const double tho = d.omega_h * ((double)(n - M) + 0.5) * d.dt;
+                ps.cn = std::cos(th);
+                ps.sn = std::sin(th);
+                ps.co = std::cos(tho);
+                ps.so = std::sin(tho);
+                ps.ring = ring;
+                ps.acc = acc;
+                ps.onaxis_id = onaxis_id;
+                ps.onaxis_out = ser_e + n;
                 const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
                 const double scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
-                CU(launch_power_reduce(ring, phase_cs, M, g, scale, partial, npartial, ser_p + n, stream));
+                if (!ring || !acc || !partial) return fail(MITHRA_EINVAL, "power diagnostic buffers missing");
+                CU(launch_power_step<real>(E6, g, ps, scale, partial, npartial, ser_p + n, stream));
             }
-            CU(launch_onaxis<real>(E6, onaxis_id, ser_e + n, stream));
             pend(MITHRA_K_POWER, e0);
             base = (base + 1) % 3;
             ++nstep;

@@ -236,7 +236,7 @@ __device__ __forceinline__ void box_merge(int lo[3], int hi[3], int* box_out)
 }
 
 template <typename real>
-__global__ void __launch_bounds__(128) k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb,
+__global__ void __launch_bounds__(128, sizeof(real) == 4 ? 6 : 5) k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb,
                                               Fields4<real> src, PushConst pc, int* box_out)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
