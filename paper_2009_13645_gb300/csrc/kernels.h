@@ -28,6 +28,16 @@ struct StencilCoef {
 template <typename real>
 cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const StencilCoef& cf, int ncomp,
                            cudaStream_t st);
+// TMA-staged stencil (stencil_tma.cu): tensor maps of the three ring levels and the sources,
+// built once per run; null when the grid's row pitch is not a multiple of 16 bytes.
+struct TmaMaps;
+template <typename real>
+TmaMaps* make_tma_maps(real* const pot[3][4], real* const src[4], const Geom& g);
+void free_tma_maps(TmaMaps* m);
+template <typename real>
+cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], int lev_n, int lev_m, const Geom& g,
+                               const StencilCoef& cf, int ncomp, int* err, cudaStream_t st);
+
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, cudaStream_t st);
 // Region of one E/B emission: box == null emits the whole interior and clears nothing.

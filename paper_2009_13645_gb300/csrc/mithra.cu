@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -212,6 +213,8 @@ struct RunT final : mithra_run {
     int64_t onaxis_id = 0;
     int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
     double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables (one per planar field)
+    TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
+    int* err_word = nullptr;   // set by a kernel whose bounded wait expired
 
     int lev(int k) const { return (base + k) % 3; }
 
@@ -299,6 +302,10 @@ struct RunT final : mithra_run {
                 if (!(ptab[b] = (double2*)mem.get((size_t)g.nz * sizeof(double2))))
                     return fail(MITHRA_ENOMEM, "device allocation failed (phase table)");
         }
+        if (!(err_word = (int*)mem.get(sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (error word)");
+        CU(cudaMemsetAsync(err_word, 0, sizeof(int), stream));
+        const char* no_tma = std::getenv("MITHRA_NO_TMA");
+        if (!(no_tma && no_tma[0] == '1')) tma = make_tma_maps<real>(pot, src, g);
         int rc = full_box(nstep % 2);
         if (rc) return rc;
         return grow_series(1024);
@@ -403,7 +410,12 @@ struct RunT final : mithra_run {
             CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
             pend(MITHRA_K_PUSH, e0);
             pbeg(MITHRA_K_STENCIL, &e0);
-            CU(launch_stencil<real>(L, g, cf, ncomp, stream));
+            if (tma) {
+                real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
+                CU(launch_stencil_tma<real>(tma, outp, lev(1), lev(0), g, cf, ncomp, err_word, stream));
+            } else {
+                CU(launch_stencil<real>(L, g, cf, ncomp, stream));
+            }
             pend(MITHRA_K_STENCIL, e0);
             pbeg(MITHRA_K_MUR, &e0);
             CU(launch_mur<real>(L, g, mur_order, ncomp, stream));
@@ -551,6 +563,9 @@ struct RunT final : mithra_run {
     {
         CU(cudaStreamSynchronize(stream));
         if (prof) prof_collect();
+        int e = 0;
+        CU(cudaMemcpy(&e, err_word, sizeof e, cudaMemcpyDeviceToHost));
+        if (e) return fail(MITHRA_ETIMEDOUT, "a bounded device-side wait expired (TMA copy never completed)");
         return MITHRA_OK;
     }
 
@@ -558,6 +573,8 @@ struct RunT final : mithra_run {
     {
         if (stream) cudaStreamSynchronize(stream);
         prof_collect();
+        free_tma_maps(tma);
+        tma = nullptr;
         for (auto e : ev_free) cudaEventDestroy(e);
         ev_free.clear();
         mem.release_all();

@@ -274,3 +274,35 @@ def test_fullsize_fel_two_steps():
         idx = np.random.default_rng(0).choice(len(po), 20000, replace=False)
         assert np.max(np.abs(pg[idx, :3] - po[idx, :3]) / D) < (1e-9 if precision == 0 else 1e-5)
         g.close()
+
+
+@pytest.mark.parametrize("shape", [(40, 29, 45), (64, 9, 70), (132, 17, 38)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 3e-5)])
+def test_tma_stencil_matches_oracle_and_plain_kernel(shape, precision, tol, monkeypatch):
+    """Row pitches that are multiples of 16 bytes take the TMA-staged stencil; it must match the
+    oracle and the plain z-marching kernel (MITHRA_NO_TMA=1) on tiles with ragged edges."""
+    nx, ny, nz = shape
+    w = vacuum(nx, ny, nz, 1.3e-3, 1.1e-3, 1.0e-3, solver=0, mur_order=2)
+    o = oracle.Run(oracle.params_from(w))
+    runs = {}
+    for tag, env in (("tma", "0"), ("plain", "1")):
+        monkeypatch.setenv("MITHRA_NO_TMA", env)
+        runs[tag] = mithra.Run.from_workload(w, np.zeros((0, 6)), precision=precision)
+    rng = np.random.default_rng(3)
+    for c in range(4):
+        for lev in range(2):
+            a = rng.standard_normal((nz, ny, nx))
+            if precision == 1:
+                a = a.astype(np.float32).astype(np.float64)
+            o.set_field(c, lev, a)
+            for r in runs.values():
+                r.set_field(c, lev, a)
+    o.step(25)
+    for r in runs.values():
+        r.step(25)
+        r.sync()
+    for c in range(4):
+        for lev in range(2):
+            a, b = runs["tma"].field(c, lev), runs["plain"].field(c, lev)
+            assert rel(a, b) <= (1e-14 if precision == 0 else 1e-6)
+            assert rel(a, o.field(c, lev)) < tol
