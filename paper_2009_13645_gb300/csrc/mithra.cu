@@ -212,7 +212,8 @@ struct RunT final : mithra_run {
     double* rest_buf = nullptr;
     int64_t onaxis_id = 0;
     int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
-    double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables (one per planar field)
+    double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables, FP64 path (one per planar field)
+    float2* ptab32[2] = {nullptr, nullptr};  // the same rounded to FP32 with inside flags, FP32-mixed path
     TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
     int* err_word = nullptr;   // set by a kernel whose bounded wait expired
 
@@ -298,9 +299,11 @@ struct RunT final : mithra_run {
         for (int b = 0; b < 2; ++b)
             if (!(box[b] = (int*)mem.get(6 * sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (box)");
         if (ef.kind == 0 || ef.kind == 1) {
-            for (int b = 0; b < (ef.kind == 1 ? 2 : 1); ++b)
-                if (!(ptab[b] = (double2*)mem.get((size_t)g.nz * sizeof(double2))))
-                    return fail(MITHRA_ENOMEM, "device allocation failed (phase table)");
+            for (int b = 0; b < (ef.kind == 1 ? 2 : 1); ++b) {
+                if (sizeof(real) == 8) ptab[b] = (double2*)mem.get((size_t)g.nz * sizeof(double2));
+                else ptab32[b] = (float2*)mem.get((size_t)g.nz * sizeof(float2));
+                if (!ptab[b] && !ptab32[b]) return fail(MITHRA_ENOMEM, "device allocation failed (phase table)");
+            }
         }
         if (!(err_word = (int*)mem.get(sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (error word)");
         CU(cudaMemsetAsync(err_word, 0, sizeof(int), stream));
@@ -402,11 +405,18 @@ struct RunT final : mithra_run {
             pc.cdtb[2] = kC * d.dtb / d.dz;
             pc.ptab[0] = ptab[0];
             pc.ptab[1] = ptab[1];
+            pc.ptab32[0] = ptab32[0];
+            pc.ptab32[1] = ptab32[1];
             pc.Z0 = d.g0 * (d.z0 + d.b0 * kC * pc.t_half);
             pc.kz = d.g0 * d.dz;
             pc.zstep = d.g0 * d.b0 * kC * d.dtb;
+            pc.kdz = (float)(ef.ku * pc.kz);
+            pc.kzs = (float)(ef.ku * pc.zstep);
             pbeg(MITHRA_K_PUSH, &e0);
             if (ptab[0]) CU(launch_phase_table(ef, pc.Z0, pc.kz, g.nz, ptab[0], ptab[1], stream));
+            if (ptab32[0])
+                CU(launch_phase_table32(ef, pc.Z0, pc.kz, pc.kz + (double)g.substeps * pc.zstep, g.nz, ptab32[0],
+                                        ptab32[1], stream));
             CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
             pend(MITHRA_K_PUSH, e0);
             pbeg(MITHRA_K_STENCIL, &e0);

@@ -73,23 +73,21 @@ __device__ __forceinline__ void static_field_mixed(const ExtField& f, const Push
                                                    float x, float y, double E[3], double B[3])
 {
     float Bp[3] = {0.f, 0.f, 0.f};
-    const double dzl = fma(pc.kz, (double)fz, (double)m * pc.zstep);
-    const double zn = fma(pc.kz, (double)iz, pc.Z0);
     const int nplanar = f.kind == 1 ? 2 : 1;
     const float ku = (float)f.ku, B0 = (float)f.B0;
     for (int j = 0; j < nplanar; ++j) {
         const float c = j ? -(float)f.spol : (float)f.cpol, s = j ? (float)f.cpol : (float)f.spol;
-        const double u = (zn - (j ? f.qlam : 0.0)) + dzl;
+        const float2 t = __ldg(pc.ptab32[j] + iz);
         float sn, cs;
-        const double d = f.ku * dzl;
-        if (u >= 0.0 && u <= f.Lu && fabs(d) <= 1.0) {
-            const double2 t = __ldg(pc.ptab[j] + iz);
+        if (!isnan(t.x)) {
+            // the cell lies inside the undulator: rotate the exact phase of its node plane
             float sd, cd;
-            sincosf((float)d, &sd, &cd);
-            const float ts = (float)t.x, tc = (float)t.y;
-            sn = fmaf(ts, cd, tc * sd);
-            cs = fmaf(tc, cd, -ts * sd);
+            sincosf(fmaf(pc.kdz, fz, pc.kzs * (float)m), &sd, &cd);
+            sn = fmaf(t.x, cd, t.y * sd);
+            cs = fmaf(t.y, cd, -t.x * sd);
         } else {
+            const double dzl = fma(pc.kz, (double)fz, (double)m * pc.zstep);
+            const double u = (fma(pc.kz, (double)iz, pc.Z0) - (j ? f.qlam : 0.0)) + dzl;
             double sd, cd;
             if (u >= 0.0 && u <= f.Lu) {
                 sincos(f.ku * u, &sd, &cd);
@@ -116,6 +114,33 @@ __device__ __forceinline__ void static_field_mixed(const ExtField& f, const Push
     B[0] = f.g0 * (double)Bp[0];
     B[1] = f.g0 * (double)Bp[1];
     B[2] = (double)Bp[2];
+}
+
+// FP32 table for the mixed path: sin, cos of the exact FP64 phase at the node plane, rounded to
+// FP32; NaN when [zeta, zeta + span] of the cell is not inside [0, L_u] for that planar field.
+__global__ void k_phase_table32(ExtField f, double Z0, double kz, double span, int nz, float2* t0, float2* t1)
+{
+    const int iz = blockIdx.x * blockDim.x + threadIdx.x;
+    if (iz >= nz) return;
+    const double zn = fma(kz, (double)iz, Z0);
+    for (int j = 0; j < (t1 ? 2 : 1); ++j) {
+        const double u = zn - (j ? f.qlam : 0.0);
+        float2 v = make_float2(__int_as_float(0x7fc00000), 0.f);
+        if (u >= 0.0 && u + span <= f.Lu) {
+            double s, c;
+            sincos(f.ku * u, &s, &c);
+            v = make_float2((float)s, (float)c);
+        }
+        (j ? t1 : t0)[iz] = v;
+    }
+}
+
+cudaError_t launch_phase_table32(const ExtField& ef, double Z0, double kz, double span, int nz, float2* t0,
+                                 float2* t1, cudaStream_t st)
+{
+    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, Z0, kz, span, nz, t0, t1);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 __global__ void k_phase_table(ExtField f, double Z0, double kz, int nz, double2* t0, double2* t1)
@@ -248,7 +273,8 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 6 : 5) k_push(Particl
         double u[3] = {P.ux[p], P.uy[p], P.uz[p]};
         for (int m = 0; m < g.substeps; ++m) {
             double E[3], B[3];
-            if (pc.ptab[0] && ci[2] >= 0 && ci[2] < g.nz) {
+            if ((std::is_same<real, float>::value ? (const void*)pc.ptab32[0] : (const void*)pc.ptab[0]) &&
+                ci[2] >= 0 && ci[2] < g.nz) {
                 if constexpr (std::is_same<real, float>::value) {
                     const float x = (float)g.x0 + ((float)ci[0] + f[0]) * (float)g.dx;
                     const float y = (float)g.y0 + ((float)ci[1] + f[1]) * (float)g.dy;
