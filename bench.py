@@ -229,6 +229,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
+    ap.add_argument("--workload", default=WORKLOAD, help="workload name from workloads.WORKLOADS")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -245,7 +246,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     m.use_torch_allocator(True)
-    w = workloads.WORKLOADS[WORKLOAD]
+    wname = args.workload
+    w = workloads.WORKLOADS[wname]
     lab = workloads.lab_bunch(w)
     cells = w.nx * w.ny * w.nz
     K, W = args.steps, max(args.warmup, 3)
@@ -356,7 +358,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         o, s_cpu, dt_cpu, _ = cpu_oracle_rate(w, lab, args.cpu_budget, 6)
         cpu = {"value": cells * s_cpu / dt_cpu, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{s_cpu} full field steps of {WORKLOAD} after creation, serial FP64 C",
+               "sample": f"{s_cpu} full field steps of {wname} after creation, serial FP64 C",
                "particle_pushes_per_s": w.n_particles * s_cpu / dt_cpu}
         err = {"steps": s_cpu}
         fo, bo = o.diag()
@@ -382,10 +384,11 @@ def main():
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [w.nx, w.ny, w.nz], "particles": w.n_particles,
+        "config": {"workload": wname, "grid": [w.nx, w.ny, w.nz], "particles": w.n_particles,
                    "precision": "fp32-mixed (fields, offsets, gather, deposit in f32; momentum, external "
                                 "field, diagnostics in f64)",
-                   "l2": "inputs larger than L2 (fields 0.74 GB + particles 0.1 GB resident)",
+                   "l2": f"inputs larger than L2 (fields {22 * cells * 4 / 1e9:.2f} GB + particles "
+                         f"{w.n_particles * 96 / 1e9:.2f} GB resident)",
                    "parallelism": f"{ws} independent replica(s)", "sort_every": 20},
         "particle_pushes_per_s": ws * w.n_particles * K / (ms32 * 1e-3),
         "kernel_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stats32.items() if v[1]},

@@ -60,19 +60,29 @@ struct PushConst {
     // static undulator: per-step table of (sin, cos) of k_u (zeta - offset) at every z node plane
     // (one table per planar field; null: evaluate directly)
     const double2* ptab[2];
-    // FP32-mixed path: the same table rounded to FP32, NaN where the cell (with every sub-step)
-    // is not entirely inside the undulator (those particles take the FP64 general path)
-    const float2* ptab32[2];
+    // FP32-mixed path: per node plane and planar field two float4, {eB0 sin, eB0 cos, bB0 sin,
+    // bB0 cos} and {B0 sin, B0 cos, k_u u, k_u (u - L_u)} of the plane's undulator coordinate u,
+    // evaluated in FP64 and rounded to FP32
+    const float4* ptab32[2];
     double Z0;            // lab coordinate zeta of node plane 0 at t_half: gamma0 (z0 + beta0 c t_half)
     double kz;            // gamma0 dz: zeta per cell along z
     double zstep;         // gamma0 beta0 c dt_b: zeta per sub-step
     float kdz, kzs;       // k_u kz and k_u zstep in FP32: the sub-cell rotation per offset and sub-step
+    // FP32-mixed path: the run's constants rounded once on the host
+    float x0f, y0f, dxf, dyf, dtbf, qrhof, kuf, cpolf, spolf;
+    float qJf[3], cdtbf[3];
+    // rest-frame amplitudes of the static undulator field, gamma0 beta0 c B0, gamma0 B0 and B0,
+    // evaluated in FP64 and rounded to FP32 (the fringe of the FP32-mixed path)
+    float eB0f, bB0f, B0f;
+    // FP32-mixed deposit tile: fixed-point scale per source grid (2^30 / (128 |qJ_l|), 2^30 /
+    // (128 |q|)) and its inverse
+    float tscale[4], tunit[4];
 };
 
 cudaError_t launch_phase_table(const ExtField& ef, double Z0, double kz, int nz, double2* t0, double2* t1,
                                cudaStream_t st);
-cudaError_t launch_phase_table32(const ExtField& ef, double Z0, double kz, double span, int nz, float2* t0,
-                                 float2* t1, cudaStream_t st);
+cudaError_t launch_phase_table32(const ExtField& ef, double Z0, double kz, int nz, float4* t0, float4* t1,
+                                 cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,

@@ -213,7 +213,7 @@ struct RunT final : mithra_run {
     int64_t onaxis_id = 0;
     int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
     double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables, FP64 path (one per planar field)
-    float2* ptab32[2] = {nullptr, nullptr};  // the same rounded to FP32 with inside flags, FP32-mixed path
+    float4* ptab32[2] = {nullptr, nullptr};  // FP32-mixed path: phase and edge distances rounded to FP32
     TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
     int* err_word = nullptr;   // set by a kernel whose bounded wait expired
 
@@ -301,7 +301,7 @@ struct RunT final : mithra_run {
         if (ef.kind == 0 || ef.kind == 1) {
             for (int b = 0; b < (ef.kind == 1 ? 2 : 1); ++b) {
                 if (sizeof(real) == 8) ptab[b] = (double2*)mem.get((size_t)g.nz * sizeof(double2));
-                else ptab32[b] = (float2*)mem.get((size_t)g.nz * sizeof(float2));
+                else ptab32[b] = (float4*)mem.get((size_t)g.nz * 2 * sizeof(float4));
                 if (!ptab[b] && !ptab32[b]) return fail(MITHRA_ENOMEM, "device allocation failed (phase table)");
             }
         }
@@ -412,11 +412,31 @@ struct RunT final : mithra_run {
             pc.zstep = d.g0 * d.b0 * kC * d.dtb;
             pc.kdz = (float)(ef.ku * pc.kz);
             pc.kzs = (float)(ef.ku * pc.zstep);
+            pc.x0f = (float)g.x0;
+            pc.y0f = (float)g.y0;
+            pc.dxf = (float)g.dx;
+            pc.dyf = (float)g.dy;
+            pc.dtbf = (float)g.dtb;
+            pc.qrhof = (float)pc.qrho;
+            pc.kuf = (float)ef.ku;
+            pc.cpolf = (float)ef.cpol;
+            pc.spolf = (float)ef.spol;
+            for (int l = 0; l < 3; ++l) {
+                pc.qJf[l] = (float)pc.qJ[l];
+                pc.cdtbf[l] = (float)pc.cdtb[l];
+            }
+            for (int l = 0; l < 4; ++l) {
+                const double qa = fabs(l < 3 ? pc.qJ[l] : pc.qrho);
+                const double sc = qa > 0.0 ? 1073741824.0 / (128.0 * qa) : 1.0;
+                pc.tscale[l] = (float)sc;
+                pc.tunit[l] = (float)(1.0 / (double)pc.tscale[l]);
+            }
+            pc.eB0f = (float)(ef.g0 * ef.b0 * kC * ef.B0);
+            pc.bB0f = (float)(ef.g0 * ef.B0);
+            pc.B0f = (float)ef.B0;
             pbeg(MITHRA_K_PUSH, &e0);
             if (ptab[0]) CU(launch_phase_table(ef, pc.Z0, pc.kz, g.nz, ptab[0], ptab[1], stream));
-            if (ptab32[0])
-                CU(launch_phase_table32(ef, pc.Z0, pc.kz, pc.kz + (double)g.substeps * pc.zstep, g.nz, ptab32[0],
-                                        ptab32[1], stream));
+            if (ptab32[0]) CU(launch_phase_table32(ef, pc.Z0, pc.kz, g.nz, ptab32[0], ptab32[1], stream));
             CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
             pend(MITHRA_K_PUSH, e0);
             pbeg(MITHRA_K_STENCIL, &e0);
@@ -855,7 +875,7 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
     int64_t cap = 1024;
     while (cap < nsteps) cap *= 2;
     t += 4 * up(cap * 8);                                                     // series (old and new while growing)
-    t += 2 * up(6 * 4) + 2 * up(gr->nz * 16);                                 // boxes, phase tables
+    t += 2 * up(6 * 4) + 2 * up(gr->nz * 32);                                 // boxes, phase tables
     t += up(n * 48);                                                          // lab particles during the boost
     return t;
 }

@@ -1,8 +1,9 @@
 // Particle kernels: boost of the lab bunch into the rest frame (Eqs. LorentzTrasnformParticles,
 // LorentzTransformDeltaR), and one fused pass per field step that evaluates the external
-// field in FP64, gathers the self-field with linear weights (Eq. fieldInterpolation), advances
-// the momentum with the Boris scheme (Eq. BorisScheme, FP64) and deposits the Umeda zigzag
-// current and the linear-weight charge (Sec. "Current Deposition") with atomics.
+// field (Lorentz-transformed in FP64), gathers the self-field with linear weights (Eq.
+// fieldInterpolation), advances the momentum with the Boris scheme (Eq. BorisScheme) and deposits
+// the Umeda zigzag current and the linear-weight charge (Sec. "Current Deposition").  The FP32-mixed
+// pass accumulates each block's deposit in a fixed-point tile in shared memory first.
 #include <type_traits>
 
 #include "common.cuh"
@@ -65,80 +66,124 @@ __device__ __forceinline__ void static_field_fast(const ExtField& f, const PushC
     B[2] = Bp[2];
 }
 
-// FP32-mixed variant: the lab coordinate of the particle (the undulator phase) and the
-// Lorentz transform stay in FP64; the field shape evaluated from that phase - the rotation of
-// the tabulated sin/cos by the sub-cell angle (< 1 rad) and cosh/sinh of k_u y - is computed in
-// FP32, the precision of the fields it is added to.
-__device__ __forceinline__ void static_field_mixed(const ExtField& f, const PushConst& pc, int iz, float fz, int m,
-                                                   float x, float y, double E[3], double B[3])
+// sin and cos of a small angle from their Taylor series about 0 (|t| <= 0.8: the first omitted
+// terms are below 3e-9); larger angles are halved until they are small and restored with the
+// double-angle formulas (never needed when a sub-step moves less than a cell).
+__device__ __forceinline__ void sincos_rot32(float t, float* s, float* c)
 {
-    float Bp[3] = {0.f, 0.f, 0.f};
-    const int nplanar = f.kind == 1 ? 2 : 1;
-    const float ku = (float)f.ku, B0 = (float)f.B0;
-    for (int j = 0; j < nplanar; ++j) {
-        const float c = j ? -(float)f.spol : (float)f.cpol, s = j ? (float)f.cpol : (float)f.spol;
-        const float2 t = __ldg(pc.ptab32[j] + iz);
-        float sn, cs;
-        if (!isnan(t.x)) {
-            // the cell lies inside the undulator: rotate the exact phase of its node plane
-            float sd, cd;
-            sincosf(fmaf(pc.kdz, fz, pc.kzs * (float)m), &sd, &cd);
-            sn = fmaf(t.x, cd, t.y * sd);
-            cs = fmaf(t.y, cd, -t.x * sd);
-        } else {
-            const double dzl = fma(pc.kz, (double)fz, (double)m * pc.zstep);
-            const double u = (fma(pc.kz, (double)iz, pc.Z0) - (j ? f.qlam : 0.0)) + dzl;
-            double sd, cd;
-            if (u >= 0.0 && u <= f.Lu) {
-                sincos(f.ku * u, &sd, &cd);
-            } else {
-                const double kd = f.ku * ((u < 0.0) ? u : (u - f.Lu));
-                const double g = exp(-0.5 * kd * kd);
-                sd = kd * g;
-                cd = g;
-            }
-            sn = (float)sd;
-            cs = (float)cd;
-        }
-        const float ky = ku * (c * y - s * x);
-        const float ch = coshf(ky), sh = sinhf(ky);
-        const float Bt = B0 * ch * sn;
-        Bp[0] -= Bt * s;
-        Bp[1] += Bt * c;
-        Bp[2] += B0 * sh * cs;
+    int k = 0;
+    while (fabsf(t) > 0.8f && k < 24) {
+        t *= 0.5f;
+        ++k;
     }
-    const double gbc = f.g0 * f.b0 * kC;
-    E[0] = -gbc * (double)Bp[1];
-    E[1] = gbc * (double)Bp[0];
-    E[2] = 0.0;
-    B[0] = f.g0 * (double)Bp[0];
-    B[1] = f.g0 * (double)Bp[1];
-    B[2] = (double)Bp[2];
+    const float t2 = t * t;
+    float ps = fmaf(t2, 1.f / 362880.f, -1.f / 5040.f);
+    ps = fmaf(ps, t2, 1.f / 120.f);
+    ps = fmaf(ps, t2, -1.f / 6.f);
+    float sn = t * fmaf(ps, t2, 1.f);
+    float pc = fmaf(t2, -1.f / 3628800.f, 1.f / 40320.f);
+    pc = fmaf(pc, t2, -1.f / 720.f);
+    pc = fmaf(pc, t2, 1.f / 24.f);
+    pc = fmaf(pc, t2, -0.5f);
+    float cs = fmaf(pc, t2, 1.f);
+    for (; k > 0; --k) {
+        const float s2 = 2.f * sn * cs;
+        cs = fmaf(cs, cs, -sn * sn);
+        sn = s2;
+    }
+    *s = sn;
+    *c = cs;
 }
 
-// FP32 table for the mixed path: sin, cos of the exact FP64 phase at the node plane, rounded to
-// FP32; NaN when [zeta, zeta + span] of the cell is not inside [0, L_u] for that planar field.
-__global__ void k_phase_table32(ExtField f, double Z0, double kz, double span, int nz, float2* t0, float2* t1)
+// cosh and sinh of the transverse argument k_u y from their Taylor series (|x| <= 0.5: the first
+// omitted terms are below 3e-10), the library functions beyond.
+__device__ __forceinline__ void coshsinh32(float x, float* ch, float* sh)
+{
+    if (fabsf(x) <= 0.5f) {
+        const float y = x * x;
+        float pc = fmaf(y, 1.f / 40320.f, 1.f / 720.f);
+        pc = fmaf(pc, y, 1.f / 24.f);
+        pc = fmaf(pc, y, 0.5f);
+        *ch = fmaf(pc, y, 1.f);
+        float ps = fmaf(y, 1.f / 362880.f, 1.f / 5040.f);
+        ps = fmaf(ps, y, 1.f / 120.f);
+        ps = fmaf(ps, y, 1.f / 6.f);
+        *sh = x * fmaf(ps, y, 1.f);
+    } else {
+        *ch = coshf(x);
+        *sh = sinhf(x);
+    }
+}
+
+// FP32-mixed variant.  The step's table holds, per node plane and planar field, the lab field
+// at the plane already Lorentz-transformed to the rest frame in FP64 (sin and cos of the plane's
+// undulator phase times the FP64 amplitudes gamma0 beta0 c B0, gamma0 B0, B0) and the phase
+// distances to both ends of the undulator, all rounded to FP32.  The transform is linear with
+// constant coefficients, so rotating the transformed plane values by the sub-cell angle equals
+// transforming the rotated ones; that rotation, the fringe factor outside [0, L_u] and cosh/sinh
+// of k_u y are evaluated in FP32, the precision of the self-field they are added to.
+__device__ __forceinline__ void static_field_mixed(const ExtField& f, const PushConst& pc, int iz, float fz, int m,
+                                                   float x, float y, float E[3], float B[3])
+{
+    E[0] = E[1] = E[2] = 0.f;
+    B[0] = B[1] = B[2] = 0.f;
+    const int nplanar = f.kind == 1 ? 2 : 1;
+    const float th = fmaf(pc.kdz, fz, pc.kzs * (float)m);   // phase beyond the node plane
+    for (int j = 0; j < nplanar; ++j) {
+        const float c = j ? -pc.spolf : pc.cpolf, s = j ? pc.cpolf : pc.spolf;
+        const float4 t0 = __ldg(pc.ptab32[j] + 2 * iz);       // eB0 sin, eB0 cos, bB0 sin, bB0 cos
+        const float4 t1 = __ldg(pc.ptab32[j] + 2 * iz + 1);   // B0 sin, B0 cos, k_u u, k_u (u - L_u)
+        const float ua = t1.z + th, ub = t1.w + th;
+        float eS, bS, zC;   // eB0 sin, bB0 sin, B0 cos of the particle's phase
+        if (ua >= 0.f && ub <= 0.f) {
+            float sd, cd;
+            sincos_rot32(th, &sd, &cd);
+            eS = fmaf(t0.x, cd, t0.y * sd);
+            bS = fmaf(t0.z, cd, t0.w * sd);
+            zC = fmaf(t1.y, cd, -t1.x * sd);
+        } else {
+            const float kd = ua < 0.f ? ua : ub;
+            const float g = expf(-0.5f * kd * kd);
+            eS = pc.eB0f * (kd * g);
+            bS = pc.bB0f * (kd * g);
+            zC = pc.B0f * g;
+        }
+        float ch, sh;
+        coshsinh32(pc.kuf * (c * y - s * x), &ch, &sh);
+        eS *= ch;
+        bS *= ch;
+        E[0] -= eS * c;
+        E[1] -= eS * s;
+        B[0] -= bS * s;
+        B[1] += bS * c;
+        B[2] += sh * zC;
+    }
+}
+
+// FP32 table for the mixed path, two float4 per node plane and planar field: the sin and cos of
+// the plane's phase k_u u times the FP64 rest-frame amplitudes (gamma0 beta0 c B0, gamma0 B0, B0),
+// and the distances k_u u, k_u (u - L_u) to both ends of the undulator; FP64 throughout, rounded
+// once.
+__global__ void k_phase_table32(ExtField f, double Z0, double kz, int nz, float4* t0, float4* t1)
 {
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
     if (iz >= nz) return;
     const double zn = fma(kz, (double)iz, Z0);
+    const double eB0 = f.g0 * f.b0 * kC * f.B0, bB0 = f.g0 * f.B0;
     for (int j = 0; j < (t1 ? 2 : 1); ++j) {
-        const double u = zn - (j ? f.qlam : 0.0);
-        float2 v = make_float2(__int_as_float(0x7fc00000), 0.f);
-        if (u >= 0.0 && u + span <= f.Lu) {
-            double s, c;
-            sincos(f.ku * u, &s, &c);
-            v = make_float2((float)s, (float)c);
-        }
-        (j ? t1 : t0)[iz] = v;
+        const double ph = f.ku * (zn - (j ? f.qlam : 0.0));
+        double s, c;
+        sincos(ph, &s, &c);
+        float4* t = (j ? t1 : t0) + 2 * iz;
+        t[0] = make_float4((float)(eB0 * s), (float)(eB0 * c), (float)(bB0 * s), (float)(bB0 * c));
+        t[1] = make_float4((float)(f.B0 * s), (float)(f.B0 * c), (float)ph, (float)(ph - f.ku * f.Lu));
     }
 }
 
-cudaError_t launch_phase_table32(const ExtField& ef, double Z0, double kz, double span, int nz, float2* t0,
-                                 float2* t1, cudaStream_t st)
+cudaError_t launch_phase_table32(const ExtField& ef, double Z0, double kz, int nz, float4* t0, float4* t1,
+                                 cudaStream_t st)
 {
-    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, Z0, kz, span, nz, t0, t1);
+    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, Z0, kz, nz, t0, t1);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -181,12 +226,42 @@ __device__ __forceinline__ void split_pos(double X, int32_t* c, real* f)
     *f = o;
 }
 
+// Where a deposit goes.  GlobalTarget: the four source grids (J_x, J_y, J_z, rho) in global
+// memory, atomics in the grids' type.  TileTarget (FP32-mixed path): a block's tile of them in
+// shared memory, node (i, j, k) at (k - oz) sz + (j - oy) sy + (i - ox), accumulated in 32-bit
+// fixed point - shared-memory integer adds are native, floating-point ones are not - with a
+// scale per grid chosen so that no sum can overflow (see the push kernel).
+template <typename real>
+struct GlobalTarget {
+    real* c[4];
+    int64_t sy, sz;
+    __device__ __forceinline__ int64_t at(int i, int j, int k) const { return (int64_t)k * sz + (int64_t)j * sy + i; }
+    __device__ __forceinline__ void add(int comp, int64_t off, real v) const { atomicAdd(c[comp] + off, v); }
+};
+
+struct TileTarget {
+    int* t;
+    int vol;
+    int64_t sy, sz;
+    int ox, oy, oz;
+    float scale[4];
+    __device__ __forceinline__ int64_t at(int i, int j, int k) const
+    {
+        return (int64_t)(k - oz) * sz + (int64_t)(j - oy) * sy + (i - ox);
+    }
+    __device__ __forceinline__ void add(int comp, int64_t off, float v) const
+    {
+        const unsigned a = (unsigned)__cvta_generic_to_shared(t + comp * vol + off);
+        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(__float2int_rn(v * scale[comp])) : "memory");
+    }
+};
+
 // One straight piece a -> b (cell units, relative to the base cell) lying in local cell `cl`:
 // current on the edges parallel to each axis with the exact path average of the linear
 // weights of the two other axes.
-template <typename real>
+template <typename real, typename Tgt>
 __device__ __forceinline__ void deposit_piece(const real a[3], const real b[3], const int cl[3], const int base[3],
-                                              const Fields4<real>& src, const Geom& g, const PushConst& pc)
+                                              const Tgt& T, const real qJ[3])
 {
     real la[3], d[3], mid[3];
 #pragma unroll
@@ -195,28 +270,27 @@ __device__ __forceinline__ void deposit_piece(const real a[3], const real b[3], 
         d[l] = b[l] - a[l];
         mid[l] = la[l] + (real)0.5 * d[l];
     }
-    const int64_t o = (int64_t)(base[2] + cl[2]) * g.sz + (int64_t)(base[1] + cl[1]) * g.sy + (base[0] + cl[0]);
-    const int64_t st[3] = {1, g.sy, g.sz};
+    const int64_t o = T.at(base[0] + cl[0], base[1] + cl[1], base[2] + cl[2]);
+    const int64_t st[3] = {1, T.sy, T.sz};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
         if (d[l] == (real)0) continue;
         const int m = (l + 1) % 3, n = (l + 2) % 3;
-        const real F = (real)pc.qJ[l] * d[l];
+        const real F = qJ[l] * d[l];
         const real cross = d[m] * d[n] * (real)(1.0 / 12.0);
         const real wm1 = mid[m], wm0 = (real)1 - mid[m];
         const real wn1 = mid[n], wn0 = (real)1 - mid[n];
-        real* J = src.c[l];
-        atomicAdd(J + o, F * (wm0 * wn0 + cross));
-        atomicAdd(J + o + st[m], F * (wm1 * wn0 - cross));
-        atomicAdd(J + o + st[n], F * (wm0 * wn1 - cross));
-        atomicAdd(J + o + st[m] + st[n], F * (wm1 * wn1 + cross));
+        T.add(l, o, F * (wm0 * wn0 + cross));
+        T.add(l, o + st[m], F * (wm1 * wn0 - cross));
+        T.add(l, o + st[n], F * (wm0 * wn1 - cross));
+        T.add(l, o + st[m] + st[n], F * (wm1 * wn1 + cross));
     }
 }
 
 // Umeda zigzag of the move A -> B (relative to the base cell, |B - A| <= 1 per axis).
-template <typename real>
-__device__ __forceinline__ void zigzag(const real A[3], const real B[3], const int base[3], const Fields4<real>& src,
-                                       const Geom& g, const PushConst& pc)
+template <typename real, typename Tgt>
+__device__ __forceinline__ void zigzag(const real A[3], const real B[3], const int base[3], const Tgt& T,
+                                       const real qJ[3])
 {
     int c1[3], c2[3];
     real R[3];
@@ -228,8 +302,52 @@ __device__ __forceinline__ void zigzag(const real A[3], const real B[3], const i
         const real mid = (real)0.5 * (A[l] + B[l]);
         R[l] = fmin(lo + (real)1, fmax(hi, mid));
     }
-    deposit_piece(A, R, c1, base, src, g, pc);
-    deposit_piece(R, B, c2, base, src, g, pc);
+    deposit_piece(A, R, c1, base, T, qJ);
+    deposit_piece(R, B, c2, base, T, qJ);
+}
+
+// Charge of one particle at cell c, offset fo, on the cell's eight nodes (linear weights).
+template <typename real, typename Tgt>
+__device__ __forceinline__ void deposit_rho(const int c[3], const real fo[3], real q, const Tgt& T)
+{
+    const real wx[2] = {(real)1 - fo[0], fo[0]};
+    const real wy[2] = {(real)1 - fo[1], fo[1]};
+    const real wz[2] = {(real)1 - fo[2], fo[2]};
+    const int64_t o = T.at(c[0], c[1], c[2]);
+#pragma unroll
+    for (int K = 0; K < 2; ++K)
+#pragma unroll
+        for (int J = 0; J < 2; ++J)
+#pragma unroll
+            for (int I = 0; I < 2; ++I) T.add(3, o + K * T.sz + J * T.sy + I, q * wx[I] * wy[J] * wz[K]);
+}
+
+// Block-wide bounding box of [lo, hi] (inclusive node ranges; empty when lo > hi), returned to
+// every thread.  Two barriers.
+__device__ __forceinline__ void block_box(const int lo[3], const int hi[3], int out[6])
+{
+    __shared__ int sh[6][4];   // 128 threads = 4 warps
+    __shared__ int res[6];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int a = __reduce_min_sync(0xffffffffu, lo[d]);
+        const int b = __reduce_max_sync(0xffffffffu, hi[d]);
+        if (lane == 0) {
+            sh[d][w] = a;
+            sh[3 + d][w] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int q = threadIdx.x;
+        int v = sh[q][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = q < 3 ? min(v, sh[q][k]) : max(v, sh[q][k]);
+        res[q] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 6; ++q) out[q] = res[q];
 }
 
 // Block-wide min/max of the cells this block deposited into (or will gather from next step),
@@ -260,141 +378,287 @@ __device__ __forceinline__ void box_merge(int lo[3], int hi[3], int* box_out)
     }
 }
 
+// One sub-step of one particle: external field (FP64 lab coordinate and Lorentz transform),
+// gather of the self-field with linear weights, Boris push, and the move.  b = end point of the
+// move in cell units relative to cell ci, (nc, nf) = the new cell and offset.  Returns whether
+// the particle starts in an active cell (the gather and the deposit need its whole stencil).
 template <typename real>
-__global__ void __launch_bounds__(128, sizeof(real) == 4 ? 6 : 5) k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb,
-                                              Fields4<real> src, PushConst pc, int* box_out)
+__device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3], double u[3], real b[3], int nc[3],
+                                         real nf[3], const Geom& g, const ExtField& ef, const Fields6<real>& eb,
+                                         const PushConst& pc)
+{
+    double E[3], B[3];    // external field in FP64 (FP64 path, and the general evaluation)
+    float Ef[3], Bf[3];   // external field rounded to FP32 (FP32-mixed path)
+    bool tab = false;
+    if constexpr (std::is_same<real, float>::value) {
+        if (pc.ptab32[0] && ci[2] >= 0 && ci[2] < g.nz) {
+            const float x = fmaf((float)ci[0] + f[0], pc.dxf, pc.x0f);
+            const float y = fmaf((float)ci[1] + f[1], pc.dyf, pc.y0f);
+            static_field_mixed(ef, pc, ci[2], f[2], m, x, y, Ef, Bf);
+            tab = true;
+        }
+    } else {
+        if (pc.ptab[0] && ci[2] >= 0 && ci[2] < g.nz) {
+            const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
+            const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
+            static_field_fast(ef, pc, ci[2], (double)f[2], m, x, y, E, B);
+            tab = true;
+        }
+    }
+    if (!tab) {
+        const double t = pc.t_half + (double)m * g.dtb;
+        const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
+        const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
+        const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
+        external_field(ef, x, y, z, t, E, B);
+        if constexpr (std::is_same<real, float>::value) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Ef[c] = (float)E[c];
+                Bf[c] = (float)B[c];
+            }
+        }
+    }
+    const bool a1 = active_cell(ci[0], ci[1], ci[2], g);
+    real s[6] = {0, 0, 0, 0, 0, 0};
+    if (a1) {
+        const real wx[2] = {(real)1 - f[0], f[0]};
+        const real wy[2] = {(real)1 - f[1], f[1]};
+        const real wz[2] = {(real)1 - f[2], f[2]};
+        const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
+#pragma unroll
+        for (int K = 0; K < 2; ++K)
+#pragma unroll
+            for (int J = 0; J < 2; ++J)
+#pragma unroll
+                for (int I = 0; I < 2; ++I) {
+                    const real w = wx[I] * wy[J] * wz[K];
+                    const int64_t id = o + K * g.sz + J * g.sy + I;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) s[c] += w * __ldg(eb.c[c] + id);
+                }
+    }
+    real ig;
+    real cdt[3];
+    real um[3];   // the momentum the move uses, in the path's precision
+    if constexpr (std::is_same<real, float>::value) {
+        // Boris rotation in FP32 on the momentum rounded to FP32; its increment is added to the
+        // FP64 momentum, and the move uses the rotated FP32 momentum
+        float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
+        const float Et[3] = {Ef[0] + s[0], Ef[1] + s[1], Ef[2] + s[2]};
+        const float Bt[3] = {Bf[0] + s[3], Bf[1] + s[4], Bf[2] + s[5]};
+        const float u0[3] = {uf[0], uf[1], uf[2]};
+        boris_f32(uf, Et, Bt, pc.dtbf);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            u[l] += (double)(uf[l] - u0[l]);
+            cdt[l] = pc.cdtbf[l];
+            um[l] = uf[l];
+        }
+        // gamma^2 = 1 + u.u accumulated in FP64 from the FP64 momentum; its reciprocal root only
+        // scales the FP32 move, so it is taken in FP32
+        ig = rsqrtf((float)fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            E[c] += (double)s[c];
+            B[c] += (double)s[3 + c];
+            cdt[c] = pc.cdtb[c];
+        }
+        boris(u, E, B, g.dtb);
+        ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) um[l] = u[l];
+    }
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        b[l] = f[l] + cdt[l] * (um[l] * ig);
+        const real fl = floor(b[l]);
+        int c = (int)fl;
+        real o = b[l] - fl;
+        if (o >= (real)1) { o -= (real)1; c += 1; }
+        b[l] = (real)c + o;   // the deposit ends exactly at the stored (cell, offset) point
+        nc[l] = ci[l] + c;
+        nf[l] = o;
+    }
+    return a1;
+}
+
+// Resident blocks of 128 threads per SM the push is compiled for (the register budget per thread).
+#ifndef MITHRA_PUSH_MIN_BLOCKS_F32
+#define MITHRA_PUSH_MIN_BLOCKS_F32 6
+#endif
+#ifndef MITHRA_PUSH_MIN_BLOCKS_F64
+#define MITHRA_PUSH_MIN_BLOCKS_F64 5
+#endif
+
+// Nodes per grid of the FP32-mixed push's deposit tile in shared memory.
+constexpr int kTileNodes = 1024;
+
+// The push: one thread per particle, 128 per block, the particles in cell-sorted order.
+//
+// Deposit (FP32-mixed path).  The block's current (and, after the last sub-step, charge) first
+// accumulates in a fixed-point tile of the source grids in shared memory that covers the block's
+// bounding box of touched nodes; the tile's nonzero nodes are then added to the grids in global
+// memory, one atomic per node and grid.  Neighbouring particles of the sorted order share cells,
+// so many shared-memory adds meet in one global add.  A block whose box does not fit the tile,
+// and every move longer than a cell on some axis (split into pieces), adds to global memory
+// directly, as does the whole FP64 path.
+template <typename real>
+__global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCKS_F32 : MITHRA_PUSH_MIN_BLOCKS_F64)
+    k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb, Fields4<real> src, PushConst pc,
+           int* box_out)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff};
     int hi[3] = {(int)0x80000000, (int)0x80000000, (int)0x80000000};
-    if (p < np) {
-        int ci[3] = {P.ix[p], P.iy[p], P.iz[p]};
-        real f[3] = {P.fx[p], P.fy[p], P.fz[p]};
-        double u[3] = {P.ux[p], P.uy[p], P.uz[p]};
-        for (int m = 0; m < g.substeps; ++m) {
-            double E[3], B[3];
-            if ((std::is_same<real, float>::value ? (const void*)pc.ptab32[0] : (const void*)pc.ptab[0]) &&
-                ci[2] >= 0 && ci[2] < g.nz) {
-                if constexpr (std::is_same<real, float>::value) {
-                    const float x = (float)g.x0 + ((float)ci[0] + f[0]) * (float)g.dx;
-                    const float y = (float)g.y0 + ((float)ci[1] + f[1]) * (float)g.dy;
-                    static_field_mixed(ef, pc, ci[2], f[2], m, x, y, E, B);
-                } else {
-                    const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
-                    const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
-                    static_field_fast(ef, pc, ci[2], (double)f[2], m, x, y, E, B);
-                }
-            } else {
-                const double t = pc.t_half + (double)m * g.dtb;
-                const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
-                const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
-                const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
-                external_field(ef, x, y, z, t, E, B);
-            }
-            const bool a1 = active_cell(ci[0], ci[1], ci[2], g);
-            real s[6] = {0, 0, 0, 0, 0, 0};
-            if (a1) {
-                const real wx[2] = {(real)1 - f[0], f[0]};
-                const real wy[2] = {(real)1 - f[1], f[1]};
-                const real wz[2] = {(real)1 - f[2], f[2]};
-                const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
-#pragma unroll
-                for (int K = 0; K < 2; ++K)
-#pragma unroll
-                    for (int J = 0; J < 2; ++J)
-#pragma unroll
-                        for (int I = 0; I < 2; ++I) {
-                            const real w = wx[I] * wy[J] * wz[K];
-                            const int64_t id = o + K * g.sz + J * g.sy + I;
-#pragma unroll
-                            for (int c = 0; c < 6; ++c) s[c] += w * __ldg(eb.c[c] + id);
-                        }
-            }
-            real ig;
-            if constexpr (std::is_same<real, float>::value) {
-                // Boris rotation in FP32 on the momentum rounded to FP32; its increment is added
-                // to the FP64 momentum, and 1/gamma of the move comes from the FP64 momentum
-                float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
-                const float Et[3] = {(float)E[0] + s[0], (float)E[1] + s[1], (float)E[2] + s[2]};
-                const float Bt[3] = {(float)B[0] + s[3], (float)B[1] + s[4], (float)B[2] + s[5]};
-                const float u0[3] = {uf[0], uf[1], uf[2]};
-                boris_f32(uf, Et, Bt, (float)g.dtb);
-#pragma unroll
-                for (int l = 0; l < 3; ++l) u[l] += (double)(uf[l] - u0[l]);
-                ig = (float)rsqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            } else {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    E[c] += (double)s[c];
-                    B[c] += (double)s[3 + c];
-                }
-                boris(u, E, B, g.dtb);
-                ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            }
-            real b[3];
-            int nc[3];
-            real nf[3];
+    // every thread runs the loop (the block shares the tile); threads past the end carry a
+    // particle outside the grid that deposits nothing
+    const bool alive = p < np;
+    int ci[3] = {-4, -4, -4};
+    real f[3] = {0, 0, 0};
+    double u[3] = {0.0, 0.0, 0.0};
+    if (alive) {
+        ci[0] = P.ix[p];
+        ci[1] = P.iy[p];
+        ci[2] = P.iz[p];
+        f[0] = P.fx[p];
+        f[1] = P.fy[p];
+        f[2] = P.fz[p];
+        u[0] = P.ux[p];
+        u[1] = P.uy[p];
+        u[2] = P.uz[p];
+    }
+    real qJ[3], q;
+    if constexpr (std::is_same<real, float>::value) {
+        qJ[0] = pc.qJf[0];
+        qJ[1] = pc.qJf[1];
+        qJ[2] = pc.qJf[2];
+        q = pc.qrhof;
+    } else {
+        qJ[0] = pc.qJ[0];
+        qJ[1] = pc.qJ[1];
+        qJ[2] = pc.qJ[2];
+        q = pc.qrho;
+    }
+    GlobalTarget<real> G;
+    G.c[0] = src.c[0];
+    G.c[1] = src.c[1];
+    G.c[2] = src.c[2];
+    G.c[3] = src.c[3];
+    G.sy = g.sy;
+    G.sz = g.sz;
+    bool rho_done = false;
+    for (int m = 0; m < g.substeps; ++m) {
+        real b[3] = {f[0], f[1], f[2]};
+        int nc[3] = {ci[0], ci[1], ci[2]};
+        real nf[3] = {f[0], f[1], f[2]};
+        const bool a1 = alive && push_one<real>(m, ci, f, u, b, nc, nf, g, ef, eb, pc);
+        bool simple = false;   // a move of at most one cell per axis: deposited through the tile
+        if (a1 && active_cell(nc[0], nc[1], nc[2], g)) {
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
-                b[l] = f[l] + (real)pc.cdtb[l] * ((real)u[l] * ig);
-                const real fl = floor(b[l]);
-                int c = (int)fl;
-                real o = b[l] - fl;
-                if (o >= (real)1) { o -= (real)1; c += 1; }
-                b[l] = (real)c + o;   // the deposit ends exactly at the stored (cell, offset) point
-                nc[l] = ci[l] + c;
-                nf[l] = o;
+                lo[l] = min(lo[l], min(ci[l], nc[l]));
+                hi[l] = max(hi[l], max(ci[l], nc[l]));
             }
-            if (a1 && active_cell(nc[0], nc[1], nc[2], g)) {
+            real mx = fmax(fabs(b[0] - f[0]), fmax(fabs(b[1] - f[1]), fabs(b[2] - f[2])));
+            if (mx <= (real)1) {
+                simple = true;
+            } else {
+                const int ns = (int)ceil((double)mx);
+                real A[3], Bq[3];
+                for (int s = 0; s < ns; ++s) {
 #pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    lo[l] = min(lo[l], min(ci[l], nc[l]));
-                    hi[l] = max(hi[l], max(ci[l], nc[l]));
+                    for (int l = 0; l < 3; ++l) {
+                        const real dl = b[l] - f[l];
+                        A[l] = (s == 0) ? f[l] : f[l] + dl * ((real)s / (real)ns);
+                        Bq[l] = (s == ns - 1) ? b[l] : f[l] + dl * ((real)(s + 1) / (real)ns);
+                    }
+                    zigzag(A, Bq, ci, G, qJ);
                 }
-                real mx = fmax(fabs(b[0] - f[0]), fmax(fabs(b[1] - f[1]), fabs(b[2] - f[2])));
-                if (mx <= (real)1) {
-                    zigzag(f, b, ci, src, g, pc);
-                } else {
-                    const int ns = (int)ceil((double)mx);
-                    real A[3], Bq[3];
-                    for (int s = 0; s < ns; ++s) {
+            }
+        }
+        // the charge at the end of the last sub-step goes through the tile with the current
+        // when the move was simple; otherwise it is added directly below
+        const bool last = m == g.substeps - 1;
+        const bool rho_t = simple && g.space_charge && last;
+        if constexpr (std::is_same<real, float>::value) {
+            __shared__ int tile[4 * kTileNodes];
+            int tlo[3], thi[3], box[6];
 #pragma unroll
-                        for (int l = 0; l < 3; ++l) {
-                            const real dl = b[l] - f[l];
-                            A[l] = (s == 0) ? f[l] : f[l] + dl * ((real)s / (real)ns);
-                            Bq[l] = (s == ns - 1) ? b[l] : f[l] + dl * ((real)(s + 1) / (real)ns);
-                        }
-                        zigzag(A, Bq, ci, src, g, pc);
+            for (int l = 0; l < 3; ++l) {
+                tlo[l] = simple ? min(ci[l], nc[l]) : 0x7fffffff;
+                thi[l] = simple ? max(ci[l], nc[l]) + 1 : (int)0x80000000;
+            }
+            block_box(tlo, thi, box);
+            const int tx = box[3] - box[0] + 1, ty = box[4] - box[1] + 1, tz = box[5] - box[2] + 1;
+            const int ngrid = (g.space_charge && last) ? 4 : 3;
+            if (box[0] <= box[3] && (int64_t)tx * ty * tz <= kTileNodes) {
+                const int vol = tx * ty * tz;
+                for (int i = threadIdx.x; i < ngrid * vol; i += blockDim.x) tile[i] = 0;
+                __syncthreads();
+                // A particle adds at most |qJ_l| to any node of J_l over its two pieces (the
+                // path-averaged weights lie in [0, 1] and the pieces' extents along l sum to at
+                // most one cell) and at most |q| to a node of rho, so a block of 128 sums to at most
+                // 128 |qJ_l| (128 |q|): that maps to 2^30, and the rounding of each term adds at
+                // most 1/2.
+                TileTarget T;
+                T.t = tile;
+                T.vol = vol;
+                T.sy = tx;
+                T.sz = (int64_t)tx * ty;
+                T.ox = box[0];
+                T.oy = box[1];
+                T.oz = box[2];
+                T.scale[0] = pc.tscale[0];
+                T.scale[1] = pc.tscale[1];
+                T.scale[2] = pc.tscale[2];
+                T.scale[3] = pc.tscale[3];
+                if (simple) {
+                    zigzag(f, b, ci, T, qJ);
+                    if (rho_t) deposit_rho(nc, nf, q, T);
+                }
+                __syncthreads();
+                // index -> (grid, k, j, i) with FP32 reciprocals: the quotients are below 2^12 and
+                // (index + 1/2) / divisor stays at least 1/(2 divisor) away from an integer
+                const float ivol = 1.f / (float)vol, itxy = 1.f / (float)(tx * ty), itx = 1.f / (float)tx;
+                for (int i = threadIdx.x; i < ngrid * vol; i += blockDim.x) {
+                    const int v = tile[i];
+                    if (v != 0) {
+                        const int c = (int)(((float)i + 0.5f) * ivol), r = i - c * vol;
+                        const int k = (int)(((float)r + 0.5f) * itxy), r2 = r - k * tx * ty;
+                        const int j = (int)(((float)r2 + 0.5f) * itx), ii = r2 - j * tx;
+                        const float inv = c == 0 ? pc.tunit[0] : c == 1 ? pc.tunit[1] : c == 2 ? pc.tunit[2] : pc.tunit[3];
+                        real* dst = c == 0 ? src.c[0] : c == 1 ? src.c[1] : c == 2 ? src.c[2] : src.c[3];
+                        atomicAdd(dst + G.at(box[0] + ii, box[1] + j, box[2] + k), (float)v * inv);
                     }
                 }
+                __syncthreads();   // the tile is reused by the next sub-step
+            } else if (simple) {
+                zigzag(f, b, ci, G, qJ);
+                if (rho_t) deposit_rho(nc, nf, q, G);
             }
-#pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                ci[l] = nc[l];
-                f[l] = nf[l];
-            }
+        } else if (simple) {
+            // FP64 path: floating-point adds straight into the grids
+            zigzag(f, b, ci, G, qJ);
+            if (rho_t) deposit_rho(nc, nf, q, G);
         }
-        if (active_cell(ci[0], ci[1], ci[2], g)) {
+        if (last) rho_done = rho_t;
 #pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                lo[l] = min(lo[l], ci[l]);
-                hi[l] = max(hi[l], ci[l]);
-            }
-            if (g.space_charge) {
-                const real wx[2] = {(real)1 - f[0], f[0]};
-                const real wy[2] = {(real)1 - f[1], f[1]};
-                const real wz[2] = {(real)1 - f[2], f[2]};
-                const int64_t o = (int64_t)ci[2] * g.sz + (int64_t)ci[1] * g.sy + ci[0];
-                const real q = (real)pc.qrho;
-#pragma unroll
-                for (int K = 0; K < 2; ++K)
-#pragma unroll
-                    for (int J = 0; J < 2; ++J)
-#pragma unroll
-                        for (int I = 0; I < 2; ++I)
-                            atomicAdd(src.c[3] + o + K * g.sz + J * g.sy + I, q * wx[I] * wy[J] * wz[K]);
-            }
+        for (int l = 0; l < 3; ++l) {
+            ci[l] = nc[l];
+            f[l] = nf[l];
         }
+    }
+    if (alive && active_cell(ci[0], ci[1], ci[2], g)) {
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            lo[l] = min(lo[l], ci[l]);
+            hi[l] = max(hi[l], ci[l]);
+        }
+        if (g.space_charge && !rho_done) deposit_rho(ci, f, q, G);
+    }
+    if (alive) {
         P.ix[p] = ci[0];
         P.iy[p] = ci[1];
         P.iz[p] = ci[2];
