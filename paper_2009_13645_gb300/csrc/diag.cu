@@ -55,22 +55,23 @@ __global__ void __launch_bounds__(kRedThreads) k_power_step(Fields6<real> eb, Ge
     __shared__ double sh[32];
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const StepDev sd = *ps.sd;
     double contrib = 0.0;
     if (pl < plane) {
         const int64_t id = (int64_t)ps.kp * g.sz + pl;
-        if (id == ps.onaxis_id) *ps.onaxis_out = (double)eb.c[0][id];
+        if (id == ps.onaxis_id) ps.onaxis_series[sd.n] = (double)eb.c[0][id];
         const double x[4] = {(double)eb.c[0][id], (double)eb.c[1][id], (double)eb.c[3][id], (double)eb.c[4][id]};
-        double* r = ps.ring + (int64_t)ps.slot * 4 * plane + pl;
+        double* r = ps.ring + (int64_t)sd.slot * 4 * plane + pl;
         double re[4], im[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             double a = ps.acc[(2 * q) * plane + pl], b = ps.acc[(2 * q + 1) * plane + pl];
-            a += x[q] * ps.cn;
-            b -= x[q] * ps.sn;
-            if (ps.full) {
+            a += x[q] * sd.cn;
+            b -= x[q] * sd.sn;
+            if (sd.full) {
                 const double o = r[q * plane];
-                a -= o * ps.co;
-                b += o * ps.so;
+                a -= o * sd.co;
+                b += o * sd.so;
             }
             ps.acc[(2 * q) * plane + pl] = a;
             ps.acc[(2 * q + 1) * plane + pl] = b;
@@ -79,26 +80,64 @@ __global__ void __launch_bounds__(kRedThreads) k_power_step(Fields6<real> eb, Ge
             im[q] = b;
         }
         const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
-        if (ps.emit && i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2)
+        if (sd.emit && i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2)
             contrib = (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
     }
     const double tot = block_sum(contrib, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
+// Compensated sum of the step's partials to series[n] once the window is complete.
+__global__ void k_power_final(const double* __restrict__ partial, int npartial, double scale, const StepDev* sd,
+                              double* __restrict__ series)
+{
+    __shared__ double sh[32];
+    if (!sd->emit) return;
+    double s = 0.0, comp = 0.0;
+    for (int i = threadIdx.x; i < npartial; i += blockDim.x) {
+        const double v = partial[i];
+        const double t = s + v;
+        comp += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    const double tot = block_sum(s + comp, sh);
+    if (threadIdx.x == 0) series[sd->n] = tot * scale;
+}
+
 template <typename real>
 cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const PowerStep& ps, double scale,
-                              double* partial, int npartial, double* out, cudaStream_t st)
+                              double* partial, int npartial, double* series, cudaStream_t st)
 {
     const int64_t plane = (int64_t)g.nx * g.ny;
     const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
     if ((int)nb > npartial) return cudaErrorInvalidValue;
     k_power_step<real><<<nb, kRedThreads, 0, st>>>(eb, g, ps, partial);
+    k_power_final<<<1, kRedThreads, 0, st>>>(partial, (int)nb, scale, ps.sd, series);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+// Per-step values from the step counter (one thread).
+__global__ void k_step_begin(StepDev* sd, StepConst c)
+{
+    const int64_t n = sd->next;
+    StepDev v;
+    v.n = n;
+    v.next = n + 1;
+    v.t_half = c.T0 + ((double)n + 0.5) * c.dt;
+    v.Z0 = c.g0 * (c.z0 + c.b0 * kC * v.t_half);
+    v.slot = (int)(n % c.M);
+    v.full = n >= c.M ? 1 : 0;
+    v.emit = n + 1 >= c.M ? 1 : 0;
+    sincos(c.omega_h * ((double)n + 0.5) * c.dt, &v.sn, &v.cn);
+    sincos(c.omega_h * ((double)(n - c.M) + 0.5) * c.dt, &v.so, &v.co);
+    *sd = v;
+}
+
+cudaError_t launch_step_begin(StepDev* sd, const StepConst& c, cudaStream_t st)
+{
+    k_step_begin<<<1, 1, 0, st>>>(sd, c);
     count_launches(1);
-    if (ps.emit) {
-        k_final<<<1, kRedThreads, 0, st>>>(partial, (int)nb, 1, scale, out);
-        count_launches(1);
-    }
     return cudaGetLastError();
 }
 template cudaError_t launch_power_step<float>(const Fields6<float>&, const Geom&, const PowerStep&, double, double*,

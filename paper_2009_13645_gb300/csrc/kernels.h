@@ -51,9 +51,28 @@ template <typename real>
 cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, const EmitBox& bx,
                         cudaStream_t st);
 
+// Per-step values derived on the device from the step counter, so that a captured sequence of
+// steps replays without host-side parameters.  k_step_begin fills it at the start of every step.
+struct StepDev {
+    int64_t n;        // the step being computed
+    int64_t next;     // the counter: the step after it
+    double t_half;    // rest-frame time of r^{n+1/2}: T0 + (n + 1/2) dt
+    double Z0;        // lab coordinate zeta of node plane 0 at t_half: gamma0 (z0 + beta0 c t_half)
+    int slot;         // power-plane ring slot of step n (the slot of step n - M is the same)
+    int full;         // the ring holds step n - M
+    int emit;         // the power window is complete
+    double cn, sn;    // cos, sin of w t_n
+    double co, so;    // cos, sin of w t_{n-M}
+};
+struct StepConst {
+    double T0, dt, g0, b0, z0, omega_h;
+    int M;
+};
+cudaError_t launch_step_begin(StepDev* sd, const StepConst& c, cudaStream_t st);
+
 // Particles.
 struct PushConst {
-    double t_half;        // rest-frame time of r^{n+1/2}
+    const StepDev* sd;    // the step's time (t_half) and lab offset of the node planes (Z0)
     double qJ[3];         // q / (D_m D_n dt): current density per unit displacement (cells) along each axis
     double qrho;          // q / (dx dy dz)
     double cdtb[3];       // c dt_b / D_l
@@ -64,7 +83,6 @@ struct PushConst {
     // bB0 cos} and {B0 sin, B0 cos, k_u u, k_u (u - L_u)} of the plane's undulator coordinate u,
     // evaluated in FP64 and rounded to FP32
     const float4* ptab32[2];
-    double Z0;            // lab coordinate zeta of node plane 0 at t_half: gamma0 (z0 + beta0 c t_half)
     double kz;            // gamma0 dz: zeta per cell along z
     double zstep;         // gamma0 beta0 c dt_b: zeta per sub-step
     float kdz, kzs;       // k_u kz and k_u zstep in FP32: the sub-cell rotation per offset and sub-step
@@ -79,9 +97,9 @@ struct PushConst {
     float tscale[4], tunit[4];
 };
 
-cudaError_t launch_phase_table(const ExtField& ef, double Z0, double kz, int nz, double2* t0, double2* t1,
+cudaError_t launch_phase_table(const ExtField& ef, const StepDev* sd, double kz, int nz, double2* t0, double2* t1,
                                cudaStream_t st);
-cudaError_t launch_phase_table32(const ExtField& ef, double Z0, double kz, int nz, float4* t0, float4* t1,
+cudaError_t launch_phase_table32(const ExtField& ef, const StepDev* sd, double kz, int nz, float4* t0, float4* t1,
                                  cudaStream_t st);
 
 template <typename real>
@@ -117,19 +135,16 @@ size_t sort_scan_partials(int64_t nbins);
 // Diagnostics.
 struct PowerStep {
     int kp;                 // plane index
-    int slot;               // ring slot of step n (the slot of step n - M is the same)
-    int full;               // the ring holds step n - M: subtract it
-    int emit;               // window complete: reduce the power
-    double cn, sn;          // cos, sin of w t_n
-    double co, so;          // cos, sin of w t_{n-M}
+    const StepDev* sd;      // step n: ring slot, window state, exp(-j w t) of steps n and n - M
     double* ring;           // M x 4 x plane samples
     double* acc;            // 8 x plane accumulators (re, im of Ex, Ey, Bx, By)
     int64_t onaxis_id;
-    double* onaxis_out;
+    double* onaxis_series;  // on-axis E_x of step n goes to entry n
 };
+// The power of step n goes to series[n] once the window is complete.
 template <typename real>
 cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const PowerStep& ps, double scale,
-                              double* partial, int npartial, double* out, cudaStream_t st);
+                              double* partial, int npartial, double* series, cudaStream_t st);
 template <typename real>
 cudaError_t launch_energy(const Fields6<real>& eb, const Geom& g, double* partial, int npartial, double* out,
                           cudaStream_t st);

@@ -53,7 +53,13 @@ extern "C" int mithra_set_allocator(mithra_alloc_fn alloc, mithra_free_fn free_f
 }
 
 static std::atomic<int64_t> g_launches{0};
-void mithra::count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local int64_t t_launches = 0;   // this thread's launches (graph capture counts its nodes)
+void mithra::count_launches(int64_t n)
+{
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
+static int64_t launch_count() { return t_launches; }
 extern "C" int64_t mithra_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" const char* mithra_last_error(void) { return g_err.c_str(); }
@@ -201,7 +207,6 @@ struct RunT final : mithra_run {
     Particles<real> P{}, T{};
     SortScratch ss{};
     double* ring = nullptr;
-    double* phase_cs = nullptr;
     double* acc = nullptr;      // running DFT accumulators of the power plane
     double* partial = nullptr;
     int npartial = 304;
@@ -216,6 +221,14 @@ struct RunT final : mithra_run {
     float4* ptab32[2] = {nullptr, nullptr};  // FP32-mixed path: phase and edge distances rounded to FP32
     TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
     int* err_word = nullptr;   // set by a kernel whose bounded wait expired
+    StepDev* sd = nullptr;     // per-step values derived on the device from the step counter
+    StepConst scst{};
+    // captured steps: one graph of glen steps replayed from every aligned step
+    static constexpr int64_t kGraphMaxSteps = 480;
+    bool use_graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t glen = 0;
+    int64_t gnodes = 0;
 
     int lev(int k) const { return (base + k) % 3; }
 
@@ -288,11 +301,10 @@ struct RunT final : mithra_run {
         const size_t plane = (size_t)g.nx * g.ny;
         npartial = std::max<int>(304, (int)((plane + 255) / 256));
         ring = (double*)mem.get((size_t)M * 4 * plane * 8);
-        phase_cs = (double*)mem.get((size_t)2 * M * 8);
         acc = (double*)mem.get((size_t)8 * plane * 8);
         partial = (double*)mem.get((size_t)4 * npartial * 8);   // energy: [0, n); bunching: [n, 3n)
         small = (double*)mem.get(8 * 8);
-        if (!ring || !phase_cs || !acc || !partial || !small)
+        if (!ring || !acc || !partial || !small)
             return fail(MITHRA_ENOMEM, "device allocation failed (diagnostics)");
         CU(cudaMemsetAsync(ring, 0, (size_t)M * 4 * plane * 8, stream));
         CU(cudaMemsetAsync(acc, 0, (size_t)8 * plane * 8, stream));
@@ -307,6 +319,17 @@ struct RunT final : mithra_run {
         }
         if (!(err_word = (int*)mem.get(sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (error word)");
         CU(cudaMemsetAsync(err_word, 0, sizeof(int), stream));
+        if (!(sd = (StepDev*)mem.get(sizeof(StepDev)))) return fail(MITHRA_ENOMEM, "device allocation failed (step state)");
+        CU(cudaMemsetAsync(sd, 0, sizeof(StepDev), stream));   // the counter starts at step 0
+        scst.T0 = d.T0;
+        scst.dt = d.dt;
+        scst.g0 = d.g0;
+        scst.b0 = d.b0;
+        scst.z0 = d.z0;
+        scst.omega_h = d.omega_h;
+        scst.M = (int)d.M;
+        const char* no_graph = std::getenv("MITHRA_NO_GRAPHS");
+        use_graphs = !(no_graph && no_graph[0] == '1');
         const char* no_tma = std::getenv("MITHRA_NO_TMA");
         if (!(no_tma && no_tma[0] == '1')) tma = make_tma_maps<real>(pot, src, g);
         int rc = full_box(nstep % 2);
@@ -324,6 +347,7 @@ struct RunT final : mithra_run {
         if (!np_ || !ne_) return fail(MITHRA_ENOMEM, "device allocation failed (series)");
         CU(cudaMemsetAsync(np_, 0, (size_t)cap * 8, stream));
         CU(cudaMemsetAsync(ne_, 0, (size_t)cap * 8, stream));
+        graph_reset();   // the captured steps write into the old series
         if (ser_cap) {
             CU(cudaMemcpyAsync(np_, ser_p, (size_t)ser_cap * 8, cudaMemcpyDeviceToDevice, stream));
             CU(cudaMemcpyAsync(ne_, ser_e, (size_t)ser_cap * 8, cudaMemcpyDeviceToDevice, stream));
@@ -373,113 +397,192 @@ struct RunT final : mithra_run {
         return MITHRA_OK;
     }
 
-    int step(int64_t nsteps) override
+    // One field step (launches only).  Host state advanced here: the level ring, the step count
+    // and, on sort steps, the particle buffers.
+    int one_step()
     {
-        int rc = grow_series(nstep + nsteps);
-        if (rc) return rc;
         const int ncomp = g.space_charge ? 4 : 3;
         Fields6<real> E6;
         for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
         Fields4<real> S4;
         for (int c = 0; c < 4; ++c) S4.c[c] = src[c];
-        for (int64_t s = 0; s < nsteps; ++s) {
-            const int64_t n = nstep;
-            if (sort_every > 0 && n > 0 && n % sort_every == 0 && np > 1) {
-                if ((rc = sort_now())) return rc;
+        int rc = MITHRA_OK;
+        const int64_t n = nstep;
+        CU(launch_step_begin(sd, scst, stream));
+        if (sort_every > 0 && n > 0 && n % sort_every == 0 && np > 1) {
+            if ((rc = sort_now())) return rc;
+        }
+        FieldLevels<real> L = levels();
+        cudaEvent_t e0 = nullptr;
+        // E/B where the particles are (and on the power plane); clears the previous sources
+        const EmitBox bx{box[n % 2], box[(n + 1) % 2], (int)d.kp, true};
+        pbeg(MITHRA_K_EMIT, &e0);
+        CU(launch_emit<real>(L, E6, g, bx, stream));
+        pend(MITHRA_K_EMIT, e0);
+        PushConst pc;
+        pc.sd = sd;
+        pc.qJ[0] = d.q / (d.dy * d.dz * d.dt);
+        pc.qJ[1] = d.q / (d.dz * d.dx * d.dt);
+        pc.qJ[2] = d.q / (d.dx * d.dy * d.dt);
+        pc.qrho = d.q / (d.dx * d.dy * d.dz);
+        pc.cdtb[0] = kC * d.dtb / d.dx;
+        pc.cdtb[1] = kC * d.dtb / d.dy;
+        pc.cdtb[2] = kC * d.dtb / d.dz;
+        pc.ptab[0] = ptab[0];
+        pc.ptab[1] = ptab[1];
+        pc.ptab32[0] = ptab32[0];
+        pc.ptab32[1] = ptab32[1];
+        pc.kz = d.g0 * d.dz;
+        pc.zstep = d.g0 * d.b0 * kC * d.dtb;
+        pc.kdz = (float)(ef.ku * pc.kz);
+        pc.kzs = (float)(ef.ku * pc.zstep);
+        pc.x0f = (float)g.x0;
+        pc.y0f = (float)g.y0;
+        pc.dxf = (float)g.dx;
+        pc.dyf = (float)g.dy;
+        pc.dtbf = (float)g.dtb;
+        pc.qrhof = (float)pc.qrho;
+        pc.kuf = (float)ef.ku;
+        pc.cpolf = (float)ef.cpol;
+        pc.spolf = (float)ef.spol;
+        for (int l = 0; l < 3; ++l) {
+            pc.qJf[l] = (float)pc.qJ[l];
+            pc.cdtbf[l] = (float)pc.cdtb[l];
+        }
+        for (int l = 0; l < 4; ++l) {
+            const double qa = fabs(l < 3 ? pc.qJ[l] : pc.qrho);
+            const double sc = qa > 0.0 ? 1073741824.0 / (128.0 * qa) : 1.0;
+            pc.tscale[l] = (float)sc;
+            pc.tunit[l] = (float)(1.0 / (double)pc.tscale[l]);
+        }
+        pc.eB0f = (float)(ef.g0 * ef.b0 * kC * ef.B0);
+        pc.bB0f = (float)(ef.g0 * ef.B0);
+        pc.B0f = (float)ef.B0;
+        pbeg(MITHRA_K_PUSH, &e0);
+        if (ptab[0]) CU(launch_phase_table(ef, sd, pc.kz, g.nz, ptab[0], ptab[1], stream));
+        if (ptab32[0]) CU(launch_phase_table32(ef, sd, pc.kz, g.nz, ptab32[0], ptab32[1], stream));
+        CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
+        pend(MITHRA_K_PUSH, e0);
+        pbeg(MITHRA_K_STENCIL, &e0);
+        if (tma) {
+            real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
+            CU(launch_stencil_tma<real>(tma, outp, lev(1), lev(0), g, cf, ncomp, err_word, stream));
+        } else {
+            CU(launch_stencil<real>(L, g, cf, ncomp, stream));
+        }
+        pend(MITHRA_K_STENCIL, e0);
+        pbeg(MITHRA_K_MUR, &e0);
+        CU(launch_mur<real>(L, g, mur_order, ncomp, stream));
+        pend(MITHRA_K_MUR, e0);
+        pbeg(MITHRA_K_POWER, &e0);
+        {
+            const int M = (int)d.M;
+            PowerStep ps;
+            ps.kp = (int)d.kp;
+            ps.sd = sd;
+            ps.ring = ring;
+            ps.acc = acc;
+            ps.onaxis_id = onaxis_id;
+            ps.onaxis_series = ser_e;
+            const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
+            const double scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
+            if (!ring || !acc || !partial) return fail(MITHRA_EINVAL, "power diagnostic buffers missing");
+            CU(launch_power_step<real>(E6, g, ps, scale, partial, npartial, ser_p, stream));
+        }
+        pend(MITHRA_K_POWER, e0);
+        base = (base + 1) % 3;
+        ++nstep;
+        if (prof && prof_pending.size() > 4096) {
+            CU(cudaStreamSynchronize(stream));
+            prof_collect();
+        }
+        return rc;
+    }
+
+    // Steps per captured graph: the level ring (3), the deposit boxes (2) and the particle
+    // buffers swapped by every sort (2 sort periods) all return to their state after it; 0 when
+    // that period is too long to capture.
+    int64_t graph_period() const
+    {
+        int64_t L = 6;
+        if (sort_every > 0 && np > 1) {
+            const int64_t s2 = 2 * (int64_t)sort_every;
+            int64_t a = L, b = s2;
+            while (b) {
+                const int64_t t = a % b;
+                a = b;
+                b = t;
             }
-            FieldLevels<real> L = levels();
-            cudaEvent_t e0 = nullptr;
-            // E/B where the particles are (and on the power plane); clears the previous sources
-            const EmitBox bx{box[n % 2], box[(n + 1) % 2], (int)d.kp, true};
-            pbeg(MITHRA_K_EMIT, &e0);
-            CU(launch_emit<real>(L, E6, g, bx, stream));
-            pend(MITHRA_K_EMIT, e0);
-            PushConst pc;
-            pc.t_half = d.T0 + ((double)n + 0.5) * d.dt;
-            pc.qJ[0] = d.q / (d.dy * d.dz * d.dt);
-            pc.qJ[1] = d.q / (d.dz * d.dx * d.dt);
-            pc.qJ[2] = d.q / (d.dx * d.dy * d.dt);
-            pc.qrho = d.q / (d.dx * d.dy * d.dz);
-            pc.cdtb[0] = kC * d.dtb / d.dx;
-            pc.cdtb[1] = kC * d.dtb / d.dy;
-            pc.cdtb[2] = kC * d.dtb / d.dz;
-            pc.ptab[0] = ptab[0];
-            pc.ptab[1] = ptab[1];
-            pc.ptab32[0] = ptab32[0];
-            pc.ptab32[1] = ptab32[1];
-            pc.Z0 = d.g0 * (d.z0 + d.b0 * kC * pc.t_half);
-            pc.kz = d.g0 * d.dz;
-            pc.zstep = d.g0 * d.b0 * kC * d.dtb;
-            pc.kdz = (float)(ef.ku * pc.kz);
-            pc.kzs = (float)(ef.ku * pc.zstep);
-            pc.x0f = (float)g.x0;
-            pc.y0f = (float)g.y0;
-            pc.dxf = (float)g.dx;
-            pc.dyf = (float)g.dy;
-            pc.dtbf = (float)g.dtb;
-            pc.qrhof = (float)pc.qrho;
-            pc.kuf = (float)ef.ku;
-            pc.cpolf = (float)ef.cpol;
-            pc.spolf = (float)ef.spol;
-            for (int l = 0; l < 3; ++l) {
-                pc.qJf[l] = (float)pc.qJ[l];
-                pc.cdtbf[l] = (float)pc.cdtb[l];
+            L = L / a * s2;
+        }
+        return L <= kGraphMaxSteps ? L : 0;
+    }
+
+    void graph_reset()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        glen = 0;
+        gnodes = 0;
+    }
+
+    // Capture the L steps from an aligned step (a multiple of L, after the first period) into a
+    // graph and run it.  The capture advances the host state by L steps, exactly as running them
+    // does; the graph then does the device work.
+    int graph_capture_run(int64_t L)
+    {
+        const int base0 = base;
+        const Particles<real> P0 = P;
+        const int64_t l0 = launch_count();
+        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail(MITHRA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        int rc = MITHRA_OK;
+        for (int64_t k = 0; k < L && rc == MITHRA_OK; ++k) rc = one_step();
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamEndCapture(stream, &gr);
+        if (rc != MITHRA_OK || e != cudaSuccess || !gr) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            return rc != MITHRA_OK ? rc : fail(MITHRA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
+        if (base != base0 || P.ix != P0.ix) {
+            cudaGraphDestroy(gr);
+            return fail(MITHRA_ECUDA, "graph capture: the step state is not periodic");
+        }
+        e = cudaGraphInstantiate(&gexec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            gexec = nullptr;
+            return fail(MITHRA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        glen = L;
+        gnodes = launch_count() - l0;
+        CU(cudaGraphLaunch(gexec, stream));
+        return MITHRA_OK;
+    }
+
+    int step(int64_t nsteps) override
+    {
+        int rc = grow_series(nstep + nsteps);
+        if (rc) return rc;
+        int64_t s = 0;
+        while (s < nsteps) {
+            // capture needs a created stream (not the legacy default one)
+            const int64_t L = (use_graphs && !prof && stream) ? graph_period() : 0;
+            if (L > 0 && nstep >= L && nstep % L == 0 && nsteps - s >= L) {
+                if (gexec && glen == L) {
+                    CU(cudaGraphLaunch(gexec, stream));
+                    count_launches(gnodes);
+                    nstep += L;
+                } else {
+                    graph_reset();
+                    if ((rc = graph_capture_run(L))) return rc;
+                }
+                s += L;
+                continue;
             }
-            for (int l = 0; l < 4; ++l) {
-                const double qa = fabs(l < 3 ? pc.qJ[l] : pc.qrho);
-                const double sc = qa > 0.0 ? 1073741824.0 / (128.0 * qa) : 1.0;
-                pc.tscale[l] = (float)sc;
-                pc.tunit[l] = (float)(1.0 / (double)pc.tscale[l]);
-            }
-            pc.eB0f = (float)(ef.g0 * ef.b0 * kC * ef.B0);
-            pc.bB0f = (float)(ef.g0 * ef.B0);
-            pc.B0f = (float)ef.B0;
-            pbeg(MITHRA_K_PUSH, &e0);
-            if (ptab[0]) CU(launch_phase_table(ef, pc.Z0, pc.kz, g.nz, ptab[0], ptab[1], stream));
-            if (ptab32[0]) CU(launch_phase_table32(ef, pc.Z0, pc.kz, g.nz, ptab32[0], ptab32[1], stream));
-            CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
-            pend(MITHRA_K_PUSH, e0);
-            pbeg(MITHRA_K_STENCIL, &e0);
-            if (tma) {
-                real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
-                CU(launch_stencil_tma<real>(tma, outp, lev(1), lev(0), g, cf, ncomp, err_word, stream));
-            } else {
-                CU(launch_stencil<real>(L, g, cf, ncomp, stream));
-            }
-            pend(MITHRA_K_STENCIL, e0);
-            pbeg(MITHRA_K_MUR, &e0);
-            CU(launch_mur<real>(L, g, mur_order, ncomp, stream));
-            pend(MITHRA_K_MUR, e0);
-            pbeg(MITHRA_K_POWER, &e0);
-            {
-                const int M = (int)d.M;
-                PowerStep ps;
-                ps.kp = (int)d.kp;
-                ps.slot = (int)(n % M);
-                ps.full = n >= M ? 1 : 0;
-                ps.emit = n + 1 >= M ? 1 : 0;
-                const double th = d.omega_h * ((double)n + 0.5) * d.dt;
-                const double tho = d.omega_h * ((double)(n - M) + 0.5) * d.dt;
-                ps.cn = std::cos(th);
-                ps.sn = std::sin(th);
-                ps.co = std::cos(tho);
-                ps.so = std::sin(tho);
-                ps.ring = ring;
-                ps.acc = acc;
-                ps.onaxis_id = onaxis_id;
-                ps.onaxis_out = ser_e + n;
-                const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
-                const double scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
-                if (!ring || !acc || !partial) return fail(MITHRA_EINVAL, "power diagnostic buffers missing");
-                CU(launch_power_step<real>(E6, g, ps, scale, partial, npartial, ser_p + n, stream));
-            }
-            pend(MITHRA_K_POWER, e0);
-            base = (base + 1) % 3;
-            ++nstep;
-            if (prof && prof_pending.size() > 4096) {
-                CU(cudaStreamSynchronize(stream));
-                prof_collect();
-            }
+            if ((rc = one_step())) return rc;
+            ++s;
         }
         return MITHRA_OK;
     }
@@ -602,6 +705,7 @@ struct RunT final : mithra_run {
     void destroy_all() override
     {
         if (stream) cudaStreamSynchronize(stream);
+        graph_reset();
         prof_collect();
         free_tma_maps(tma);
         tma = nullptr;

@@ -15,12 +15,12 @@ namespace mithra {
 // step's table (entry of the particle's z cell, in FP64) and rotated by the small angle of the
 // offset within the cell and of the sub-step; cosh / sinh of the small transverse argument from
 // their series.  Same fields as external_field(), evaluated with fewer FP64 operations.
-__device__ __forceinline__ void static_field_fast(const ExtField& f, const PushConst& pc, int iz, double fz, int m,
-                                                  double x, double y, double E[3], double B[3])
+__device__ __forceinline__ void static_field_fast(const ExtField& f, const PushConst& pc, double Z0, int iz, double fz,
+                                                  int m, double x, double y, double E[3], double B[3])
 {
     double Bp[3] = {0.0, 0.0, 0.0};
     const double dzl = fma(pc.kz, fz, (double)m * pc.zstep);   // zeta beyond the cell's node plane
-    const double zn = fma(pc.kz, (double)iz, pc.Z0);           // zeta of the node plane
+    const double zn = fma(pc.kz, (double)iz, Z0);              // zeta of the node plane
     const int nplanar = f.kind == 1 ? 2 : 1;
     for (int j = 0; j < nplanar; ++j) {
         const double c = j ? -f.spol : f.cpol, s = j ? f.cpol : f.spol;
@@ -164,11 +164,11 @@ __device__ __forceinline__ void static_field_mixed(const ExtField& f, const Push
 // the plane's phase k_u u times the FP64 rest-frame amplitudes (gamma0 beta0 c B0, gamma0 B0, B0),
 // and the distances k_u u, k_u (u - L_u) to both ends of the undulator; FP64 throughout, rounded
 // once.
-__global__ void k_phase_table32(ExtField f, double Z0, double kz, int nz, float4* t0, float4* t1)
+__global__ void k_phase_table32(ExtField f, const StepDev* sd, double kz, int nz, float4* t0, float4* t1)
 {
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
     if (iz >= nz) return;
-    const double zn = fma(kz, (double)iz, Z0);
+    const double zn = fma(kz, (double)iz, sd->Z0);
     const double eB0 = f.g0 * f.b0 * kC * f.B0, bB0 = f.g0 * f.B0;
     for (int j = 0; j < (t1 ? 2 : 1); ++j) {
         const double ph = f.ku * (zn - (j ? f.qlam : 0.0));
@@ -180,19 +180,19 @@ __global__ void k_phase_table32(ExtField f, double Z0, double kz, int nz, float4
     }
 }
 
-cudaError_t launch_phase_table32(const ExtField& ef, double Z0, double kz, int nz, float4* t0, float4* t1,
+cudaError_t launch_phase_table32(const ExtField& ef, const StepDev* sd, double kz, int nz, float4* t0, float4* t1,
                                  cudaStream_t st)
 {
-    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, Z0, kz, nz, t0, t1);
+    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, sd, kz, nz, t0, t1);
     count_launches(1);
     return cudaGetLastError();
 }
 
-__global__ void k_phase_table(ExtField f, double Z0, double kz, int nz, double2* t0, double2* t1)
+__global__ void k_phase_table(ExtField f, const StepDev* sd, double kz, int nz, double2* t0, double2* t1)
 {
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
     if (iz >= nz) return;
-    const double zn = fma(kz, (double)iz, Z0);
+    const double zn = fma(kz, (double)iz, sd->Z0);
     double s, c;
     sincos(f.ku * zn, &s, &c);
     t0[iz] = make_double2(s, c);
@@ -202,10 +202,10 @@ __global__ void k_phase_table(ExtField f, double Z0, double kz, int nz, double2*
     }
 }
 
-cudaError_t launch_phase_table(const ExtField& ef, double Z0, double kz, int nz, double2* t0, double2* t1,
+cudaError_t launch_phase_table(const ExtField& ef, const StepDev* sd, double kz, int nz, double2* t0, double2* t1,
                                cudaStream_t st)
 {
-    k_phase_table<<<(nz + 127) / 128, 128, 0, st>>>(ef, Z0, kz, nz, t0, t1);
+    k_phase_table<<<(nz + 127) / 128, 128, 0, st>>>(ef, sd, kz, nz, t0, t1);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -385,7 +385,7 @@ __device__ __forceinline__ void box_merge(int lo[3], int hi[3], int* box_out)
 template <typename real>
 __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3], double u[3], real b[3], int nc[3],
                                          real nf[3], const Geom& g, const ExtField& ef, const Fields6<real>& eb,
-                                         const PushConst& pc)
+                                         const PushConst& pc, double t_half, double Z0)
 {
     double E[3], B[3];    // external field in FP64 (FP64 path, and the general evaluation)
     float Ef[3], Bf[3];   // external field rounded to FP32 (FP32-mixed path)
@@ -401,12 +401,12 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
         if (pc.ptab[0] && ci[2] >= 0 && ci[2] < g.nz) {
             const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
             const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
-            static_field_fast(ef, pc, ci[2], (double)f[2], m, x, y, E, B);
+            static_field_fast(ef, pc, Z0, ci[2], (double)f[2], m, x, y, E, B);
             tab = true;
         }
     }
     if (!tab) {
-        const double t = pc.t_half + (double)m * g.dtb;
+        const double t = t_half + (double)m * g.dtb;
         const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
         const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
         const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
@@ -548,12 +548,13 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
     G.c[3] = src.c[3];
     G.sy = g.sy;
     G.sz = g.sz;
+    const double t_half = pc.sd->t_half, Z0 = pc.sd->Z0;
     bool rho_done = false;
     for (int m = 0; m < g.substeps; ++m) {
         real b[3] = {f[0], f[1], f[2]};
         int nc[3] = {ci[0], ci[1], ci[2]};
         real nf[3] = {f[0], f[1], f[2]};
-        const bool a1 = alive && push_one<real>(m, ci, f, u, b, nc, nf, g, ef, eb, pc);
+        const bool a1 = alive && push_one<real>(m, ci, f, u, b, nc, nf, g, ef, eb, pc, t_half, Z0);
         bool simple = false;   // a move of at most one cell per axis: deposited through the tile
         if (a1 && active_cell(nc[0], nc[1], nc[2], g)) {
 #pragma unroll
