@@ -146,6 +146,7 @@ struct mithra_run {
     virtual int diag(double* fe, double* b3) = 0;
     virtual int series(int which, double* out, size_t cap, size_t* n_out) = 0;
     virtual int sync() = 0;
+    virtual int64_t graph_steps() const = 0;
     virtual void destroy_all() = 0;
 
     // common state
@@ -561,6 +562,8 @@ struct RunT final : mithra_run {
         return MITHRA_OK;
     }
 
+    int64_t graph_steps() const override { return (use_graphs && !prof && stream) ? graph_period() : 0; }
+
     int step(int64_t nsteps) override
     {
         int rc = grow_series(nstep + nsteps);
@@ -568,7 +571,7 @@ struct RunT final : mithra_run {
         int64_t s = 0;
         while (s < nsteps) {
             // capture needs a created stream (not the legacy default one)
-            const int64_t L = (use_graphs && !prof && stream) ? graph_period() : 0;
+            const int64_t L = graph_steps();
             if (L > 0 && nstep >= L && nstep % L == 0 && nsteps - s >= L) {
                 if (gexec && glen == L) {
                     CU(cudaGraphLaunch(gexec, stream));
@@ -961,6 +964,12 @@ extern "C" int mithra_create(const mithra_grid* gr, double dt_lab, const mithra_
         a = g_alloc;
     }
     return mithra::create_with(gr, dt_lab, u, b, a.alloc, a.free_fn, a.ctx, out);
+}
+
+int64_t mithra::graph_steps(mithra_t r, int64_t* nstep)
+{
+    if (nstep) *nstep = r ? r->nstep : 0;
+    return r ? r->graph_steps() : 0;
 }
 
 int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, const mithra_bunch* b, int64_t nsteps)

@@ -16,5 +16,8 @@ int create_with(const mithra_grid* gr, double dt_lab, const mithra_undulator* u,
 void get_allocator(mithra_alloc_fn* alloc, mithra_free_fn* free_fn, void** ctx);
 // Upper bound of the device bytes a run of nsteps steps holds (what admission reserves).
 int64_t footprint(const mithra_grid* gr, const mithra_undulator* u, const mithra_bunch* b, int64_t nsteps);
+// Steps of the run's captured graph (0: steps are launched one by one) and the steps enqueued so
+// far; a call of exactly that many steps from a multiple of it (after the first) is one replay.
+int64_t graph_steps(mithra_t r, int64_t* nstep);
 
 }  // namespace mithra

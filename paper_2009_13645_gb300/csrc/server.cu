@@ -244,7 +244,15 @@ void Server::loop()
                 progress = true;
             }
             if (r->enqueued < r->nsteps && r->inflight.size() < 2) {
-                const int64_t n = std::min<int64_t>(chunk, r->nsteps - r->enqueued);
+                // chunks end on the run's graph boundaries, and a whole graph period from a
+                // boundary goes as one replay
+                int64_t n = std::min<int64_t>(chunk, r->nsteps - r->enqueued);
+                int64_t at = 0;
+                const int64_t L = mithra::graph_steps(r->run, &at);
+                if (L > 0) {
+                    if (at >= L && at % L == 0 && r->nsteps - r->enqueued >= L) n = L;
+                    else n = std::min<int64_t>(n, L - at % L);
+                }
                 int rc = mithra_step(r->run, n);
                 if (rc != MITHRA_OK) {
                     r->enqueued = r->nsteps;
