@@ -113,7 +113,12 @@ int mithra_set_stream(mithra_t run, void *stream);
 /* Enqueue nsteps field steps (>= 0).  One step: E and B at nodes (Sec. "Field Evaluation"),
    external field + gather + Boris + zigzag/CIC deposition (Sec. "Update Algorithm",
    "Current Deposition"), potential update (Eq. updateEquation) and Mur boundaries, the
-   radiated-power sample; a counting sort by cell every sort_every steps. */
+   radiated-power sample; a counting sort by cell every sort_every steps.
+   Every L = lcm(6, 2 sort_every) steps (L <= 480) the run's state returns to the same buffers, so
+   a whole block of L steps starting at a multiple of L (after the first) is captured once into a
+   CUDA graph and replayed; the results are those of launching the steps one by one.  Capture
+   needs a created stream and is skipped while profiling or with MITHRA_NO_GRAPHS=1 in the
+   environment at create time.  Errors: EINVAL, ENOMEM (series growth), ECUDA. */
 int mithra_step(mithra_t run, int64_t nsteps);
 
 /* Wait for the run's stream; returns EDIVERGED if the last field energy is not finite. */
