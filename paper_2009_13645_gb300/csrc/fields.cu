@@ -96,7 +96,7 @@ struct MurArgs {
     int ex[4], ey[4], ez[4];
     int ncomp;
     int order;
-    double cdt, dt, D[3];
+    int face0;           // first face handled (2: the TMA stencil wrote the x faces)
     // face coefficients per normal axis, in the storage type: first order beta_0 (= beta_4),
     // beta_1 (= beta_3); second order gamma_0, gamma_1 and the tangential gammas of the axes
     // (a+1)%3 and (a+2)%3
@@ -105,13 +105,15 @@ struct MurArgs {
 
 __device__ inline int64_t lin(int i, int j, int k, int64_t sy, int64_t sz) { return (int64_t)k * sz + (int64_t)j * sy + i; }
 
-// One face per blockIdx.z (axis = z / 2, side = z % 2), one component per blockIdx.y.
+// One face per blockIdx.z (axis = f / 2, side = f % 2 with f = face0 + z), one component per
+// blockIdx.y.
 template <typename real>
 __global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
 {
     const int comp = blockIdx.y;
     if (comp >= a.ncomp) return;
-    const int ax = blockIdx.z >> 1, sd = blockIdx.z & 1;
+    const int f = a.face0 + (int)blockIdx.z;
+    const int ax = f >> 1, sd = f & 1;
     const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
     const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;   // tangential axes, u before v
     const int nu = e[u] - 2, nv = e[v] - 2;
@@ -127,35 +129,40 @@ __global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
     real* __restrict__ n1 = a.n1[comp];
     const real* __restrict__ n0 = a.n0[comp];
     const real* __restrict__ nm = a.nm[comp];
-    real vout;
-    if (a.order == 1) {
-        const real b0 = a.f0[ax], b1 = a.f1[ax];
-        vout = b0 * (nm[ib] + n1[iq]) + b1 * (n0[ib] + n0[iq]) - nm[iq];
-    } else {
+    real sa = (real)0, sb = (real)0;
+    if (a.order != 1) {
         // tangential neighbours at level n on the face and on the inner plane
         const int ta = (ax + 1) % 3, tb = (ax + 2) % 3;
-        const real ga = a.ft[ax][0], gb = a.ft[ax][1];
-        const real sa = n0[ib + st[ta]] + n0[ib - st[ta]] + n0[iq + st[ta]] + n0[iq - st[ta]];
-        const real sb = n0[ib + st[tb]] + n0[ib - st[tb]] + n0[iq + st[tb]] + n0[iq - st[tb]];
-        vout = a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + ga * sa + gb * sb;
+        sa = n0[ib + st[ta]] + n0[ib - st[ta]] + n0[iq + st[ta]] + n0[iq - st[ta]];
+        sb = n0[ib + st[tb]] + n0[ib - st[tb]] + n0[iq + st[tb]] + n0[iq - st[tb]];
     }
-    n1[ib] = vout;
+    // first order: the tangential gammas are zero
+    n1[ib] = a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + a.ft[ax][0] * sa + a.ft[ax][1] * sb;
 }
 
-// Edges (cls = 2) and corners (cls = 3).
+// Edges and corners.  Class 0..2: the edges whose free axis is 0..2 (the two other coordinates
+// on a boundary); class 3: the corners.  The closed-form coefficients of each class (the FP64
+// expression above, divided by sum_a w_a + g) are computed on the host.
 template <typename real>
-__global__ void k_mur_edges(MurArgs<real> a, int64_t sy, int64_t sz, int cls, int64_t maxpts)
+struct MurEdgeCoef {
+    real A[4][8];   // n+1 values of the square / cube points (point 0, the unknown, has none)
+    real B[4][8];   // n-1 values
+    real C[4];      // n values (all points alike)
+};
+
+template <typename real>
+__global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy, int64_t sz,
+                                                  int corners, int64_t maxpts)
 {
     const int comp = blockIdx.y;
     if (comp >= a.ncomp) return;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= maxpts) return;
     const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
-    int p[3], sg[3], axes[3], ns = 0;
-    if (cls == 3) {
-        if (t >= 8) return;
+    int p[3], sg[3], axes[3], ns = 0, cls = 3;
+    if (corners) {
         for (int d = 0; d < 3; ++d) {
-            const int hi = (t >> d) & 1;
+            const int hi = (int)(t >> d) & 1;
             p[d] = hi ? e[d] - 1 : 0;
             sg[ns] = hi ? -1 : 1;
             axes[ns++] = d;
@@ -177,6 +184,7 @@ __global__ void k_mur_edges(MurArgs<real> a, int64_t sy, int64_t sz, int cls, in
                     sg[0] = (p[lo] == 0) ? 1 : -1;
                     sg[1] = (p[hi] == 0) ? 1 : -1;
                     ns = 2;
+                    cls = f;
                     found = true;
                 } else {
                     t -= len;
@@ -189,27 +197,16 @@ __global__ void k_mur_edges(MurArgs<real> a, int64_t sy, int64_t sz, int cls, in
     const real* __restrict__ n0 = a.n0[comp];
     const real* __restrict__ nm = a.nm[comp];
     const int npts = 1 << ns;
-    const double h = (double)(npts >> 1);
-    double wa[3], wsum = 0.0;
-    for (int s = 0; s < ns; ++s) {
-        wa[s] = 1.0 / (2.0 * a.dt * a.D[axes[s]] * h);
-        wsum += wa[s];
-    }
-    const double g = (double)ns / (kC * a.dt * a.dt * (double)npts);
-    double num = 0.0;
+    real num = (real)0;
     for (int ei = 0; ei < npts; ++ei) {
         int q[3] = {p[0], p[1], p[2]};
-        double W = 0.0;
-        for (int s = 0; s < ns; ++s) {
-            const bool on = (ei >> s) & 1;
-            if (on) q[axes[s]] += sg[s];
-            W += on ? wa[s] : -wa[s];
-        }
+        for (int s = 0; s < ns; ++s)
+            if ((ei >> s) & 1) q[axes[s]] += sg[s];
         const int64_t id = lin(q[0], q[1], q[2], sy, sz);
-        if (ei != 0) num += (double)n1[id] * (W - g);
-        num += -(double)nm[id] * (W + g) + 2.0 * g * (double)n0[id];
+        if (ei != 0) num += cf.A[cls][ei] * n1[id];
+        num += cf.B[cls][ei] * nm[id] + cf.C[cls] * n0[id];
     }
-    n1[lin(p[0], p[1], p[2], sy, sz)] = (real)(num / (wsum + g));
+    n1[lin(p[0], p[1], p[2], sy, sz)] = num;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -219,6 +216,13 @@ __global__ void k_mur_edges(MurArgs<real> a, int64_t sy, int64_t sz, int cls, in
 // push kernel reduced from the cells it deposited into) and the power plane are needed; inside
 // that box the sources of the previous step are cleared in the same pass.  With box == null the
 // whole interior is emitted (diagnostics) and nothing is cleared.
+//
+// One block owns a 32 x 8 tile of node columns and marches a short run of z planes.  Each plane
+// of the six potentials and phi is read once, with a one-node halo, into shared memory; the
+// node-averaged sums S_c = <A_c^n> + <A_c^{n+1}> of the plane are formed once per node there;
+// the z neighbours (S_x, S_y and phi at k -+ 1) stay in registers, so plane k is finished while
+// plane k+1 is being read.  The next plane's loads are issued before the current plane is
+// computed.
 // ---------------------------------------------------------------------------------------
 template <typename real>
 struct EmitArgs {
@@ -228,75 +232,198 @@ struct EmitArgs {
     real* eb[6];
     real* src[4];        // sources to clear inside the box (entries may be null)
     real idt, i2dx, i2dy, i2dz;
-    int kchunk;
+    int nchunk;          // blocks along z covering the box; a further z slice emits plane kp
     int kp;              // plane emitted in full (< 0: none)
     const int* box;      // cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit; null: whole grid
     int* box_reset;      // box the next push reduces into: reset to empty here (may be null)
 };
 
+constexpr int EX = 32, EY = 8, EKZ = 8;              // tile and planes per block
+constexpr int RW = EX + 2, RH = EY + 2, RN = RW * RH; // region: columns i0-1 .. i0+32, rows j0-1 .. j0+8
+constexpr int EHALO = 2 * RW + 2 * EY;                // region positions outside the tile
+constexpr int ENT = EX * EY;                          // threads per block
+static_assert(EHALO <= ENT, "emit tile: one halo position per thread at most");
+
+// Shared memory of one block: raw[p % ENS] holds A_x^n, A_x^{n+1}, A_y^n, A_y^{n+1}, A_z^n,
+// A_z^{n+1}, phi of plane p over the region, filled by asynchronous copies ENS - 1 planes ahead;
+// sum[p & 1] the node-averaged sums S_x, S_y, S_z of plane p.
+constexpr int ENS = 4;
 template <typename real>
-__device__ __forceinline__ real navg(const real* __restrict__ A, int64_t id, int64_t back)
+struct EmitSmem {
+    real raw[ENS][7][RN];
+    real sum[2][3][RN];
+};
+
+// Region position of halo entry h: the rows above and below the tile, then the columns left
+// and right of it.
+__device__ __forceinline__ int halo_pos(int h)
 {
-    return (real)0.5 * (__ldg(A + id) + __ldg(A + id - back));
+    if (h < RW) return h;
+    if (h < 2 * RW) return (RH - 1) * RW + (h - RW);
+    if (h < 2 * RW + EY) return (h - 2 * RW + 1) * RW;
+    return (h - 2 * RW - EY + 1) * RW + RW - 1;
 }
 
+// Asynchronous global -> shared copy of one value; n = 0 writes zero and reads nothing.
 template <typename real>
-__global__ void __launch_bounds__(256) k_emit(EmitArgs<real> a, Geom g)
+__device__ __forceinline__ void cp_async_val(real* dst, const real* src, bool in)
 {
-    const int i0 = 1 + blockIdx.x * blockDim.x, j0 = 1 + blockIdx.y * blockDim.y;
-    const int k0 = 1 + blockIdx.z * a.kchunk;
-    const int k1 = min(g.nz - 2, k0 + a.kchunk - 1);
-    if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < 6 && threadIdx.y == 0)
-        a.box_reset[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if (sizeof(real) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(in ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename real>
+__global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2) k_emit(EmitArgs<real> a, Geom g)
+{
+    extern __shared__ __align__(16) unsigned char emit_smem[];
+    EmitSmem<real>& sm = *reinterpret_cast<EmitSmem<real>*>(emit_smem);
+    const int t = threadIdx.x, tx = t % EX, ty = t / EX;
+    if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t < 6)
+        a.box_reset[t] = t < 3 ? 0x7fffffff : (int)0x80000000;
     // nodes [lo - 1, hi + 2] around the cells of the last deposit: the particles gather at their
     // cells' nodes next step, and with sub-steps they move up to one cell during that step
     int bl[3] = {1, 1, 1}, bh[3] = {g.nx - 2, g.ny - 2, g.nz - 2};
     if (a.box) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            bl[d] = __ldg(a.box + d) - 1;
-            bh[d] = __ldg(a.box + 3 + d) + 2;
+            bl[d] = max(__ldg(a.box + d) - 1, 1);
+            bh[d] = min(__ldg(a.box + 3 + d) + 2, d == 0 ? g.nx - 2 : (d == 1 ? g.ny - 2 : g.nz - 2));
         }
     }
-    const bool plane_here = a.kp >= k0 && a.kp <= k1;
-    const bool box_here = bl[0] <= min(bh[0], i0 + (int)blockDim.x - 1) && bh[0] >= i0 &&
-                          bl[1] <= min(bh[1], j0 + (int)blockDim.y - 1) && bh[1] >= j0 && bl[2] <= min(bh[2], k1) &&
-                          bh[2] >= k0;
-    if (!plane_here && !box_here) return;
-    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (i > g.nx - 2 || j > g.ny - 2) return;
-    const bool col_in = i >= bl[0] && i <= bh[0] && j >= bl[1] && j <= bh[1];
+    const bool plane_slice = (int)blockIdx.z == a.nchunk;   // the power plane, whole interior
+    int xl = 1, xh = g.nx - 2, yl = 1, yh = g.ny - 2, ka, kb;
+    if (plane_slice) {
+        ka = kb = a.kp;
+    } else {
+        xl = bl[0], xh = bh[0], yl = bl[1], yh = bh[1];
+        ka = max(1 + (int)blockIdx.z * EKZ, bl[2]);
+        kb = min((int)(blockIdx.z + 1) * EKZ, bh[2]);
+    }
+    // tiles start at the region's corner, so a box that is not aligned to the tile grid costs no
+    // extra tiles (the grid has enough blocks for the whole interior)
+    const int i0 = xl + (int)blockIdx.x * EX, j0 = yl + (int)blockIdx.y * EY;
+    if (ka > kb || xl > xh || yl > yh || i0 > xh || j0 > yh) return;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool emit = i >= xl && i <= xh && j >= yl && j <= yh;
+    // with a box, the plane slice leaves the box's nodes to the box blocks
+    const bool skip_xy = plane_slice && a.box && i >= bl[0] && i <= bh[0] && j >= bl[1] && j <= bh[1];
+    const bool clear = a.box && !plane_slice;
     const int64_t sy = g.sy, sz = g.sz;
-    const int64_t back[3] = {1, sy, sz};
-    for (int k = k0; k <= k1; ++k) {
-        const bool in = col_in && k >= bl[2] && k <= bh[2];
-        if (!in && k != a.kp) continue;
-        const int64_t id = (int64_t)k * sz + (int64_t)j * sy + i;
-        if (in && a.box) {
+
+    // region positions of this thread: its node, and a halo position for the first EHALO threads
+    const int qo = (ty + 1) * RW + tx + 1;
+    const bool has_halo = t < EHALO;
+    const int qh = has_halo ? halo_pos(t) : qo;
+    // which sums the halo position needs: S_x on the rows above / below the tile, S_y on the
+    // columns left / right of it, S_z and phi on both
+    const bool hrow = has_halo && t < 2 * RW && (qh % RW) != 0;
+    const bool hcol = has_halo && t >= 2 * RW;
+    auto offset = [&](int q, bool& in) -> int64_t {
+        const int ii = i0 - 1 + q % RW, jj = j0 - 1 + q / RW;
+        in = ii <= g.nx - 1 && jj <= g.ny - 1;
+        return in ? (int64_t)jj * sy + ii : 0;
+    };
+    bool in_o, in_h;
+    const int64_t off_o = offset(qo, in_o), off_h = offset(qh, in_h);
+    const real* srcs[7] = {a.a0[0], a.a1[0], a.a0[1], a.a1[1], a.a0[2], a.a1[2], a.phi ? a.phi : a.a0[0]};
+    const bool use_phi = a.phi != nullptr;
+    // copies of plane p into its stage, one commit group per plane (empty past the last plane)
+    auto issue = [&](int p) {
+        if (p <= kb + 1) {
+            real(*st)[RN] = sm.raw[p % ENS];
+            const int64_t pz = (int64_t)p * sz;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (a.src[c]) a.src[c][id] = (real)0;
-        }
-        real E[3];
+            for (int c = 0; c < 7; ++c) cp_async_val(&st[c][qo], srcs[c] + pz + off_o, in_o && (c < 6 || use_phi));
+            if (has_halo) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) E[c] = (navg(a.a0[c], id, back[c]) - navg(a.a1[c], id, back[c])) * a.idt;
-        if (a.phi) {
-            E[0] -= (__ldg(a.phi + id + 1) - __ldg(a.phi + id - 1)) * a.i2dx;
-            E[1] -= (__ldg(a.phi + id + sy) - __ldg(a.phi + id - sy)) * a.i2dy;
-            E[2] -= (__ldg(a.phi + id + sz) - __ldg(a.phi + id - sz)) * a.i2dz;
+                for (int c = 0; c < 7; ++c)
+                    cp_async_val(&st[c][qh], srcs[c] + pz + off_h, in_h && (c < 6 || use_phi));
+            }
         }
-        // node-averaged sums of the two levels, S_c = A_c^n + A_c^{n+1}, at the six neighbours
-        auto S = [&](int c, int64_t at) { return navg(a.a0[c], at, back[c]) + navg(a.a1[c], at, back[c]); };
-        const real bx = (S(2, id + sy) - S(2, id - sy)) * a.i2dy - (S(1, id + sz) - S(1, id - sz)) * a.i2dz;
-        const real by = (S(0, id + sz) - S(0, id - sz)) * a.i2dz - (S(2, id + 1) - S(2, id - 1)) * a.i2dx;
-        const real bz = (S(1, id + 1) - S(1, id - 1)) * a.i2dx - (S(0, id + sy) - S(0, id - sy)) * a.i2dy;
-        a.eb[0][id] = E[0];
-        a.eb[1][id] = E[1];
-        a.eb[2][id] = E[2];
-        a.eb[3][id] = (real)0.5 * bx;
-        a.eb[4][id] = (real)0.5 * by;
-        a.eb[5][id] = (real)0.5 * bz;
+        cp_async_commit();
+    };
+    auto navg = [](real u, real w) { return (real)0.5 * (u + w); };
+
+#pragma unroll
+    for (int d = 0; d < ENS - 1; ++d) issue(ka - 1 + d);
+    // per-column state: A_z at plane p-1 (own and halo position); S_x, S_y, phi at planes p-2 (0)
+    // and p-1 (1); the partial E, B of plane p-1
+    real az0m = 0, az1m = 0, haz0m = 0, haz1m = 0;
+    real sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0, ph0 = 0, ph1 = 0;
+    real ex1 = 0, ey1 = 0, ez1 = 0, bz1 = 0, bxp1 = 0, byp1 = 0;
+    for (int p = ka - 1; p <= kb + 1; ++p) {
+        cp_async_wait<ENS - 2>();   // this thread's copies of plane p have landed
+        __syncthreads();            // everyone's have; everyone is done with plane p-1's stage
+        issue(p + ENS - 1);         // into the stage of plane p-1
+        const real(*r)[RN] = sm.raw[p % ENS];
+        const int b = p & 1;
+        // node averages and sums of plane p at this thread's positions (A_z of the first plane
+        // has no previous plane: its S_z and E_z are never read)
+        const real az0 = r[4][qo], az1 = r[5][qo], php = r[6][qo];
+        const real nx0 = navg(r[0][qo], r[0][qo - 1]), nx1 = navg(r[1][qo], r[1][qo - 1]);
+        const real ny0 = navg(r[2][qo], r[2][qo - RW]), ny1 = navg(r[3][qo], r[3][qo - RW]);
+        const real nz0 = navg(az0, az0m), nz1 = navg(az1, az1m);
+        const real sxp = nx0 + nx1, syp = ny0 + ny1;
+        sm.sum[b][0][qo] = sxp;
+        sm.sum[b][1][qo] = syp;
+        sm.sum[b][2][qo] = nz0 + nz1;
+        az0m = az0;
+        az1m = az1;
+        if (has_halo) {
+            if (hrow) sm.sum[b][0][qh] = navg(r[0][qh], r[0][qh - 1]) + navg(r[1][qh], r[1][qh - 1]);
+            if (hcol) sm.sum[b][1][qh] = navg(r[2][qh], r[2][qh - RW]) + navg(r[3][qh], r[3][qh - RW]);
+            const real h0 = r[4][qh], h1 = r[5][qh];
+            sm.sum[b][2][qh] = navg(h0, haz0m) + navg(h1, haz1m);
+            haz0m = h0;
+            haz1m = h1;
+        }
+        __syncthreads();
+        const real(*S)[RN] = sm.sum[b];
+        const int q = qo;
+        real ex = (nx0 - nx1) * a.idt;
+        real ey = (ny0 - ny1) * a.idt;
+        const real ez = (nz0 - nz1) * a.idt;
+        if (use_phi) {
+            ex -= (r[6][q + 1] - r[6][q - 1]) * a.i2dx;
+            ey -= (r[6][q + RW] - r[6][q - RW]) * a.i2dy;
+        }
+        const real bz = (S[1][q + 1] - S[1][q - 1]) * a.i2dx - (S[0][q + RW] - S[0][q - RW]) * a.i2dy;
+        const real bxp = (S[2][q + RW] - S[2][q - RW]) * a.i2dy;
+        const real byp = (S[2][q + 1] - S[2][q - 1]) * a.i2dx;
+        // plane k = p - 1 has its z neighbours now
+        const int k = p - 1;
+        if (k >= ka && emit && !(skip_xy && k >= bl[2] && k <= bh[2])) {
+            const int64_t id = (int64_t)k * sz + off_o;
+            const real bx = bxp1 - (syp - sy0) * a.i2dz;
+            const real by = (sxp - sx0) * a.i2dz - byp1;
+            real ezk = ez1;
+            if (use_phi) ezk -= (php - ph0) * a.i2dz;
+            a.eb[0][id] = ex1;
+            a.eb[1][id] = ey1;
+            a.eb[2][id] = ezk;
+            a.eb[3][id] = (real)0.5 * bx;
+            a.eb[4][id] = (real)0.5 * by;
+            a.eb[5][id] = (real)0.5 * bz1;
+            if (clear) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (a.src[c]) a.src[c][id] = (real)0;
+            }
+        }
+        sx0 = sx1, sx1 = sxp;
+        sy0 = sy1, sy1 = syp;
+        ph0 = ph1, ph1 = php;
+        ex1 = ex, ey1 = ey, ez1 = ez, bz1 = bz, bxp1 = bxp, byp1 = byp;
+        // sum[b] is next written two planes later, after the first barrier of the next plane,
+        // which every thread reaches only once it is done with it
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -333,10 +460,74 @@ cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const Sten
     return cudaGetLastError();
 }
 
+MurFaceCoef mur_face_coef(const Geom& g, int order)
+{
+    MurFaceCoef m;
+    const double cdt = kC * g.dt, D3[3] = {g.dx, g.dy, g.dz};
+    for (int ax = 0; ax < 3; ++ax) {
+        const double D = D3[ax], den = 1.0 / (cdt + D);
+        if (order == 1) {
+            m.f0[ax] = (cdt - D) * den;            // beta_0 = beta_4
+            m.f1[ax] = 2.0 * D * den;              // beta_1 = beta_3
+            m.ft[ax][0] = m.ft[ax][1] = 0.0;
+        } else {
+            const int ta = (ax + 1) % 3, tb = (ax + 2) % 3;
+            const double ra = (cdt / D3[ta]) * (cdt / D3[ta]), rb = (cdt / D3[tb]) * (cdt / D3[tb]);
+            m.f0[ax] = (cdt - D) * den;            // gamma_0 = gamma_4
+            m.f1[ax] = D * (2.0 - ra - rb) * den;  // gamma_1 = gamma_3
+            m.ft[ax][0] = 0.5 * ra * D * den;      // gamma of the (ax+1) neighbours
+            m.ft[ax][1] = 0.5 * rb * D * den;      // gamma of the (ax+2) neighbours
+        }
+    }
+    return m;
+}
+
+// Edge (class f: free axis f) and corner (class 3) coefficients of the closed form, in FP64,
+// divided by its denominator and rounded once to the storage type.
 template <typename real>
-cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, cudaStream_t st)
+static MurEdgeCoef<real> mur_edge_coef(const Geom& g)
+{
+    MurEdgeCoef<real> c{};
+    const double D3[3] = {g.dx, g.dy, g.dz};
+    for (int cls = 0; cls < 4; ++cls) {
+        int axes[3], ns = 0;
+        if (cls == 3) {
+            axes[0] = 0;
+            axes[1] = 1;
+            axes[2] = 2;
+            ns = 3;
+        } else {
+            const int u = (cls + 1) % 3, v = (cls + 2) % 3;
+            axes[0] = u < v ? u : v;
+            axes[1] = u < v ? v : u;
+            ns = 2;
+        }
+        const int npts = 1 << ns;
+        const double h = (double)(npts >> 1);
+        double wa[3], wsum = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            wa[s] = 1.0 / (2.0 * g.dt * D3[axes[s]] * h);
+            wsum += wa[s];
+        }
+        const double gg = (double)ns / (kC * g.dt * g.dt * (double)npts);
+        const double inv = 1.0 / (wsum + gg);
+        for (int ei = 0; ei < npts; ++ei) {
+            double W = 0.0;
+            for (int s = 0; s < ns; ++s) W += ((ei >> s) & 1) ? wa[s] : -wa[s];
+            c.A[cls][ei] = (real)(ei != 0 ? (W - gg) * inv : 0.0);
+            c.B[cls][ei] = (real)(-(W + gg) * inv);
+        }
+        c.C[cls] = (real)(2.0 * gg * inv);
+    }
+    return c;
+}
+
+template <typename real>
+cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
+                       cudaStream_t st)
 {
     MurArgs<real> a;
+    a.face0 = x_faces_done ? 2 : 0;
     for (int c = 0; c < 4; ++c) {
         a.n1[c] = L.out[c];
         a.n0[c] = L.n1[c];
@@ -347,41 +538,33 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     }
     a.ncomp = ncomp;
     a.order = order;
-    a.cdt = kC * g.dt;
-    a.dt = g.dt;
-    a.D[0] = g.dx;
-    a.D[1] = g.dy;
-    a.D[2] = g.dz;
+    const MurFaceCoef m = mur_face_coef(g, order);
     for (int ax = 0; ax < 3; ++ax) {
-        const double D = a.D[ax], cdt = a.cdt, den = 1.0 / (cdt + D);
-        if (order == 1) {
-            a.f0[ax] = (real)((cdt - D) * den);            // beta_0 = beta_4
-            a.f1[ax] = (real)(2.0 * D * den);              // beta_1 = beta_3
-            a.ft[ax][0] = a.ft[ax][1] = (real)0;
-        } else {
-            const int ta = (ax + 1) % 3, tb = (ax + 2) % 3;
-            const double ra = (cdt / a.D[ta]) * (cdt / a.D[ta]), rb = (cdt / a.D[tb]) * (cdt / a.D[tb]);
-            a.f0[ax] = (real)((cdt - D) * den);            // gamma_0 = gamma_4
-            a.f1[ax] = (real)(D * (2.0 - ra - rb) * den);  // gamma_1 = gamma_3
-            a.ft[ax][0] = (real)(0.5 * ra * D * den);      // gamma of the (ax+1) neighbours
-            a.ft[ax][1] = (real)(0.5 * rb * D * den);      // gamma of the (ax+2) neighbours
-        }
+        a.f0[ax] = (real)m.f0[ax];
+        a.f1[ax] = (real)m.f1[ax];
+        a.ft[ax][0] = (real)m.ft[ax][0];
+        a.ft[ax][1] = (real)m.ft[ax][1];
     }
-    int64_t maxface = 0;
-    for (int c = 0; c < ncomp; ++c) {
-        const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
-        for (int ax = 0; ax < 3; ++ax) {
-            const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
-            maxface = std::max<int64_t>(maxface, (e[u] - 2) * (e[v] - 2));
+    int nl = 0;
+    {
+        int64_t maxface = 0;
+        for (int c = 0; c < ncomp; ++c) {
+            const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
+            for (int ax = 0; ax < 3; ++ax) {
+                const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
+                maxface = std::max<int64_t>(maxface, (e[u] - 2) * (e[v] - 2));
+            }
         }
+        const int thr = 256;
+        k_mur_faces<real>
+            <<<dim3((unsigned)((maxface + thr - 1) / thr), ncomp, 6 - a.face0), thr, 0, st>>>(a, g.sy, g.sz);
+        ++nl;
     }
-    const int64_t nx = g.nx, ny = g.ny, nz = g.nz;
-    const int64_t edges = 4 * ((nx - 2) + (ny - 2) + (nz - 2));
-    const int thr = 256;
-    k_mur_faces<real><<<dim3((unsigned)((maxface + thr - 1) / thr), ncomp, 6), thr, 0, st>>>(a, g.sy, g.sz);
-    k_mur_edges<real><<<dim3((unsigned)((edges + thr - 1) / thr), ncomp), thr, 0, st>>>(a, g.sy, g.sz, 2, edges);
-    k_mur_edges<real><<<dim3(1, ncomp), 32, 0, st>>>(a, g.sy, g.sz, 3, 8);
-    count_launches(3);
+    const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
+    const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
+    k_mur_edges<real><<<dim3((unsigned)((edges + 63) / 64), ncomp), 64, 0, st>>>(a, ec, g.sy, g.sz, 0, edges);
+    k_mur_edges<real><<<dim3(1, ncomp), 64, 0, st>>>(a, ec, g.sy, g.sz, 1, 8);
+    count_launches(nl + 2);
     return cudaGetLastError();
 }
 
@@ -402,22 +585,23 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     a.i2dx = (real)(0.5 / g.dx);
     a.i2dy = (real)(0.5 / g.dy);
     a.i2dz = (real)(0.5 / g.dz);
-    a.kchunk = 16;
     a.kp = bx.kp;
     a.box = bx.box;
     a.box_reset = bx.box_reset;
-    a.kchunk = bx.box ? 4 : 16;   // short z chunks spread the box over more blocks
-    const dim3 blk(32, 8);
-    const dim3 grd((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, (g.nz - 2 + a.kchunk - 1) / a.kchunk);
-    k_emit<real><<<grd, blk, 0, st>>>(a, g);
+    a.nchunk = (g.nz - 2 + EKZ - 1) / EKZ;
+    const dim3 grd((g.nx - 2 + EX - 1) / EX, (g.ny - 2 + EY - 1) / EY, a.nchunk + (a.kp >= 1 ? 1 : 0));
+    static const cudaError_t attr = cudaFuncSetAttribute(k_emit<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)sizeof(EmitSmem<real>));
+    if (attr != cudaSuccess) return attr;
+    k_emit<real><<<grd, ENT, sizeof(EmitSmem<real>), st>>>(a, g);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_stencil<float>(const FieldLevels<float>&, const Geom&, const StencilCoef&, int, cudaStream_t);
 template cudaError_t launch_stencil<double>(const FieldLevels<double>&, const Geom&, const StencilCoef&, int, cudaStream_t);
-template cudaError_t launch_mur<float>(const FieldLevels<float>&, const Geom&, int, int, cudaStream_t);
-template cudaError_t launch_mur<double>(const FieldLevels<double>&, const Geom&, int, int, cudaStream_t);
+template cudaError_t launch_mur<float>(const FieldLevels<float>&, const Geom&, int, int, bool, cudaStream_t);
+template cudaError_t launch_mur<double>(const FieldLevels<double>&, const Geom&, int, int, bool, cudaStream_t);
 template cudaError_t launch_emit<float>(const FieldLevels<float>&, const Fields6<float>&, const Geom&, const EmitBox&,
                                         cudaStream_t);
 template cudaError_t launch_emit<double>(const FieldLevels<double>&, const Fields6<double>&, const Geom&,

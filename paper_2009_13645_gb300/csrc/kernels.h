@@ -34,12 +34,34 @@ struct TmaMaps;
 template <typename real>
 TmaMaps* make_tma_maps(real* const pot[3][4], real* const src[4], const Geom& g);
 void free_tma_maps(TmaMaps* m);
+// Mur face coefficients (Sec. "First/Second Order ABCs") per normal axis a: the boundary value
+//   psi_b^{n+1} = f0 (psi_b^{n-1} + psi_q^{n+1}) + f1 (psi_b^n + psi_q^n) - psi_q^{n-1}
+//               + ft[a][0] S_{(a+1)%3} + ft[a][1] S_{(a+2)%3},
+// q the inward neighbour of b, S_t the four level-n neighbours along axis t of b and q.
+struct MurFaceCoef {
+    double f0[3], f1[3], ft[3][2];
+};
+MurFaceCoef mur_face_coef(const Geom& g, int order);
+
+// With `mur` (not null: the run's Mur coefficients) and FP32 storage the stencil also writes the
+// Mur values of the interior nodes of the x faces (x = 0 and x = ex - 1) of every lattice it
+// updates; tma_x_faces<real>() tells whether it does.
 template <typename real>
-cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], int lev_n, int lev_m, const Geom& g,
-                               const StencilCoef& cf, int ncomp, int* err, cudaStream_t st);
+cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* const prev[4], const MurFaceCoef* mur,
+                               int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp, int* err,
+                               cudaStream_t st);
 
 template <typename real>
-cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, cudaStream_t st);
+constexpr bool tma_x_faces()
+{
+    return sizeof(real) == 4;
+}
+
+// Mur boundary values of level n+1: the faces, then the edges, then the corners.  With
+// x_faces_done the TMA stencil of this step has already written the x faces.
+template <typename real>
+cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
+                       cudaStream_t st);
 // Region of one E/B emission: box == null emits the whole interior and clears nothing.
 struct EmitBox {
     const int* box;      // device: cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit

@@ -221,6 +221,7 @@ struct RunT final : mithra_run {
     double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables, FP64 path (one per planar field)
     float4* ptab32[2] = {nullptr, nullptr};  // FP32-mixed path: phase and edge distances rounded to FP32
     TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
+    MurFaceCoef murc{};        // Mur face coefficients (the FP32 TMA stencil writes the x faces)
     int* err_word = nullptr;   // set by a kernel whose bounded wait expired
     StepDev* sd = nullptr;     // per-step values derived on the device from the step counter
     StepConst scst{};
@@ -333,6 +334,7 @@ struct RunT final : mithra_run {
         use_graphs = !(no_graph && no_graph[0] == '1');
         const char* no_tma = std::getenv("MITHRA_NO_TMA");
         if (!(no_tma && no_tma[0] == '1')) tma = make_tma_maps<real>(pot, src, g);
+        murc = mur_face_coef(g, mur_order);
         int rc = full_box(nstep % 2);
         if (rc) return rc;
         return grow_series(1024);
@@ -467,13 +469,14 @@ struct RunT final : mithra_run {
         pbeg(MITHRA_K_STENCIL, &e0);
         if (tma) {
             real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
-            CU(launch_stencil_tma<real>(tma, outp, lev(1), lev(0), g, cf, ncomp, err_word, stream));
+            real* prevp[4] = {pot[lev(0)][0], pot[lev(0)][1], pot[lev(0)][2], pot[lev(0)][3]};
+            CU(launch_stencil_tma<real>(tma, outp, prevp, &murc, lev(1), lev(0), g, cf, ncomp, err_word, stream));
         } else {
             CU(launch_stencil<real>(L, g, cf, ncomp, stream));
         }
         pend(MITHRA_K_STENCIL, e0);
         pbeg(MITHRA_K_MUR, &e0);
-        CU(launch_mur<real>(L, g, mur_order, ncomp, stream));
+        CU(launch_mur<real>(L, g, mur_order, ncomp, tma != nullptr && tma_x_faces<real>(), stream));
         pend(MITHRA_K_MUR, e0);
         pbeg(MITHRA_K_POWER, &e0);
         {

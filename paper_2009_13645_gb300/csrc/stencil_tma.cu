@@ -9,7 +9,14 @@
 // into a ring of NST shared-memory stages, NST - 1 planes ahead of the plane being computed.
 // Each thread owns one column and keeps planes k-1, k, k+1 of its column and of its four
 // transverse neighbours in registers, reading only the new plane k+1 from shared memory.  Results
-// go straight to global memory (coalesced rows).  Every wait on an mbarrier has an iteration limit;
+// go straight to global memory (coalesced rows).
+//
+// In FP32 the threads next to an x boundary also write the Mur value of the face node beside them
+// (Sec. "First/Second Order ABCs"): every input of the face formula is already in their registers
+// or in the staged tiles, whereas a separate face kernel reads one 32-byte sector per row for two
+// useful values.  In FP64 that lane's arithmetic would occupy the FP64 pipe for a whole warp
+// instruction (GB300's FP64 rate is low and the FP64 stencil is bound by it), so there the faces
+// stay in their own kernel.  Every wait on an mbarrier has an iteration limit;
 // on expiry the CTA records an error word, waits (again bounded) for its copies in flight, and
 // returns.
 #include <cuda.h>
@@ -95,6 +102,9 @@ struct TmaMaps {
 template <typename real>
 struct TmaArgs {
     real* out[4];
+    const real* prev[4];       // psi^{n-1} arrays (read where a staged tile does not reach)
+    int mur;                   // Mur order of the x faces written here (0: none)
+    real mf0, mf1, mfy, mfz;   // their coefficients: f0, f1 and the tangential gammas along y, z
     int lev_n, lev_m;          // ring levels of psi^n and psi^{n-1}
     int ex[4], ey[4], ez[4];
     int ncomp;
@@ -193,8 +203,23 @@ __global__ void __launch_bounds__(TX * TY) k_stencil_tma(const __grid_constant__
             const real bxm = a.w * (xm0 + xm2) + a.w0 * xm1;
             const real byp = a.w * (yp0 + yp2) + a.w0 * yp1;
             const real bym = a.w * (ym0 + ym2) + a.w0 * ym1;
-            o[(int64_t)k * sz + (int64_t)y * sy + x] =
-                a.a1 * c1 - pm + a.ax * (bxp + bxm) + a.ay * (byp + bym) + a.a6 * (c0 + c2) + s * sr;
+            const real v = a.a1 * c1 - pm + a.ax * (bxp + bxm) + a.ay * (byp + bym) + a.a6 * (c0 + c2) + s * sr;
+            o[(int64_t)k * sz + (int64_t)y * sy + x] = v;
+            if (tma_x_faces<real>() && a.mur && (x == 1 || x == ex - 2)) {
+                // Mur x face: b = x -+ 1 on the boundary, q = x its inward neighbour (the formula
+                // and the summation order of k_mur_faces)
+                const int64_t row = (int64_t)k * sz + (int64_t)y * sy;
+                const real* pk = (const real*)(stk + T::OFF_PREV) + ty * TX + tx;
+                const int db = x == 1 ? -1 : 1;
+                const real n0b = x == 1 ? xm1 : xp1;
+                const real nmb = (tx + db < TX) ? pk[db] : a.prev[comp][row + x + db];
+                real sa = (real)0, sb = (real)0;
+                if (a.mur != 1) {
+                    sa = halo_at(k, db, 1) + halo_at(k, db, -1) + yp1 + ym1;
+                    sb = (x == 1 ? xm2 : xp2) + (x == 1 ? xm0 : xp0) + c2 + c0;
+                }
+                o[row + x + db] = a.mf0 * (nmb + v) + a.mf1 * (n0b + c1) - pm + a.mfy * sa + a.mfz * sb;
+            }
         }
         c0 = c1; c1 = c2;
         xp0 = xp1; xp1 = xp2;
@@ -283,8 +308,9 @@ TmaMaps* make_tma_maps(real* const pot[3][4], real* const src[4], const Geom& g)
 void free_tma_maps(TmaMaps* m) { delete m; }
 
 template <typename real>
-cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], int lev_n, int lev_m, const Geom& g,
-                               const StencilCoef& cf, int ncomp, int* err, cudaStream_t st)
+cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* const prev[4], const MurFaceCoef* mur,
+                               int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp, int* err,
+                               cudaStream_t st)
 {
     using T = Tile<real>;
     static bool attr_set = false;
@@ -296,6 +322,7 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], int lev_
     TmaArgs<real> a;
     for (int c = 0; c < 4; ++c) {
         a.out[c] = out[c];
+        a.prev[c] = prev[c];
         a.ex[c] = g.nx - (c == 0);
         a.ey[c] = g.ny - (c == 1);
         a.ez[c] = g.nz - (c == 2);
@@ -311,6 +338,11 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], int lev_
     a.w = (real)cf.w;
     a.w0 = (real)cf.w0;
     a.err = err;
+    a.mur = (mur && tma_x_faces<real>()) ? ((mur->ft[0][0] != 0.0 || mur->ft[0][1] != 0.0) ? 2 : 1) : 0;
+    a.mf0 = mur ? (real)mur->f0[0] : (real)0;
+    a.mf1 = mur ? (real)mur->f1[0] : (real)0;
+    a.mfy = mur ? (real)mur->ft[0][0] : (real)0;
+    a.mfz = mur ? (real)mur->ft[0][1] : (real)0;
     const int nchunk = (g.nz - 2 + KZ - 1) / KZ;
     const dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, nchunk * ncomp);
     k_stencil_tma<real><<<grd, TX * TY, T::SMEM, st>>>(*maps, a, g.sy, g.sz);
@@ -322,9 +354,10 @@ template bool tma_supported<float>(const Geom&);
 template bool tma_supported<double>(const Geom&);
 template TmaMaps* make_tma_maps<float>(float* const[3][4], float* const[4], const Geom&);
 template TmaMaps* make_tma_maps<double>(double* const[3][4], double* const[4], const Geom&);
-template cudaError_t launch_stencil_tma<float>(const TmaMaps*, float* const[4], int, int, const Geom&,
-                                               const StencilCoef&, int, int*, cudaStream_t);
-template cudaError_t launch_stencil_tma<double>(const TmaMaps*, double* const[4], int, int, const Geom&,
-                                                const StencilCoef&, int, int*, cudaStream_t);
+template cudaError_t launch_stencil_tma<float>(const TmaMaps*, float* const[4], float* const[4], const MurFaceCoef*,
+                                               int, int, const Geom&, const StencilCoef&, int, int*, cudaStream_t);
+template cudaError_t launch_stencil_tma<double>(const TmaMaps*, double* const[4], double* const[4],
+                                                const MurFaceCoef*, int, int, const Geom&, const StencilCoef&, int,
+                                                int*, cudaStream_t);
 
 }  // namespace mithra
