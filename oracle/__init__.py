@@ -52,6 +52,7 @@ class Params(C.Structure):
         ("n_periods", C.c_double), ("pol_deg", C.c_double), ("waist", C.c_double),
         ("pulse_fwhm", C.c_double), ("signal", C.c_int32), ("dist_head", C.c_double),
         ("gamma", C.c_double), ("charge_e", C.c_double), ("sig_z", C.c_double),
+        ("gap", C.c_double), ("n_modules", C.c_int32), ("taper", C.c_double),
     ]
 
 
@@ -104,6 +105,7 @@ def params_from(w, periodic=(0, 0, 0)) -> Params:
     p.und_kind, p.K, p.lambda_u, p.n_periods = w.und_kind, w.K, w.lambda_u, w.n_periods
     p.pol_deg, p.waist, p.pulse_fwhm, p.signal = w.pol_deg, w.waist, w.pulse_fwhm, w.signal
     p.dist_head, p.gamma, p.charge_e, p.sig_z = w.dist_head, w.gamma, w.charge_e, w.sig_z
+    p.gap, p.n_modules, p.taper = w.gap, w.n_modules, w.taper
     return p
 
 

@@ -119,7 +119,8 @@ orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np)
     /* rest frame: gamma0 = gamma / sqrt(1 + K^2/2) for a planar undulator or a
        linearly polarised laser (a0 as K); helical: gamma / sqrt(1 + K^2). */
     double g0 = p->gamma;
-    if (p->und_kind == 0 || p->und_kind == 2 || p->und_kind == 3) g0 = p->gamma / sqrt(1.0 + 0.5 * p->K * p->K);
+    if (p->und_kind == 0 || p->und_kind == 2 || p->und_kind == 3 || p->und_kind == 4)
+        g0 = p->gamma / sqrt(1.0 + 0.5 * p->K * p->K);   /* array: the first module's K */
     else if (p->und_kind == 1) g0 = p->gamma / sqrt(1.0 + p->K * p->K);
     r->gamma0 = g0;
     r->beta0 = sqrt(1.0 - 1.0 / (g0 * g0));
@@ -151,14 +152,14 @@ orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np)
     r->B0 = 2.0 * PI * ME * C0 * p->K / (QE * p->lambda_u);
     r->kL = 2.0 * PI / p->lambda_u;
     r->E0 = p->K * ME * C0 * (C0 * r->kL) / QE;
-    if (p->und_kind == 0 || p->und_kind == 1) r->kstar = g0 * r->beta0 * r->ku;
+    if (p->und_kind == 0 || p->und_kind == 1 || p->und_kind == 4) r->kstar = g0 * r->beta0 * r->ku;
     else if (p->und_kind == 2 || p->und_kind == 3) r->kstar = g0 * (1.0 + r->beta0) * r->kL;
     else r->kstar = 2.0 * PI / p->lambda_u;
     r->omega_h = p->norm_freq * C0 * r->kstar;
     /* bunching wavenumber: the rest-frame ponderomotive wave, pump + radiation
        (static: gamma0 k_u + k*; optical: 2 k*).  It is the lab resonant bunching
        wavenumber seen from the rest frame. */
-    if (p->und_kind == 0 || p->und_kind == 1) r->kb = g0 * r->ku + r->kstar;
+    if (p->und_kind == 0 || p->und_kind == 1 || p->und_kind == 4) r->kb = g0 * r->ku + r->kstar;
     else if (p->und_kind == 2 || p->und_kind == 3) r->kb = 2.0 * r->kstar;
     else r->kb = r->kstar;
 
@@ -166,7 +167,7 @@ orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np)
        entrance).  A static undulator starts with its entrance dist_head/gamma0 ahead of the
        bunch head (head = centre + 3 sig_z) in the rest frame; an optical undulator
        starts with the bunch reference at the origin. */
-    if (p->und_kind == 0 || p->und_kind == 1) {
+    if (p->und_kind == 0 || p->und_kind == 1 || p->und_kind == 4) {
         const double h = 3.0 * p->sig_z;
         r->zeta_ref = -(p->dist_head + g0 * g0 * h);
     } else {
@@ -504,6 +505,53 @@ static void planar_field(const orc_run *r, double th, double off, double xl, dou
     Bp[2] += Bz;
 }
 
+/* Window of the fringe fields inside a gap of length g (Eq. fringingFieldGap): 1 at the end of
+   the module (dz = 0), about 6e-5 at the far end of the gap (dz = g). */
+static double gap_window(double dz, double g)
+{
+    const double a = PI * dz / g;
+    return 0.35875 + 0.48829 * cos(a) + 0.14128 * cos(2.0 * a) + 0.01168 * cos(3.0 * a);
+}
+
+/* Static undulator array (Sec. "Static Undulator Array Field"; Sec. UNDULATOR,
+   static-undulator-array): n_modules planar modules of length L = n_periods lambda_u, module i
+   starting at i (L + gap) with undulator parameter K_i = K + i taper.  Each module contributes
+   the field of Eq. undulatorField in its own coordinate u (from its entrance) inside [0, L], and
+   outside the fringe of Eq. fringingField with dz the distance to its nearer end: undamped where
+   no module follows on that side (before the first entrance, after the last exit), damped by the
+   window f(dz, gap) of Eq. fringingFieldGap inside a gap and zero beyond it.  The field is the
+   sum over all modules.  Module i owns [0, L) of its coordinate and the last module [0, L]. */
+static void array_field(const orc_run *r, double th, double xl, double yl, double zeta, double Bp[3])
+{
+    const double ku = r->ku, L = r->Lu, gap = r->p.gap;
+    const int N = r->p.n_modules;
+    const double ct = cos(th), st = sin(th);
+    const double yu = -xl * st + yl * ct;
+    for (int i = 0; i < N; ++i) {
+        const double Ki = r->p.K + i * r->p.taper;
+        const double B0i = 2.0 * PI * ME * C0 * Ki / (QE * r->p.lambda_u);
+        const double u = zeta - i * (L + gap);
+        double s = 0.0, c = 0.0;
+        if (u >= 0.0 && (u < L || (i == N - 1 && u <= L))) {
+            s = sin(ku * u);
+            c = cos(ku * u);
+        } else {
+            const double dz = u < 0.0 ? u : u - L;
+            const int open = u < 0.0 ? (i == 0) : (i == N - 1);
+            if (open || fabs(dz) < gap) {
+                const double e = exp(-0.5 * (ku * dz) * (ku * dz));
+                const double w = open ? 1.0 : gap_window(dz, gap);
+                s = ku * dz * e * w;
+                c = e * w;
+            }
+        }
+        const double Bb = B0i * cosh(ku * yu) * s;
+        Bp[0] += -Bb * st;
+        Bp[1] += Bb * ct;
+        Bp[2] += B0i * sinh(ku * yu) * c;
+    }
+}
+
 /* Time signature f(t, t0, phi) (Eq. signalTypes) with A0 = 1, t - t0 = tau. */
 static double envelope_signal(const orc_run *r, double tau, double phase)
 {
@@ -527,6 +575,9 @@ void orc_lab_field(const orc_run *r, double xl, double yl, double zeta, double t
     case 1:
         planar_field(r, th, 0.0, xl, yl, zeta, Bp);
         planar_field(r, th + 0.5 * PI, 0.25 * r->p.lambda_u, xl, yl, zeta, Bp);
+        break;
+    case 4:
+        array_field(r, th, xl, yl, zeta, Bp);
         break;
     case 2:
     case 3: {

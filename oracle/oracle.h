@@ -45,7 +45,8 @@ typedef struct orc_params {
     double plane_dist;        /* lab distance of the power plane ahead of the bunch reference */
     double norm_freq;         /* normalised frequency h of the power diagnostic */
     /* undulator (Sec. UNDULATOR) */
-    int32_t und_kind;         /* -1 none, 0 planar static, 1 helical static, 2 optical plane wave, 3 optical Gaussian */
+    int32_t und_kind;         /* -1 none, 0 planar static, 1 helical static, 2 optical plane wave, 3 optical Gaussian,
+                                 4 static undulator array */
     double K;                 /* undulator parameter, or a0 for an optical undulator */
     double lambda_u;          /* period, or laser wavelength */
     double n_periods;
@@ -58,6 +59,11 @@ typedef struct orc_params {
     double gamma;             /* mean Lorentz factor (sets the rest frame) */
     double charge_e;          /* electrons in the bunch */
     double sig_z;             /* lab rms length: the head sits 3 sig_z ahead of the centre */
+    /* static undulator array (Sec. UNDULATOR, static-undulator-array): n_modules planar modules
+       of n_periods periods each, `gap` apart (lab length), K_i = K + i * taper */
+    double gap;
+    int32_t n_modules;
+    double taper;
 } orc_params;
 
 typedef struct orc_run orc_run;

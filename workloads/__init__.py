@@ -51,7 +51,8 @@ class Workload:
     mur_order: int
     space_charge: int
     substeps: int
-    und_kind: int        # 0 planar, 1 helical, 2 optical plane wave, 3 optical Gaussian beam, -1 none
+    und_kind: int        # 0 planar, 1 helical, 2 optical plane wave, 3 optical Gaussian beam,
+                         # 4 static undulator array, -1 none
     K: float             # undulator parameter K, or a0 for an optical undulator
     lambda_u: float      # undulator period, or laser wavelength
     n_periods: float
@@ -78,6 +79,9 @@ class Workload:
     steps: int
     seed: int
     precision: int = 0   # 0 FP64 plain, 1 FP32-mixed
+    gap: float = 0.0     # undulator array: lab gap between modules
+    n_modules: int = 1   # undulator array: number of modules of n_periods each
+    taper: float = 0.0   # undulator array: K_i = K + i * taper
 
 
 def lab_bunch(w: Workload, n: Optional[int] = None, seed: Optional[int] = None) -> np.ndarray:
@@ -150,6 +154,18 @@ WORKLOADS = {
         charge_e=100e-12 / 1.602176634e-19, n_particles=2_000_000,
         lambda_r=1.782e-6, shot_noise=1, quiet=1,
         plane_dist=0.3 * 512 * 9.900980e-8, steps=2000, seed=1236, precision=1),
+    # The FEL run through an undulator line: four 12-period modules two periods apart, the
+    # undulator parameter tapered by -0.005 per module (Sec. UNDULATOR, static-undulator-array).
+    "fel_array_128x128x512": _w(
+        name="fel_array_128x128x512", nx=128, ny=128, nz=512,
+        dx=1.055448e-5, dy=1.055448e-5, dz=9.900980e-8,
+        und_kind=4, K=1.4, lambda_u=0.018, n_periods=12, dist_head=0.036,
+        gap=0.036, n_modules=4, taper=-0.005,
+        gamma=100.0, rel_espread=1e-4, sig_x=50e-6, sig_y=50e-6, sig_z=7e-6,
+        sig_ux=0.02, sig_uy=0.02,
+        charge_e=100e-12 / 1.602176634e-19, n_particles=2_000_000,
+        lambda_r=1.782e-6, shot_noise=1, quiet=1,
+        plane_dist=0.3 * 512 * 9.900980e-8, steps=2000, seed=1240, precision=1),
     # Large single run: 256x256x1024, 32M particles, helical undulator, 1% bunching.
     "helical_256x256x1024": _w(
         name="helical_256x256x1024", nx=256, ny=256, nz=1024,
