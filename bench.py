@@ -230,6 +230,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--workload", default=WORKLOAD, help="workload name from workloads.WORKLOADS")
+    ap.add_argument("--no-array", action="store_true", help="skip the undulator-array workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -264,11 +265,13 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    def timed_run(precision: int, steps: int, sample_clocks: bool):
+    def timed_run(precision: int, steps: int, sample_clocks: bool, wl=None, labl=None):
         """K timed steps as a user runs them (captured graphs replayed), then K more steps with
         CUDA events around every kernel (launched one by one) for the per-kernel times."""
+        wl = w if wl is None else wl
+        labl = lab if labl is None else labl
         stream = torch.cuda.Stream()
-        run = m.Run.from_workload(w, lab, precision=precision, stream=stream.cuda_stream)
+        run = m.Run.from_workload(wl, labl, precision=precision, stream=stream.cuda_stream)
         run.step(W)
         run.sync()
         barrier()
@@ -308,6 +311,22 @@ def main():
         res64 = {"value": ws * cells * K64 / (ms64 * 1e-3), "unit": "cell-updates/s",
                  "particle_pushes_per_s": ws * w.n_particles * K64 / (ms64 * 1e-3), "ms_per_step": ms64 / K64,
                  "steps": K64, "kernel_ms_per_step": {k: v[0] / K64 for k, v in stats64.items() if v[1]}}
+
+    # ---- the same step through an undulator line (modules, gaps, taper) ----------------------
+    arr = None
+    if not args.no_array:
+        wa = workloads.WORKLOADS["fel_array_128x128x512"]
+        laba = workloads.lab_bunch(wa)
+        msa, statsa, _, _, _, _ = timed_run(1, K, False, wa, laba)
+        msa = reduce_max(msa)
+        ca = wa.nx * wa.ny * wa.nz
+        arr = {"workload": wa.name, "value": ws * ca * K / (msa * 1e-3), "unit": "cell-updates/s",
+               "particle_pushes_per_s": ws * wa.n_particles * K / (msa * 1e-3), "ms_per_step": msa / K,
+               "steps": K, "precision": "fp32-mixed",
+               "undulator": f"{wa.n_modules} modules x {wa.n_periods:g} periods, gap {wa.gap:g} m, "
+                            f"K = {wa.K:g} + i x {wa.taper:g}",
+               "kernel_ms_per_step": {k: v[0] / K for k, v in statsa.items() if v[1]}}
+        del laba
 
     # ---- end to end through the C ABI from pinned host memory -------------------------------
     pinned = torch.empty(lab.shape, dtype=torch.float64, pin_memory=True)
@@ -404,6 +423,7 @@ def main():
         "kernel_times": f"CUDA events around each kernel over {K} further steps launched one by one "
                         f"({ms32_prof / K:.4f} ms/step with the events)",
         "fp64": res64,
+        "undulator_array": arr,
         "roofline": roof,
         "stencil_roofline": stencil_roof,
         "cpu_baseline": cpu,

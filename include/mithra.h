@@ -69,7 +69,8 @@ typedef struct mithra_grid {
 /* Undulator (manual Sec. UNDULATOR, Sec. "Field Initialization"). */
 typedef struct mithra_undulator {
     int32_t kind;              /* -1 none, 0 planar static, 1 helical static (two planar, 90 deg, lambda/4 apart),
-                                  2 optical plane wave, 3 optical Gaussian beam (counter-propagating, -z) */
+                                  2 optical plane wave, 3 optical Gaussian beam (counter-propagating, -z),
+                                  4 static undulator array (Sec. "Static Undulator Array Field") */
     double K;                  /* undulator parameter K, or strength a0 of an optical undulator */
     double lambda;             /* undulator period, or laser wavelength; kind -1: rest-frame diagnostic wavelength */
     double n_periods;          /* static: undulator length in periods */
@@ -78,6 +79,14 @@ typedef struct mithra_undulator {
     double pulse_fwhm;         /* c * tau, intensity FWHM (Eq. signalTypes) */
     int32_t signal;            /* 0 modulated Gaussian, 1 flat-top (Gaussian rise, then constant) */
     double dist_to_bunch_head; /* lab distance from the bunch head to the undulator entrance / pulse */
+    /* kind 4 only (Sec. UNDULATOR, static-undulator-array): n_modules planar modules of n_periods
+       periods each, `gap` (lab length, >= 0) between one module's end and the next entrance,
+       undulator parameter K_i = K + i * taper of module i (K of the first module fixes the rest
+       frame).  Inside a gap both neighbouring fringes (Eq. fringingField) are damped by the
+       window f(dz, gap) of Eq. fringingFieldGap, dz the distance to that module's end. */
+    double gap;
+    int32_t n_modules;         /* 1 .. 100000 */
+    double taper;
 } mithra_undulator;
 
 /* Bunch given as macro-particles (bunch type "file", Sec. BUNCH). */

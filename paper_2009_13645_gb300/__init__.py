@@ -42,7 +42,8 @@ class Grid(C.Structure):
 class Undulator(C.Structure):
     _fields_ = [("kind", C.c_int32), ("K", C.c_double), ("lambda_", C.c_double),
                 ("n_periods", C.c_double), ("pol_deg", C.c_double), ("waist", C.c_double),
-                ("pulse_fwhm", C.c_double), ("signal", C.c_int32), ("dist_to_bunch_head", C.c_double)]
+                ("pulse_fwhm", C.c_double), ("signal", C.c_int32), ("dist_to_bunch_head", C.c_double),
+                ("gap", C.c_double), ("n_modules", C.c_int32), ("taper", C.c_double)]
 
 
 class Bunch(C.Structure):
@@ -240,6 +241,7 @@ def undulator_from(w) -> Undulator:
     u.kind, u.K, u.lambda_, u.n_periods = w.und_kind, w.K, w.lambda_u, w.n_periods
     u.pol_deg, u.waist, u.pulse_fwhm, u.signal = w.pol_deg, w.waist, w.pulse_fwhm, w.signal
     u.dist_to_bunch_head = w.dist_head
+    u.gap, u.n_modules, u.taper = w.gap, w.n_modules, w.taper
     return u
 
 

@@ -32,7 +32,7 @@ struct Geom {
 // Eqs. undulatorField, fringingField, opticalUndulatorPW, opticalUndulatorGB,
 // LorentzTransformR2L, LorentzTransformElectric/Magnetic).
 struct ExtField {
-    int kind;           // -1 none, 0 planar, 1 helical, 2 optical plane wave, 3 optical Gaussian
+    int kind;           // -1 none, 0 planar, 1 helical, 2 optical plane wave, 3 optical Gaussian, 4 array
     double g0, b0;      // rest-frame gamma0, beta0
     double ku, Lu, B0;  // static undulator: wavenumber, length, peak field
     double qlam;        // helical: quarter period offset of the second planar field
@@ -42,6 +42,8 @@ struct ExtField {
     double tp;          // pulse length tau (s); <= 0: continuous
     int signal;         // 0 Gaussian envelope, 1 flat-top
     double w0, zr;      // Gaussian beam waist and Rayleigh length; w0 <= 0: plane wave
+    double gap, dB0;    // undulator array: gap between modules, peak-field step per module
+    int nmod;           // undulator array: number of modules
 };
 
 // Planar static undulator field along (-sin, cos) in the xy-plane starting at lab
@@ -70,6 +72,57 @@ __host__ __device__ inline void planar_add(const ExtField& f, double c, double s
     Bp[2] += f.B0 * sh * cs;
 }
 
+// Window of a fringe inside a gap of length g (Eq. fringingFieldGap).
+__host__ __device__ inline double gap_window(double d, double g)
+{
+    const double a = kPi * d / g;
+    return 0.35875 + 0.48829 * cos(a) + 0.14128 * cos(2.0 * a) + 0.01168 * cos(3.0 * a);
+}
+
+// Static undulator array along (-sin, cos): module i (peak field B0 + i dB0) spans [i P, i P + Lu]
+// with P = Lu + gap.  At most two modules reach a given zeta: the one whose entrance lies at or
+// before it (its interior, or its exit fringe, windowed by Eq. fringingFieldGap inside the gap
+// and undamped after the last module) and the next one (its entrance fringe inside the gap);
+// before the first entrance only the first module's undamped entrance fringe.  Adds to Bp.
+__host__ __device__ inline void array_add(const ExtField& f, double xl, double yl, double zeta, double Bp[3])
+{
+    const double P = f.Lu + f.gap;
+    int i = (int)floor(zeta / P);
+    i = i < -1 ? -1 : (i > f.nmod - 1 ? f.nmod - 1 : i);
+    // keep zeta - i P in [0, P) wherever the floor rounded across a module boundary
+    if (i >= 0 && zeta - i * P < 0.0) --i;
+    if (i < f.nmod - 1 && zeta - (i + 1) * P >= 0.0) ++i;
+    double sn = 0.0, cs = 0.0;   // peak field times the shape, summed over the modules
+    auto fringe = [&](double Bm, double d, bool open) {
+        const double kd = f.ku * d;
+        const double e = exp(-0.5 * kd * kd) * (open ? 1.0 : gap_window(d, f.gap));
+        sn += Bm * kd * e;
+        cs += Bm * e;
+    };
+    if (i < 0) {
+        fringe(f.B0, zeta, true);
+    } else {
+        const double u = zeta - i * P;
+        const double Bi = f.B0 + i * f.dB0;
+        const bool last = i == f.nmod - 1;
+        if (u < f.Lu || (last && u <= f.Lu)) {
+            double s, c;
+            sincos(f.ku * u, &s, &c);
+            sn += Bi * s;
+            cs += Bi * c;
+        } else if (last || u - f.Lu < f.gap) {
+            fringe(Bi, u - f.Lu, last);
+        }
+        if (!last && P - u < f.gap) fringe(Bi + f.dB0, u - P, false);
+    }
+    const double yu = f.cpol * yl - f.spol * xl;
+    const double ky = f.ku * yu;
+    const double Bt = cosh(ky) * sn;
+    Bp[0] -= Bt * f.spol;
+    Bp[1] += Bt * f.cpol;
+    Bp[2] += sinh(ky) * cs;
+}
+
 // Time signature f(tau, phase) of the laser (Eq. signalTypes, A0 = 1).
 __host__ __device__ inline double laser_signal(const ExtField& f, double tau, double phase)
 {
@@ -90,6 +143,8 @@ __host__ __device__ inline void lab_field(const ExtField& f, double xl, double y
         planar_add(f, f.cpol, f.spol, 0.0, xl, yl, zeta, Bp);
         // rotated by +90 degrees: (cos, sin) -> (-sin, cos)
         planar_add(f, -f.spol, f.cpol, f.qlam, xl, yl, zeta, Bp);
+    } else if (f.kind == 4) {
+        array_add(f, xl, yl, zeta, Bp);
     } else if (f.kind == 2 || f.kind == 3) {
         const double tau = (tl - f.t_f) + (zeta - f.zeta_f) / kC;   // counter-propagating (-z)
         double Epar, El = 0.0, Bl = 0.0;

@@ -736,7 +736,8 @@ int derive(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, cons
 {
     const int kind = u.kind;
     double g0 = b.gamma;
-    if (kind == 0 || kind == 2 || kind == 3) g0 = b.gamma / std::sqrt(1.0 + 0.5 * u.K * u.K);
+    // planar (an array's rest frame follows its first module) or linearly polarised laser
+    if (kind == 0 || kind == 2 || kind == 3 || kind == 4) g0 = b.gamma / std::sqrt(1.0 + 0.5 * u.K * u.K);
     else if (kind == 1) g0 = b.gamma / std::sqrt(1.0 + u.K * u.K);
     if (!(g0 >= 1.0)) return fail(MITHRA_EINVAL, "gamma0 < 1: raise gamma or lower K");
     d.g0 = g0;
@@ -787,10 +788,14 @@ int derive(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, cons
     ef.signal = u.signal;
     ef.w0 = (kind == 3) ? u.waist : 0.0;
     ef.zr = (ef.w0 > 0.0) ? kPi * ef.w0 * ef.w0 / lam : 1.0;
-    if (kind == 0 || kind == 1) d.kstar = d.g0 * d.b0 * kk;
+    ef.gap = kind == 4 ? u.gap : 0.0;
+    ef.nmod = kind == 4 ? u.n_modules : 1;
+    ef.dB0 = kind == 4 ? 2.0 * kPi * kMe * kC * u.taper / (kQe * lam) : 0.0;
+    const bool stat = kind == 0 || kind == 1 || kind == 4;
+    if (stat) d.kstar = d.g0 * d.b0 * kk;
     else if (kind == 2 || kind == 3) d.kstar = d.g0 * (1.0 + d.b0) * kk;
     else d.kstar = kk;
-    if (kind == 0 || kind == 1) d.kb = d.g0 * kk + d.kstar;
+    if (stat) d.kb = d.g0 * kk + d.kstar;
     else if (kind == 2 || kind == 3) d.kb = 2.0 * d.kstar;
     else d.kb = d.kstar;
     d.omega_h = gr.norm_freq * kC * d.kstar;
@@ -801,7 +806,7 @@ int derive(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, cons
     // -(dist + gamma0^2 * 3 sig_z) at t' = 0.  Optical: reference at the origin; the pulse centre
     // starts dist ahead and meets the reference at the focus.
     double zeta_ref = 0.0;
-    if (kind == 0 || kind == 1) zeta_ref = -(u.dist_to_bunch_head + d.g0 * d.g0 * 3.0 * b.sig_z);
+    if (stat) zeta_ref = -(u.dist_to_bunch_head + d.g0 * d.g0 * 3.0 * b.sig_z);
     d.z_ref = d.g0 * zeta_ref;
     d.T0 = -d.g0 * d.b0 * zeta_ref / kC;
     ef.t_f = u.dist_to_bunch_head / (kC * (1.0 + d.b0));
@@ -930,7 +935,14 @@ int mithra::validate_request(const mithra_grid* gr, double dt_lab, const mithra_
     if (gr->precision != 0 && gr->precision != 1) return fail(MITHRA_EINVAL, "create: precision must be 0 or 1");
     if (gr->substeps < 0 || gr->substeps > 1024) return fail(MITHRA_EINVAL, "create: substeps out of range");
     if (!(gr->norm_freq > 0)) return fail(MITHRA_EINVAL, "create: norm_freq must be > 0");
-    if (u->kind < -1 || u->kind > 3) return fail(MITHRA_EINVAL, "create: unknown undulator kind");
+    if (u->kind < -1 || u->kind > 4) return fail(MITHRA_EINVAL, "create: unknown undulator kind");
+    if (u->kind == 4) {
+        if (!finite_all({u->gap, u->taper}) || !(u->gap >= 0.0))
+            return fail(MITHRA_EINVAL, "create: undulator array needs a finite gap >= 0 and a finite taper");
+        if (u->n_modules < 1 || u->n_modules > 100000)
+            return fail(MITHRA_EINVAL, "create: undulator array needs 1 .. 100000 modules");
+        if (!(u->n_periods > 0.0)) return fail(MITHRA_EINVAL, "create: undulator array needs n_periods > 0");
+    }
     if (!(u->lambda > 0)) return fail(MITHRA_EINVAL, "create: lambda must be > 0");
     if (!(b->gamma >= 1.0)) return fail(MITHRA_EINVAL, "create: gamma must be >= 1");
     if (b->n < 0 || b->n >= (int64_t(1) << 31)) return fail(MITHRA_EINVAL, "create: particle count out of range");

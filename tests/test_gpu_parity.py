@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import workloads
-from tests.helpers import vacuum
+from tests.helpers import C0, vacuum
 
 pytestmark = pytest.mark.gpu
 
@@ -185,6 +185,35 @@ def test_full_step_fp64_kinds(kind, substeps, solver, order):
     lab = workloads.lab_bunch(w)
     o, g = pair(w, 0, lab=lab)
     _compare_run(o, g, 60, 1e-11, 1e-10, w, lab)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_step_undulator_array(precision):
+    """Static undulator array (one-period modules half a period apart, K tapered by 0.1 per
+    module): within the run the bunch crosses the first module, its exit fringe, the gap with
+    both windowed fringes and the second module's entrance.  FP64: the parity bound; FP32-mixed:
+    the field-energy bound."""
+    base = workloads.WORKLOADS["fel_array_128x128x512"]
+    w = workloads.scaled(base, nx=22, ny=20, nz=40, n_particles=1200, n_periods=1, gap=0.009,
+                         n_modules=3, taper=0.1, substeps=2, sig_z=0.3e-6, dist_head=1e-4,
+                         sig_x=1.5e-5, sig_y=1.5e-5, charge_e=1e7)
+    lab = workloads.lab_bunch(w)
+    o, g = pair(w, precision, lab=lab)
+    steps = 70
+    if precision == 0:
+        _compare_run(o, g, steps, 1e-11, 1e-10, w, lab)
+    else:
+        o.step(steps)
+        g.step(steps)
+        fo, _ = o.diag()
+        fg, _ = g.diag()
+        assert abs(fg - fo) / fo < 1e-4, (fg, fo)
+        po, pg = o.particles(), g.particles()
+        assert np.max(np.abs(pg[:, 3:] - po[:, 3:])) < 1e-5 * np.max(np.abs(po[:, 3:]))
+    inf = o.info()
+    t = inf["T0"] + (steps + 0.5) * inf["dt"]
+    zeta = inf["gamma0"] * (o.particles()[:, 2] + inf["beta0"] * C0 * t)
+    assert np.median(zeta) > w.n_periods * w.lambda_u + w.gap + 0.1 * w.lambda_u
 
 
 def test_full_step_fp32_mixed_bounds():
