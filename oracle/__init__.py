@@ -53,6 +53,7 @@ class Params(C.Structure):
         ("pulse_fwhm", C.c_double), ("signal", C.c_int32), ("dist_head", C.c_double),
         ("gamma", C.c_double), ("charge_e", C.c_double), ("sig_z", C.c_double),
         ("gap", C.c_double), ("n_modules", C.c_int32), ("taper", C.c_double),
+        ("nf_min", C.c_double), ("nf_max", C.c_double), ("nf_points", C.c_int32), ("bunch_every", C.c_int32),
     ]
 
 
@@ -76,6 +77,10 @@ def _load():
             lib.orc_series.restype = C.c_int64
             lib.orc_series.argtypes = [C.c_void_p, dp, dp, dp]
             lib.orc_diag.argtypes = [C.c_void_p, dp, dp]
+            lib.orc_spectrum.restype = C.c_int64
+            lib.orc_spectrum.argtypes = [C.c_void_p, dp, dp]
+            lib.orc_bunch_series.restype = C.c_int64
+            lib.orc_bunch_series.argtypes = [C.c_void_p, dp]
             lib.orc_external_field.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp, dp]
             lib.orc_lab_field.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp, dp]
             lib.orc_boris.argtypes = [dp, dp, dp, C.c_double]
@@ -106,6 +111,7 @@ def params_from(w, periodic=(0, 0, 0)) -> Params:
     p.pol_deg, p.waist, p.pulse_fwhm, p.signal = w.pol_deg, w.waist, w.pulse_fwhm, w.signal
     p.dist_head, p.gamma, p.charge_e, p.sig_z = w.dist_head, w.gamma, w.charge_e, w.sig_z
     p.gap, p.n_modules, p.taper = w.gap, w.n_modules, w.taper
+    p.nf_min, p.nf_max, p.nf_points, p.bunch_every = w.nf_min, w.nf_max, w.nf_points, w.bunch_every
     return p
 
 
@@ -169,6 +175,23 @@ class Run:
         if n:
             self.lib.orc_series(self.h, _dp(p), _dp(t), _dp(e))
         return p, t, e
+
+    def spectrum(self):
+        """(h, p): normalised frequencies (nf) and lab power per step and frequency (steps x nf)."""
+        nf = self.p.nf_points
+        n = self.lib.orc_spectrum(self.h, None, None)
+        h, p = np.zeros(max(nf, 0)), np.zeros((n, max(nf, 0)))
+        if nf and n:
+            self.lib.orc_spectrum(self.h, _dp(h), _dp(p))
+        return h, p
+
+    def bunch_series(self):
+        """Bunch samples (rows x 15), see orc_bunch_series."""
+        n = self.lib.orc_bunch_series(self.h, None)
+        out = np.zeros((n, 15))
+        if n:
+            self.lib.orc_bunch_series(self.h, _dp(out))
+        return out
 
     def diag(self):
         fe, b = C.c_double(), np.zeros(3)

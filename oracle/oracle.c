@@ -67,6 +67,15 @@ struct orc_run {
     double *ring_t;
     int64_t nser, cap;
     double *ser_p, *ser_t, *ser_e;
+    /* spectrum: history of the plane samples (Mh slots) and the power per step and frequency */
+    int nf, Mh;
+    double *hk;
+    int *Mk;
+    double *hist, *hist_t;
+    double *spec;
+    /* bunch samples */
+    int64_t nbs, bcap;
+    double *bser;
 };
 
 static double eps0(void) { return 1.0 / (MU0 * C0 * C0); }
@@ -215,6 +224,21 @@ orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np)
         r->ring = (double *)calloc((size_t)r->M * 4 * p->nx * p->ny, sizeof(double));
         r->ring_t = (double *)calloc((size_t)r->M, sizeof(double));
     }
+    /* spectrum: frequencies h_k and windows M_k = round(2 pi / (h_k w* dt)) */
+    if (p->nf_points > 0) {
+        r->nf = p->nf_points;
+        r->hk = (double *)malloc((size_t)r->nf * sizeof(double));
+        r->Mk = (int *)malloc((size_t)r->nf * sizeof(int));
+        r->Mh = 1;
+        for (int k = 0; k < r->nf; ++k) {
+            r->hk[k] = r->nf == 1 ? p->nf_min : p->nf_min + k * (p->nf_max - p->nf_min) / (r->nf - 1);
+            long Mk = lround(2.0 * PI / (r->hk[k] * C0 * r->kstar * r->dt));
+            r->Mk[k] = (int)(Mk < 1 ? 1 : Mk);
+            if (r->Mk[k] > r->Mh) r->Mh = r->Mk[k];
+        }
+        r->hist = (double *)calloc((size_t)r->Mh * 4 * p->nx * p->ny, sizeof(double));
+        r->hist_t = (double *)calloc((size_t)r->Mh, sizeof(double));
+    }
     return r;
 }
 
@@ -231,6 +255,12 @@ void orc_destroy(orc_run *r)
     free(r->ser_p);
     free(r->ser_t);
     free(r->ser_e);
+    free(r->hk);
+    free(r->Mk);
+    free(r->hist);
+    free(r->hist_t);
+    free(r->spec);
+    free(r->bser);
     free(r);
 }
 
@@ -883,6 +913,95 @@ static void power_sample(orc_run *r)
     r->nser++;
 }
 
+/* Radiated-power spectrum (Sec. FEL-OUTPUT, radiation-power, the normalised-frequency sweep):
+   at every frequency h_k the definition of power_sample with its own window M_k, each
+   recomputed from the stored plane samples of the last M_k steps. */
+static void spectrum_sample(orc_run *r)
+{
+    if (r->nf == 0) return;
+    const int nx = r->nx, ny = r->ny, Mh = r->Mh;
+    const int64_t plane = (int64_t)nx * ny;
+    const int slot = (int)(r->step % Mh);
+    const double ts = ((double)r->step + 0.5) * r->dt;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const int64_t id = IDX(r, i, j, r->kp), pl = (int64_t)j * nx + i;
+            r->hist[((int64_t)slot * 4 + 0) * plane + pl] = r->eb[0][id];
+            r->hist[((int64_t)slot * 4 + 1) * plane + pl] = r->eb[1][id];
+            r->hist[((int64_t)slot * 4 + 2) * plane + pl] = r->eb[3][id];
+            r->hist[((int64_t)slot * 4 + 3) * plane + pl] = r->eb[4][id];
+        }
+    r->hist_t[slot] = ts;
+    r->spec = (double *)realloc(r->spec, (size_t)(r->step + 1) * r->nf * sizeof(double));
+    const double g0 = r->gamma0, b0 = r->beta0;
+    for (int k = 0; k < r->nf; ++k) {
+        const int M = r->Mk[k];
+        const double w = r->hk[k] * C0 * r->kstar;
+        double P = 0.0;
+        if (r->step + 1 >= M) {
+            for (int j = 1; j < ny - 1; ++j)
+                for (int i = 1; i < nx - 1; ++i) {
+                    const int64_t pl = (int64_t)j * nx + i;
+                    double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+                    for (int m = 0; m < M; ++m) {
+                        const int sl = (int)((r->step - m) % Mh);
+                        const double ph = w * r->hist_t[sl];
+                        for (int c = 0; c < 4; ++c) {
+                            const double v = r->hist[((int64_t)sl * 4 + c) * plane + pl];
+                            re[c] += v * cos(ph);
+                            im[c] -= v * sin(ph);
+                        }
+                    }
+                    for (int c = 0; c < 4; ++c) {
+                        re[c] *= 2.0 / M;
+                        im[c] *= 2.0 / M;
+                    }
+                    P += (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
+                }
+            P *= r->dx * r->dy / (2.0 * MU0);
+        }
+        r->spec[r->step * r->nf + k] = g0 * g0 * (1.0 + b0) * (1.0 + b0) * P;
+    }
+}
+
+/* Bunch sampling (Sec. BUNCH, bunch-sampling): mean and rms spread (population) of the
+   rest-frame positions and normalised momenta, and of the lab Lorentz factor
+   gamma0 (gamma + beta0 u_z) (Eq. LorentzTrasnformParticles inverted for the energy), over all
+   particles, in two passes. */
+static void bunch_sample(orc_run *r)
+{
+    if (r->p.bunch_every <= 0 || r->step % r->p.bunch_every != 0) return;
+    if (r->nbs >= r->bcap) {
+        r->bcap = r->bcap ? 2 * r->bcap : 256;
+        r->bser = (double *)realloc(r->bser, (size_t)r->bcap * 15 * sizeof(double));
+    }
+    double *row = r->bser + r->nbs * 15;
+    const double org[3] = {r->x0, r->y0, r->z0};
+    double mean[7] = {0, 0, 0, 0, 0, 0, 0}, var[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int64_t n = r->np;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int64_t p = 0; p < n; ++p) {
+            const double *q = r->pr + 6 * p;
+            double v[7];
+            for (int a = 0; a < 3; ++a) v[a] = q[a] + org[a];
+            for (int a = 0; a < 3; ++a) v[3 + a] = q[3 + a];
+            const double g = sqrt(1.0 + q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+            v[6] = r->gamma0 * (g + r->beta0 * q[5]);
+            for (int c = 0; c < 7; ++c) {
+                if (pass == 0) mean[c] += v[c] / (double)n;
+                else var[c] += (v[c] - mean[c]) * (v[c] - mean[c]) / (double)n;
+            }
+        }
+    row[0] = r->T0 + ((double)r->step + 1.5) * r->dt;
+    for (int a = 0; a < 6; ++a) {
+        row[1 + a] = mean[a];
+        row[7 + a] = sqrt(var[a]);
+    }
+    row[13] = mean[6];
+    row[14] = sqrt(var[6]);
+    r->nbs++;
+}
+
 /* ------------------------------------------------------------------------- */
 
 void orc_step(orc_run *r, int64_t nsteps)
@@ -890,12 +1009,14 @@ void orc_step(orc_run *r, int64_t nsteps)
     for (int64_t s = 0; s < nsteps; ++s) {
         emit_eb(r);
         push_deposit(r);
+        bunch_sample(r);
         for (int c = 0; c < 4; ++c) {
             if (c == 3 && !r->p.space_charge) continue;
             orc_stencil(r, c);
             orc_mur(r, c);
         }
         power_sample(r);
+        spectrum_sample(r);
         orc_rotate_levels(r);
         r->step++;
     }
@@ -969,6 +1090,19 @@ int64_t orc_series(const orc_run *r, double *power_lab, double *t_lab, double *o
     if (t_lab) memcpy(t_lab, r->ser_t, (size_t)r->nser * sizeof(double));
     if (onaxis_ex) memcpy(onaxis_ex, r->ser_e, (size_t)r->nser * sizeof(double));
     return r->nser;
+}
+
+int64_t orc_spectrum(const orc_run *r, double *h_out, double *p_lab)
+{
+    if (h_out && r->nf) memcpy(h_out, r->hk, (size_t)r->nf * sizeof(double));
+    if (p_lab && r->nf) memcpy(p_lab, r->spec, (size_t)r->step * r->nf * sizeof(double));
+    return r->nf ? r->step : 0;
+}
+
+int64_t orc_bunch_series(const orc_run *r, double *out)
+{
+    if (out && r->nbs) memcpy(out, r->bser, (size_t)r->nbs * 15 * sizeof(double));
+    return r->nbs;
 }
 
 /* Neumaier summation */

@@ -64,6 +64,12 @@ typedef struct orc_params {
     double gap;
     int32_t n_modules;
     double taper;
+    /* radiated-power spectrum (Sec. FEL-OUTPUT, radiation-power: minimum / maximum normalised
+       frequency, number of frequency points); nf_points = 0: off */
+    double nf_min, nf_max;
+    int32_t nf_points;
+    /* bunch sampling (Sec. BUNCH, bunch-sampling) every `bunch_every` steps; 0: off */
+    int32_t bunch_every;
 } orc_params;
 
 typedef struct orc_run orc_run;
@@ -91,6 +97,18 @@ int64_t orc_num_particles(const orc_run *r);
 
 /* Per-step series (length = steps taken): lab power (W), lab time (s), on-axis Ex (V/m). */
 int64_t orc_series(const orc_run *r, double *power_lab, double *t_lab, double *onaxis_ex);
+
+/* Radiated-power spectrum: h_out[k] (nf_points) the normalised frequencies h_k = nf_min + k
+   (nf_max - nf_min) / (nf_points - 1), p_lab (steps x nf_points) the lab power at each of them,
+   defined as the series of orc_series with h = h_k and its own window M_k = round(2 pi /
+   (h_k w* dt)).  Returns the number of steps. */
+int64_t orc_spectrum(const orc_run *r, double *h_out, double *p_lab);
+
+/* Bunch samples (rows x 15): rest-frame time of the positions (T0 + (n + 3/2) dt after step n),
+   mean x, y, z (rest frame, m), mean gamma*beta_x,y,z, rms spread of x, y, z and of
+   gamma*beta_x,y,z, mean and rms spread of the lab Lorentz factor gamma0 (gamma + beta0 u_z);
+   taken after the push of every step n with n % bunch_every == 0.  Returns the number of rows. */
+int64_t orc_bunch_series(const orc_run *r, double *out);
 
 /* Diagnostics from the last emitted E/B and the current particles: field energy (J, rest
    frame) and the bunching factor at the rest-frame ponderomotive wavenumber kb:

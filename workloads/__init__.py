@@ -82,6 +82,10 @@ class Workload:
     gap: float = 0.0     # undulator array: lab gap between modules
     n_modules: int = 1   # undulator array: number of modules of n_periods each
     taper: float = 0.0   # undulator array: K_i = K + i * taper
+    nf_min: float = 0.0  # radiated-power spectrum: normalised frequencies nf_min .. nf_max
+    nf_max: float = 0.0
+    nf_points: int = 0   # number of spectrum frequencies (0: no spectrum)
+    bunch_every: int = 0 # bunch sampling every this many steps (0: off)
 
 
 def lab_bunch(w: Workload, n: Optional[int] = None, seed: Optional[int] = None) -> np.ndarray:
