@@ -231,6 +231,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--workload", default=WORKLOAD, help="workload name from workloads.WORKLOADS")
     ap.add_argument("--no-array", action="store_true", help="skip the undulator-array workload")
+    ap.add_argument("--no-diag", action="store_true", help="skip the spectrum / bunch-sampling run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -328,6 +329,18 @@ def main():
                "kernel_ms_per_step": {k: v[0] / K for k, v in statsa.items() if v[1]}}
         del laba
 
+    # ---- the same step with the spectrum sweep and per-step bunch sampling on ----------------
+    diag = None
+    if not args.no_diag:
+        wd = workloads.scaled(w, nf_min=0.5, nf_max=3.5, nf_points=32, bunch_every=1)
+        msd, statsd, _, _, _, _ = timed_run(1, K, False, wd, lab)
+        msd = reduce_max(msd)
+        diag = {"ms_per_step": msd / K, "overhead_ms_per_step": (msd - ms32) / K,
+                "value": ws * cells * K / (msd * 1e-3), "unit": "cell-updates/s",
+                "what": "radiated power at 32 normalised frequencies 0.5 .. 3.5 (own DFT window each) and "
+                        "bunch moments after every step, FP32-mixed",
+                "kernel_ms_per_step": {k: v[0] / K for k, v in statsd.items() if v[1]}}
+
     # ---- end to end through the C ABI from pinned host memory -------------------------------
     pinned = torch.empty(lab.shape, dtype=torch.float64, pin_memory=True)
     pinned.numpy()[:] = lab
@@ -424,6 +437,7 @@ def main():
                         f"({ms32_prof / K:.4f} ms/step with the events)",
         "fp64": res64,
         "undulator_array": arr,
+        "spectrum_and_bunch_sampling": diag,
         "roofline": roof,
         "stencil_roofline": stencil_roof,
         "cpu_baseline": cpu,

@@ -64,6 +64,14 @@ typedef struct mithra_grid {
     double power_plane_dist;   /* lab distance of the radiated-power plane ahead of the bunch (Sec. FEL-OUTPUT) */
     double norm_freq;          /* normalised frequency h of the radiated-power diagnostic */
     int32_t sort_every;        /* counting sort by cell every S steps; 0 = default (20), < 0 = never */
+    /* radiated-power spectrum (Sec. FEL-OUTPUT, radiation-power: minimum-normalized-frequency,
+       maximum-normalized-frequency, number-of-frequency-points): nf_points frequencies
+       h_k = nf_min + k (nf_max - nf_min) / (nf_points - 1) (h_0 = nf_min when nf_points = 1);
+       0 .. 256 points, 0 = no spectrum; each h_k > 0 */
+    double nf_min, nf_max;
+    int32_t nf_points;
+    /* bunch sampling (Sec. BUNCH, bunch-sampling) every bunch_every steps; 0 = off */
+    int32_t bunch_every;
 } mithra_grid;
 
 /* Undulator (manual Sec. UNDULATOR, Sec. "Field Initialization"). */
@@ -170,6 +178,22 @@ int mithra_set_particles(mithra_t run, const double *rest6, size_t rows);
    steps, times gamma0^2 (1+beta0)^2 (Sec. FEL-OUTPUT "radiation-power").
    n_out receives the series length; ERANGE if cap is smaller. */
 int mithra_radiated_power(mithra_t run, double *p_lab, double *t_lab, size_t cap, size_t *n_out);
+
+/* Radiated-power spectrum (Sec. FEL-OUTPUT, radiation-power, the normalised-frequency sweep of
+   mithra_grid.nf_min .. nf_max): for every step n and frequency k, p_lab[n * nf_points + k] is the
+   power of mithra_radiated_power evaluated at h_k with its own window
+   M_k = round(2 pi / (h_k w* dt)) (zero until that window is complete).  h_out (nullable,
+   nf_points values) receives the frequencies.  n_steps receives the number of steps; ERANGE if
+   cap_values < n_steps * nf_points; EINVAL if the run has no spectrum. */
+int mithra_power_spectrum(mithra_t run, double *h_out, double *p_lab, size_t cap_values, size_t *n_steps);
+
+/* Bunch samples (Sec. BUNCH, bunch-sampling), 15 values per row, one row after the push of every
+   step n with n % bunch_every == 0: the rest-frame time of the positions T0 + (n + 3/2) dt (s),
+   the means of x, y, z (rest frame, m) and of gamma*beta_x, gamma*beta_y, gamma*beta_z, the rms
+   spreads (population) of the same six, and the mean and rms spread of the lab Lorentz factor
+   gamma0 (gamma + beta0 gamma*beta_z).  n_rows receives the number of rows; ERANGE if cap_rows is
+   smaller; EINVAL if bunch sampling is off. */
+int mithra_bunch_series(mithra_t run, double *out15, size_t cap_rows, size_t *n_rows);
 
 /* On-axis E_x at the power plane, one value per step (rest frame, V/m). */
 int mithra_onaxis_field(mithra_t run, double *ex, size_t cap, size_t *n_out);

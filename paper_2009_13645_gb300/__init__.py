@@ -36,7 +36,9 @@ class Grid(C.Structure):
                 ("cx", C.c_double), ("cy", C.c_double), ("cz", C.c_double),
                 ("solver", C.c_int32), ("courant", C.c_double), ("mur_order", C.c_int32),
                 ("space_charge", C.c_int32), ("precision", C.c_int32), ("substeps", C.c_int32),
-                ("power_plane_dist", C.c_double), ("norm_freq", C.c_double), ("sort_every", C.c_int32)]
+                ("power_plane_dist", C.c_double), ("norm_freq", C.c_double), ("sort_every", C.c_int32),
+                ("nf_min", C.c_double), ("nf_max", C.c_double), ("nf_points", C.c_int32),
+                ("bunch_every", C.c_int32)]
 
 
 class Undulator(C.Structure):
@@ -80,6 +82,8 @@ def load(rebuild: bool = False):
     L.mithra_set_particles.argtypes = [vp, dp, C.c_size_t]
     L.mithra_radiated_power.argtypes = [vp, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_onaxis_field.argtypes = [vp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.mithra_power_spectrum.argtypes = [vp, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.mithra_bunch_series.argtypes = [vp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_diag.argtypes = [vp, dp, dp]
     L.mithra_info.argtypes = [vp, dp, C.POINTER(C.c_int64)]
     L.mithra_set_profiling.argtypes = [vp, C.c_int]
@@ -233,6 +237,8 @@ def grid_from(w, precision=None, sort_every=0) -> Grid:
     g.substeps = w.substeps
     g.power_plane_dist, g.norm_freq = w.plane_dist, w.norm_freq
     g.sort_every = int(sort_every)
+    g.nf_min, g.nf_max, g.nf_points = w.nf_min, w.nf_max, w.nf_points
+    g.bunch_every = w.bunch_every
     return g
 
 
@@ -330,6 +336,26 @@ class Run:
             _check(self.L.mithra_radiated_power(self.h, _dp(p), _dp(t), n.value, C.byref(n)))
             _check(self.L.mithra_onaxis_field(self.h, _dp(e), n.value, C.byref(n)))
         return p, t, e
+
+    def spectrum(self):
+        """(h, p): the swept normalised frequencies and the lab power per step and frequency."""
+        n = C.c_size_t()
+        nf = int(self.grid.nf_points)
+        h = np.zeros(nf)
+        _check(self.L.mithra_power_spectrum(self.h, _dp(h), None, 0, C.byref(n)))
+        p = np.zeros((n.value, nf))
+        if n.value:
+            _check(self.L.mithra_power_spectrum(self.h, None, _dp(p), p.size, C.byref(n)))
+        return h, p
+
+    def bunch_series(self):
+        """Bunch samples, rows x 15 (see mithra_bunch_series)."""
+        n = C.c_size_t()
+        _check(self.L.mithra_bunch_series(self.h, None, 0, C.byref(n)))
+        out = np.zeros((n.value, 15))
+        if n.value:
+            _check(self.L.mithra_bunch_series(self.h, _dp(out), n.value, C.byref(n)))
+        return out
 
     def diag(self):
         fe = C.c_double()

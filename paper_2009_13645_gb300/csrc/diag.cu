@@ -222,7 +222,204 @@ cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g,
     return cudaGetLastError();
 }
 
+// ---- radiated-power spectrum ------------------------------------------------------------
+__global__ void k_spec_phase(SpecStep s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.nf) return;
+    const int64_t n = s.sd->n;
+    double sn, cn, so, co;
+    sincos(s.omega[k] * ((double)n + 0.5) * s.dt, &sn, &cn);
+    sincos(s.omega[k] * ((double)(n - s.M[k]) + 0.5) * s.dt, &so, &co);
+    s.phase[4 * k + 0] = cn;
+    s.phase[4 * k + 1] = sn;
+    s.phase[4 * k + 2] = co;
+    s.phase[4 * k + 3] = so;
+}
+
+// Every plane point updates the accumulators of every frequency (adding its new sample, and
+// once the frequency's window is full subtracting the sample of step n - M[k] from the ring),
+// then stores its new sample; one partial flux per block and frequency.
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_spec_step(Fields6<real> eb, Geom g, SpecStep s,
+                                                           double* __restrict__ partial)
+{
+    __shared__ double sh[32];
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = s.sd->n;
+    const bool in = pl < plane;
+    double x[4] = {0.0, 0.0, 0.0, 0.0};
+    bool interior = false;
+    if (in) {
+        const int64_t id = (int64_t)s.kp * g.sz + pl;
+        x[0] = (double)eb.c[0][id];
+        x[1] = (double)eb.c[1][id];
+        x[2] = (double)eb.c[3][id];
+        x[3] = (double)eb.c[4][id];
+        const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
+        interior = i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2;
+    }
+    for (int k = 0; k < s.nf; ++k) {
+        const int Mk = s.M[k];
+        const bool full = n >= Mk, emit = n + 1 >= Mk;
+        double contrib = 0.0;
+        if (in) {
+            const double cn = s.phase[4 * k], sn = s.phase[4 * k + 1];
+            const double co = s.phase[4 * k + 2], so = s.phase[4 * k + 3];
+            const double* ro = s.ring + (full ? (int64_t)((n - Mk) % s.Mh) : 0) * 4 * plane + pl;
+            double* ac = s.acc + (int64_t)k * 8 * plane + pl;
+            double re[4], im[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double a = ac[(2 * q) * plane], b = ac[(2 * q + 1) * plane];
+                a += x[q] * cn;
+                b -= x[q] * sn;
+                if (full) {
+                    const double o = ro[q * plane];
+                    a -= o * co;
+                    b += o * so;
+                }
+                ac[(2 * q) * plane] = a;
+                ac[(2 * q + 1) * plane] = b;
+                re[q] = a;
+                im[q] = b;
+            }
+            if (emit && interior) contrib = (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
+        }
+        const double tot = block_sum(contrib, sh);
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * s.nf + k] = tot;
+    }
+    // the leaving samples of every frequency were read above: the new one may take a slot now
+    if (in) {
+        double* r = s.ring + (int64_t)(n % s.Mh) * 4 * plane + pl;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q * plane] = x[q];
+    }
+}
+
+__global__ void k_spec_final(const double* __restrict__ partial, int npartial, SpecStep s, double* __restrict__ series)
+{
+    __shared__ double sh[32];
+    const int64_t n = s.sd->n;
+    for (int k = 0; k < s.nf; ++k) {
+        double sum = 0.0, comp = 0.0;
+        for (int i = threadIdx.x; i < npartial; i += blockDim.x) {
+            const double v = partial[(int64_t)i * s.nf + k];
+            const double t = sum + v;
+            comp += (fabs(sum) >= fabs(v)) ? (sum - t) + v : (v - t) + sum;
+            sum = t;
+        }
+        const double tot = block_sum(sum + comp, sh);
+        if (threadIdx.x == 0) series[n * s.nf + k] = (n + 1 >= s.M[k]) ? tot * s.scale[k] : 0.0;
+    }
+}
+
+template <typename real>
+cudaError_t launch_spectrum_step(const Fields6<real>& eb, const Geom& g, const SpecStep& s, double* partial,
+                                 int npartial, double* series, cudaStream_t st)
+{
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
+    if ((int)nb > npartial || s.nf < 1) return cudaErrorInvalidValue;
+    k_spec_phase<<<(s.nf + 127) / 128, 128, 0, st>>>(s);
+    k_spec_step<real><<<nb, kRedThreads, 0, st>>>(eb, g, s, partial);
+    k_spec_final<<<1, kRedThreads, 0, st>>>(partial, (int)nb, s, series);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+// ---- bunch sampling ------------------------------------------------------------------------
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_bunch_moments(Particles<real> P, int64_t np, Geom g, BunchSample b,
+                                                               double* __restrict__ partial)
+{
+    __shared__ double sh[32];
+    if (b.sd->n % b.every != 0) return;
+    double s1[7] = {0, 0, 0, 0, 0, 0, 0}, s2[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+        const double ux = P.ux[p], uy = P.uy[p], uz = P.uz[p];
+        double v[7];
+        v[0] = g.x0 + ((double)P.ix[p] + (double)P.fx[p]) * g.dx;
+        v[1] = g.y0 + ((double)P.iy[p] + (double)P.fy[p]) * g.dy;
+        v[2] = g.z0 + ((double)P.iz[p] + (double)P.fz[p]) * g.dz;
+        v[3] = ux;
+        v[4] = uy;
+        v[5] = uz;
+        v[6] = b.g0 * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) + b.b0 * uz);
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const double d = v[c] - b.shift[c];
+            s1[c] += d;
+            s2[c] += d * d;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        const double t1 = block_sum(s1[c], sh);
+        const double t2 = block_sum(s2[c], sh);
+        if (threadIdx.x == 0) {
+            partial[(int64_t)blockIdx.x * 14 + c] = t1;
+            partial[(int64_t)blockIdx.x * 14 + 7 + c] = t2;
+        }
+    }
+}
+
+__global__ void k_bunch_row(const double* __restrict__ partial, int npartial, int64_t np, BunchSample b,
+                            double* __restrict__ series)
+{
+    __shared__ double sh[32];
+    __shared__ double tot[14];
+    const int64_t n = b.sd->n;
+    if (n % b.every != 0) return;
+    for (int c = 0; c < 14; ++c) {
+        double sum = 0.0, comp = 0.0;
+        for (int i = threadIdx.x; i < npartial; i += blockDim.x) {
+            const double v = partial[(int64_t)i * 14 + c];
+            const double t = sum + v;
+            comp += (fabs(sum) >= fabs(v)) ? (sum - t) + v : (v - t) + sum;
+            sum = t;
+        }
+        const double t = block_sum(sum + comp, sh);
+        if (threadIdx.x == 0) tot[c] = t;
+    }
+    if (threadIdx.x == 0) {
+        double* row = series + (n / b.every) * 15;
+        const double inv = np > 0 ? 1.0 / (double)np : 0.0;
+        row[0] = b.T0 + ((double)n + 1.5) * b.dt;
+        double mean[7], sd[7];
+        for (int c = 0; c < 7; ++c) {
+            const double m1 = tot[c] * inv;
+            mean[c] = b.shift[c] + m1;
+            sd[c] = sqrt(fmax(tot[7 + c] * inv - m1 * m1, 0.0));
+        }
+        for (int a = 0; a < 6; ++a) {
+            row[1 + a] = mean[a];
+            row[7 + a] = sd[a];
+        }
+        row[13] = mean[6];
+        row[14] = sd[6];
+    }
+}
+
+template <typename real>
+cudaError_t launch_bunch_sample(const Particles<real>& P, int64_t np, const Geom& g, const BunchSample& b,
+                                double* partial, int npartial, double* series, cudaStream_t st)
+{
+    if (b.every < 1) return cudaErrorInvalidValue;
+    int nb = (int)std::min<int64_t>((np + kRedThreads - 1) / kRedThreads, (int64_t)npartial);
+    if (nb < 1) nb = 1;
+    k_bunch_moments<real><<<nb, kRedThreads, 0, st>>>(P, np, g, b, partial);
+    k_bunch_row<<<1, kRedThreads, 0, st>>>(partial, nb, np, b, series);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 #define MITHRA_INST(real)                                                                                              \
+    template cudaError_t launch_spectrum_step<real>(const Fields6<real>&, const Geom&, const SpecStep&, double*, int, \
+                                                    double*, cudaStream_t);                                          \
+    template cudaError_t launch_bunch_sample<real>(const Particles<real>&, int64_t, const Geom&, const BunchSample&, \
+                                                   double*, int, double*, cudaStream_t);                             \
     template cudaError_t launch_energy<real>(const Fields6<real>&, const Geom&, double*, int, double*, cudaStream_t); \
     template cudaError_t launch_bunching<real>(const Particles<real>&, int64_t, const Geom&, double, double*, int,    \
                                                double*, cudaStream_t);

@@ -170,6 +170,42 @@ cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const Powe
 template <typename real>
 cudaError_t launch_energy(const Fields6<real>& eb, const Geom& g, double* partial, int npartial, double* out,
                           cudaStream_t st);
+
+// Radiated-power spectrum (Sec. FEL-OUTPUT, radiation-power, normalised-frequency sweep): for
+// every frequency k the running DFT of the power plane over its own window M[k] of steps.  The
+// plane samples of the last Mh >= max M[k] steps are shared by all frequencies.
+struct SpecStep {
+    int kp;                 // plane index
+    int nf, Mh;             // frequencies, ring depth
+    const StepDev* sd;
+    double dt;
+    const double* omega;    // device, nf rest-frame angular frequencies
+    const int* M;           // device, nf windows
+    const double* scale;    // device, nf: lab factor x (2 / M)^2 x dx dy / (2 mu0)
+    double* ring;           // Mh x 4 x plane samples (Ex, Ey, Bx, By)
+    double* acc;            // nf x 8 x plane accumulators
+    double* phase;          // nf x 4: cos, sin of w t_n and of w t_{n-M}
+};
+// The powers of step n go to series[n * nf + k] (zero until a frequency's window is complete).
+template <typename real>
+cudaError_t launch_spectrum_step(const Fields6<real>& eb, const Geom& g, const SpecStep& s, double* partial,
+                                 int npartial, double* series, cudaStream_t st);
+
+// Bunch sampling (Sec. BUNCH, bunch-sampling): after the push of every step n with n % every == 0
+// the row n / every of `series` (15 values) receives the rest-frame time of the positions
+// T0 + (n + 3/2) dt, the means of x, y, z (rest frame) and gamma*beta_x,y,z, their rms spreads,
+// and the mean and rms spread of the lab Lorentz factor gamma0 (gamma + beta0 u_z).  Sums of
+// FP64 values shifted by `shift` (the mesh centre, zero momentum, the bunch's lab gamma) keep the
+// spreads free of cancellation.
+struct BunchSample {
+    const StepDev* sd;
+    int every;
+    double shift[7];
+    double g0, b0, T0, dt;
+};
+template <typename real>
+cudaError_t launch_bunch_sample(const Particles<real>& P, int64_t np, const Geom& g, const BunchSample& b,
+                                double* partial, int npartial, double* series, cudaStream_t st);
 template <typename real>
 cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g, double kb, double* partial,
                             int npartial, double* out3, cudaStream_t st);

@@ -145,6 +145,8 @@ struct mithra_run {
     virtual int set_particles(const double* in, size_t n) = 0;
     virtual int diag(double* fe, double* b3) = 0;
     virtual int series(int which, double* out, size_t cap, size_t* n_out) = 0;
+    virtual int spectrum(double* h, double* p, size_t cap, size_t* n_steps) = 0;
+    virtual int bunch_samples(double* out, size_t cap_rows, size_t* n_rows) = 0;
     virtual int sync() = 0;
     virtual int64_t graph_steps() const = 0;
     virtual void destroy_all() = 0;
@@ -215,6 +217,22 @@ struct RunT final : mithra_run {
     double* ser_e = nullptr;
     int64_t ser_cap = 0;
     double* small = nullptr;   // 8 doubles of diagnostic output
+    // radiated-power spectrum (nf = 0: off)
+    int nf = 0, Mh = 1;
+    std::vector<double> hk;
+    double* spec_omega = nullptr;
+    int* spec_M = nullptr;
+    double* spec_scale = nullptr;
+    double* spec_ring = nullptr;
+    double* spec_acc = nullptr;
+    double* spec_phase = nullptr;
+    double* spec_partial = nullptr;
+    double* ser_s = nullptr;   // ser_cap x nf
+    // bunch sampling (bunch_every = 0: off)
+    int bunch_every = 0;
+    double bunch_shift_g = 1.0;
+    double* bunch_partial = nullptr;
+    double* ser_b = nullptr;   // rows(ser_cap) x 15
     double* rest_buf = nullptr;
     int64_t onaxis_id = 0;
     int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
@@ -310,6 +328,38 @@ struct RunT final : mithra_run {
             return fail(MITHRA_ENOMEM, "device allocation failed (diagnostics)");
         CU(cudaMemsetAsync(ring, 0, (size_t)M * 4 * plane * 8, stream));
         CU(cudaMemsetAsync(acc, 0, (size_t)8 * plane * 8, stream));
+        if (nf > 0) {
+            std::vector<double> om(nf), sc(nf);
+            std::vector<int> Mv(nf);
+            const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
+            Mh = 1;
+            for (int k = 0; k < nf; ++k) {
+                om[k] = hk[k] * kC * d.kstar;
+                double Mk = std::round(2.0 * kPi / (om[k] * d.dt));
+                if (!(Mk >= 1.0)) Mk = 1.0;
+                if (Mk > 1e6) return fail(MITHRA_EINVAL, "spectrum window longer than 1e6 steps: raise nf_min");
+                Mv[k] = (int)Mk;
+                Mh = std::max(Mh, Mv[k]);
+                sc[k] = f * (2.0 / Mk) * (2.0 / Mk) * d.dx * d.dy / (2.0 * kMu0);
+            }
+            spec_omega = (double*)mem.get((size_t)nf * 8);
+            spec_M = (int*)mem.get((size_t)nf * 4);
+            spec_scale = (double*)mem.get((size_t)nf * 8);
+            spec_phase = (double*)mem.get((size_t)nf * 4 * 8);
+            spec_ring = (double*)mem.get((size_t)Mh * 4 * plane * 8);
+            spec_acc = (double*)mem.get((size_t)nf * 8 * plane * 8);
+            spec_partial = (double*)mem.get((size_t)nf * npartial * 8);
+            if (!spec_omega || !spec_M || !spec_scale || !spec_phase || !spec_ring || !spec_acc || !spec_partial)
+                return fail(MITHRA_ENOMEM, "device allocation failed (spectrum)");
+            CU(cudaMemcpyAsync(spec_omega, om.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, stream));
+            CU(cudaMemcpyAsync(spec_M, Mv.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, stream));
+            CU(cudaMemcpyAsync(spec_scale, sc.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, stream));
+            CU(cudaMemsetAsync(spec_ring, 0, (size_t)Mh * 4 * plane * 8, stream));
+            CU(cudaMemsetAsync(spec_acc, 0, (size_t)nf * 8 * plane * 8, stream));
+            CU(cudaStreamSynchronize(stream));   // the host vectors go out of scope
+        }
+        if (bunch_every > 0 && !(bunch_partial = (double*)mem.get((size_t)14 * npartial * 8)))
+            return fail(MITHRA_ENOMEM, "device allocation failed (bunch sampling)");
         for (int b = 0; b < 2; ++b)
             if (!(box[b] = (int*)mem.get(6 * sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (box)");
         if (ef.kind == 0 || ef.kind == 1) {
@@ -340,6 +390,9 @@ struct RunT final : mithra_run {
         return grow_series(1024);
     }
 
+    int64_t bunch_rows(int64_t steps) const { return bunch_every > 0 ? (steps + bunch_every - 1) / bunch_every : 0; }
+
+    // Grow every per-step series to hold `need` steps (old and new buffers while copying).
     int grow_series(int64_t need)
     {
         if (need <= ser_cap) return MITHRA_OK;
@@ -347,19 +400,31 @@ struct RunT final : mithra_run {
         while (cap < need) cap *= 2;
         double* np_ = (double*)mem.get((size_t)cap * 8);
         double* ne_ = (double*)mem.get((size_t)cap * 8);
-        if (!np_ || !ne_) return fail(MITHRA_ENOMEM, "device allocation failed (series)");
+        double* ns_ = nf > 0 ? (double*)mem.get((size_t)cap * nf * 8) : nullptr;
+        double* nb_ = bunch_every > 0 ? (double*)mem.get((size_t)bunch_rows(cap) * 15 * 8) : nullptr;
+        if (!np_ || !ne_ || (nf > 0 && !ns_) || (bunch_every > 0 && !nb_))
+            return fail(MITHRA_ENOMEM, "device allocation failed (series)");
         CU(cudaMemsetAsync(np_, 0, (size_t)cap * 8, stream));
         CU(cudaMemsetAsync(ne_, 0, (size_t)cap * 8, stream));
+        if (ns_) CU(cudaMemsetAsync(ns_, 0, (size_t)cap * nf * 8, stream));
+        if (nb_) CU(cudaMemsetAsync(nb_, 0, (size_t)bunch_rows(cap) * 15 * 8, stream));
         graph_reset();   // the captured steps write into the old series
         if (ser_cap) {
             CU(cudaMemcpyAsync(np_, ser_p, (size_t)ser_cap * 8, cudaMemcpyDeviceToDevice, stream));
             CU(cudaMemcpyAsync(ne_, ser_e, (size_t)ser_cap * 8, cudaMemcpyDeviceToDevice, stream));
+            if (ns_) CU(cudaMemcpyAsync(ns_, ser_s, (size_t)ser_cap * nf * 8, cudaMemcpyDeviceToDevice, stream));
+            if (nb_)
+                CU(cudaMemcpyAsync(nb_, ser_b, (size_t)bunch_rows(ser_cap) * 15 * 8, cudaMemcpyDeviceToDevice, stream));
             CU(cudaStreamSynchronize(stream));
             mem.release(ser_p);
             mem.release(ser_e);
+            if (ser_s) mem.release(ser_s);
+            if (ser_b) mem.release(ser_b);
         }
         ser_p = np_;
         ser_e = ne_;
+        ser_s = ns_;
+        ser_b = nb_;
         ser_cap = cap;
         return MITHRA_OK;
     }
@@ -466,6 +531,23 @@ struct RunT final : mithra_run {
         if (ptab32[0]) CU(launch_phase_table32(ef, sd, pc.kz, g.nz, ptab32[0], ptab32[1], stream));
         CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
         pend(MITHRA_K_PUSH, e0);
+        if (bunch_every > 0) {
+            pbeg(MITHRA_K_POWER, &e0);
+            BunchSample bs;
+            bs.sd = sd;
+            bs.every = bunch_every;
+            bs.shift[0] = g.x0 + 0.5 * (g.nx - 1) * g.dx;
+            bs.shift[1] = g.y0 + 0.5 * (g.ny - 1) * g.dy;
+            bs.shift[2] = g.z0 + 0.5 * (g.nz - 1) * g.dz;
+            bs.shift[3] = bs.shift[4] = bs.shift[5] = 0.0;
+            bs.shift[6] = bunch_shift_g;
+            bs.g0 = d.g0;
+            bs.b0 = d.b0;
+            bs.T0 = d.T0;
+            bs.dt = d.dt;
+            CU(launch_bunch_sample<real>(P, np, g, bs, bunch_partial, npartial, ser_b, stream));
+            pend(MITHRA_K_POWER, e0);
+        }
         pbeg(MITHRA_K_STENCIL, &e0);
         if (tma) {
             real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
@@ -492,6 +574,21 @@ struct RunT final : mithra_run {
             const double scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
             if (!ring || !acc || !partial) return fail(MITHRA_EINVAL, "power diagnostic buffers missing");
             CU(launch_power_step<real>(E6, g, ps, scale, partial, npartial, ser_p, stream));
+            if (nf > 0) {
+                SpecStep sp;
+                sp.kp = (int)d.kp;
+                sp.nf = nf;
+                sp.Mh = Mh;
+                sp.sd = sd;
+                sp.dt = d.dt;
+                sp.omega = spec_omega;
+                sp.M = spec_M;
+                sp.scale = spec_scale;
+                sp.ring = spec_ring;
+                sp.acc = spec_acc;
+                sp.phase = spec_phase;
+                CU(launch_spectrum_step<real>(E6, g, sp, spec_partial, npartial, ser_s, stream));
+            }
         }
         pend(MITHRA_K_POWER, e0);
         base = (base + 1) % 3;
@@ -698,6 +795,30 @@ struct RunT final : mithra_run {
         return MITHRA_OK;
     }
 
+    int spectrum(double* h, double* p, size_t cap, size_t* n_steps) override
+    {
+        if (nf <= 0) return fail(MITHRA_EINVAL, "spectrum: the run has no frequency sweep (nf_points = 0)");
+        if (n_steps) *n_steps = (size_t)nstep;
+        if (h) std::memcpy(h, hk.data(), (size_t)nf * sizeof(double));
+        if (!p || nstep == 0) return MITHRA_OK;
+        if (cap < (size_t)nstep * (size_t)nf) return fail(MITHRA_ERANGE, "spectrum: buffer too small");
+        CU(cudaMemcpyAsync(p, ser_s, (size_t)nstep * nf * 8, cudaMemcpyDeviceToHost, stream));
+        CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
+    int bunch_samples(double* out, size_t cap_rows, size_t* n_rows) override
+    {
+        if (bunch_every <= 0) return fail(MITHRA_EINVAL, "bunch_series: bunch sampling is off (bunch_every = 0)");
+        const int64_t rows = bunch_rows(nstep);
+        if (n_rows) *n_rows = (size_t)rows;
+        if (!out || rows == 0) return MITHRA_OK;
+        if (cap_rows < (size_t)rows) return fail(MITHRA_ERANGE, "bunch_series: buffer too small");
+        CU(cudaMemcpyAsync(out, ser_b, (size_t)rows * 15 * 8, cudaMemcpyDeviceToHost, stream));
+        CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
     int sync() override
     {
         CU(cudaStreamSynchronize(stream));
@@ -844,6 +965,11 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
     r->precision = gr.precision;
     r->mur_order = gr.mur_order;
     r->sort_every = gr.sort_every == 0 ? 20 : gr.sort_every;
+    r->nf = gr.nf_points;
+    for (int k = 0; k < r->nf; ++k)
+        r->hk.push_back(r->nf == 1 ? gr.nf_min : gr.nf_min + k * (gr.nf_max - gr.nf_min) / (r->nf - 1));
+    r->bunch_every = gr.bunch_every;
+    r->bunch_shift_g = b.gamma;
     r->np = b.n;
     Geom& g = r->g;
     g.nx = gr.nx;
@@ -935,6 +1061,11 @@ int mithra::validate_request(const mithra_grid* gr, double dt_lab, const mithra_
     if (gr->precision != 0 && gr->precision != 1) return fail(MITHRA_EINVAL, "create: precision must be 0 or 1");
     if (gr->substeps < 0 || gr->substeps > 1024) return fail(MITHRA_EINVAL, "create: substeps out of range");
     if (!(gr->norm_freq > 0)) return fail(MITHRA_EINVAL, "create: norm_freq must be > 0");
+    if (gr->nf_points < 0 || gr->nf_points > 256) return fail(MITHRA_EINVAL, "create: nf_points must be 0 .. 256");
+    if (gr->nf_points > 0 && !(std::isfinite(gr->nf_min) && std::isfinite(gr->nf_max) && gr->nf_min > 0 &&
+                               (gr->nf_points == 1 || gr->nf_max >= gr->nf_min)))
+        return fail(MITHRA_EINVAL, "create: spectrum needs 0 < nf_min <= nf_max");
+    if (gr->bunch_every < 0) return fail(MITHRA_EINVAL, "create: bunch_every must be >= 0");
     if (u->kind < -1 || u->kind > 4) return fail(MITHRA_EINVAL, "create: unknown undulator kind");
     if (u->kind == 4) {
         if (!finite_all({u->gap, u->taper}) || !(u->gap >= 0.0))
@@ -1005,6 +1136,12 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
     t += 4 * up(cap * 8);                                                     // series (old and new while growing)
     t += 2 * up(6 * 4) + 2 * up(gr->nz * 32);                                 // boxes, phase tables
     t += up(n * 48);                                                          // lab particles during the boost
+    if (gr->nf_points > 0) {                                                  // spectrum: ring, accumulators, series
+        const int64_t nf = gr->nf_points;
+        t += up(M * 4 * plane * 8) + up(nf * 8 * plane * 8) + 4 * up(nf * 8) + up(nf * 4 * 304 * 8) +
+             2 * up(cap * nf * 8);
+    }
+    if (gr->bunch_every > 0) t += up(14 * 304 * 8) + 2 * up((cap / gr->bunch_every + 1) * 15 * 8);
     return t;
 }
 
@@ -1066,6 +1203,18 @@ extern "C" int mithra_radiated_power(mithra_t r, double* p, double* t, size_t ca
             t[i] = r->d.g0 * (r->d.T0 + ((double)i + 0.5) * r->d.dt + r->d.b0 * zp / kC);
     }
     return MITHRA_OK;
+}
+
+extern "C" int mithra_power_spectrum(mithra_t r, double* h_out, double* p_lab, size_t cap_values, size_t* n_steps)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    return r->spectrum(h_out, p_lab, cap_values, n_steps);
+}
+
+extern "C" int mithra_bunch_series(mithra_t r, double* out15, size_t cap_rows, size_t* n_rows)
+{
+    if (!r) return fail(MITHRA_EINVAL, "null run");
+    return r->bunch_samples(out15, cap_rows, n_rows);
 }
 
 extern "C" int mithra_onaxis_field(mithra_t r, double* ex, size_t cap, size_t* n_out)
