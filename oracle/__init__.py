@@ -54,6 +54,9 @@ class Params(C.Structure):
         ("gamma", C.c_double), ("charge_e", C.c_double), ("sig_z", C.c_double),
         ("gap", C.c_double), ("n_modules", C.c_int32), ("taper", C.c_double),
         ("nf_min", C.c_double), ("nf_max", C.c_double), ("nf_points", C.c_int32), ("bunch_every", C.c_int32),
+        ("seed_type", C.c_int32), ("seed_a0", C.c_double), ("seed_lambda", C.c_double),
+        ("seed_pol_deg", C.c_double), ("seed_waist", C.c_double), ("seed_focus", C.c_double),
+        ("seed_offset", C.c_double), ("seed_pulse_fwhm", C.c_double), ("seed_cep_deg", C.c_double),
     ]
 
 
@@ -84,6 +87,7 @@ def _load():
             lib.orc_external_field.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp, dp]
             lib.orc_lab_field.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp, dp]
             lib.orc_boris.argtypes = [dp, dp, dp, C.c_double]
+            lib.orc_seed_potential.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp]
             lib.orc_mur.argtypes = [C.c_void_p, C.c_int]
             lib.orc_stencil.argtypes = [C.c_void_p, C.c_int]
             lib.orc_rotate_levels.argtypes = [C.c_void_p]
@@ -112,6 +116,9 @@ def params_from(w, periodic=(0, 0, 0)) -> Params:
     p.dist_head, p.gamma, p.charge_e, p.sig_z = w.dist_head, w.gamma, w.charge_e, w.sig_z
     p.gap, p.n_modules, p.taper = w.gap, w.n_modules, w.taper
     p.nf_min, p.nf_max, p.nf_points, p.bunch_every = w.nf_min, w.nf_max, w.nf_points, w.bunch_every
+    p.seed_type, p.seed_a0, p.seed_lambda, p.seed_pol_deg = w.seed_type, w.seed_a0, w.seed_lambda, w.seed_pol_deg
+    p.seed_waist, p.seed_focus, p.seed_offset = w.seed_waist, w.seed_focus, w.seed_offset
+    p.seed_pulse_fwhm, p.seed_cep_deg = w.seed_pulse_fwhm, w.seed_cep_deg
     return p
 
 
@@ -207,6 +214,11 @@ class Run:
         E, B = np.zeros(3), np.zeros(3)
         self.lib.orc_external_field(self.h, x, y, z, t, _dp(E), _dp(B))
         return E, B
+
+    def seed_potential(self, x, y, z, t):
+        A = np.zeros(2)
+        self.lib.orc_seed_potential(self.h, x, y, z, t, _dp(A))
+        return A
 
     def lab_field(self, x, y, zeta, t):
         E, B = np.zeros(3), np.zeros(3)

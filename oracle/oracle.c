@@ -304,6 +304,95 @@ void orc_stencil(orc_run *r, int c)
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Seed (Sec. "Seed Field"; Sec. FIELD, field-initialization; Eq. signalTypes).*/
+/* ------------------------------------------------------------------------- */
+
+/* Transverse vector potential of the seed, a beam propagating along +z in the lab, at the lab
+   event of the rest-frame event (x, y, z, t) (Eq. LorentzTransformR2L with the time coordinate).
+   A transverse potential is unchanged by the boost along z, so the lab value is the rest-frame
+   value.  Plane wave: A0 f(tau, 0); Gaussian beam (paraxial, waist w0 at the reference point):
+   A0 (w0/w(l)) exp(-r^2/w(l)^2) f(tau, atan(l/z_R) - k r^2 l / (2 (l^2 + z_R^2))), with l the
+   distance travelled past the reference point and tau = t' - t0 - (zeta - zeta_f)/c the retarded
+   lab time; f the modulated Gaussian of Eq. signalTypes (continuous for a non-positive pulse
+   length) with the carrier envelope phase.  The polarisation angle rotates A in the xy-plane. */
+void orc_seed_potential(const orc_run *r, double x, double y, double z, double t, double A[2])
+{
+    const orc_params *p = &r->p;
+    A[0] = A[1] = 0.0;
+    if (p->seed_type < 0) return;
+    const double g0 = r->gamma0, b0 = r->beta0;
+    const double zeta = g0 * (z + b0 * C0 * t);
+    const double tl = g0 * (t + b0 * z / C0);
+    const double k = 2.0 * PI / p->seed_lambda, w = C0 * k;
+    const double A0 = p->seed_a0 * ME * C0 / QE;
+    const double tau = tl - p->seed_offset / C0 - (zeta - p->seed_focus) / C0;
+    const double cep = p->seed_cep_deg * PI / 180.0;
+    double amp = 1.0, ph = 0.0;
+    if (p->seed_type == 1) {
+        const double w0 = p->seed_waist, zr = PI * w0 * w0 / p->seed_lambda;
+        const double l = zeta - p->seed_focus;
+        const double wl = w0 * sqrt(1.0 + (l / zr) * (l / zr));
+        const double r2 = x * x + y * y;
+        amp = (w0 / wl) * exp(-r2 / (wl * wl));
+        ph = atan(l / zr) - k * r2 * l / (2.0 * (l * l + zr * zr));
+    }
+    double f = cos(w * tau + ph + cep);
+    if (p->seed_pulse_fwhm > 0.0) {
+        const double tp = p->seed_pulse_fwhm / C0;
+        f *= exp(-2.0 * log(2.0) * tau * tau / (tp * tp));
+    }
+    const double th = p->seed_pol_deg * PI / 180.0;
+    A[0] = A0 * amp * f * cos(th);
+    A[1] = A0 * amp * f * sin(th);
+}
+
+/* Seed potential component c at lattice point (i, j, k) of component c's lattice (A_x sits at
+   (i + 1/2) dx, A_y at (j + 1/2) dy) and rest time t. */
+static double fval(const orc_run *r, int c, double hx, double hy, int i, int j, int k, double t)
+{
+    double A[2];
+    orc_seed_potential(r, r->x0 + (i + hx) * r->dx, r->y0 + (j + hy) * r->dy, r->z0 + k * r->dz, t, A);
+    return A[c];
+}
+
+/* TF/SF planes of the seed (Sec. "Seed Field"): node plane 1 of the z axis is the scattered-field
+   plane, plane 2 the total-field plane.  After the update of level n+1 from level n, the terms
+   of the update equation that reach across the two planes are corrected by the excitation f^n,
+   the seed potential at the lattice points at the time of level n: the SF plane loses the
+   contribution of f on plane 2 (it must see the scattered field there), the TF plane gains the
+   contribution of f on plane 1 (it must see the total field there).  (The printed corrections
+   carry the opposite signs; with these, a plane wave leaves the SF region at zero and the TF
+   region equal to f.)  Only the transverse components A_x, A_y are excited. */
+static void tfsf(orc_run *r, int c)
+{
+    if (r->p.seed_type < 0 || c > 1) return;
+    const int *e = r->ext[c];
+    if (e[2] < 4) return;
+    const double A = r->A;
+    const double rx = pow(r->cdt / r->dx, 2), ry = pow(r->cdt / r->dy, 2), rz = pow(r->cdt / r->dz, 2);
+    const double a2 = rx, a3 = rx, a4 = ry, a5 = ry;
+    const double a6 = rz - 2.0 * A * rx - 2.0 * A * ry, a7 = a6;
+    /* level n of the update that produced lev[2] is lev[1], at rest time T0 + (step + 1) dt */
+    const double t = r->T0 + ((double)r->step + 1.0) * r->dt;
+    const double hx = (c == 0) ? 0.5 : 0.0, hy = (c == 1) ? 0.5 : 0.0;
+    const int per0 = r->p.periodic[0], per1 = r->p.periodic[1];
+    const int ilo = per0 ? 0 : 1, ihi = per0 ? e[0] : e[0] - 1;
+    const int jlo = per1 ? 0 : 1, jhi = per1 ? e[1] : e[1] - 1;
+    double *out = r->lev[2][c];
+#define F(ii, jj, kk) fval(r, c, hx, hy, ii, jj, kk, t)
+    for (int j = jlo; j < jhi; ++j)
+        for (int i = ilo; i < ihi; ++i) {
+            const double sf = A * (a2 * F(i + 1, j, 2) + a3 * F(i - 1, j, 2) + a4 * F(i, j + 1, 2) + a5 * F(i, j - 1, 2))
+                              + a6 * F(i, j, 2);
+            const double tf = A * (a2 * F(i + 1, j, 1) + a3 * F(i - 1, j, 1) + a4 * F(i, j + 1, 1) + a5 * F(i, j - 1, 1))
+                              + a7 * F(i, j, 1);
+            out[IDX(r, i, j, 1)] -= sf;
+            out[IDX(r, i, j, 2)] += tf;
+        }
+#undef F
+}
+
 /* Mur boundary (Sec. "Boundary Truncation").  Level naming as in the manual:
    xi^{n+1} = lev[2], xi^n = lev[1], xi^{n-1} = lev[0]. */
 
@@ -1013,6 +1102,7 @@ void orc_step(orc_run *r, int64_t nsteps)
         for (int c = 0; c < 4; ++c) {
             if (c == 3 && !r->p.space_charge) continue;
             orc_stencil(r, c);
+            tfsf(r, c);
             orc_mur(r, c);
         }
         power_sample(r);

@@ -70,6 +70,17 @@ typedef struct orc_params {
     int32_t nf_points;
     /* bunch sampling (Sec. BUNCH, bunch-sampling) every `bunch_every` steps; 0: off */
     int32_t bunch_every;
+    /* seed injected through TF/SF planes (Sec. "Seed Field"; Sec. FIELD, field-initialization):
+       -1 none, 0 plane wave, 1 Gaussian beam, propagating along +z; lab-frame parameters */
+    int32_t seed_type;
+    double seed_a0;           /* strength a0 = e A0 / (m c) */
+    double seed_lambda;       /* wavelength */
+    double seed_pol_deg;      /* polarisation angle from x */
+    double seed_waist;        /* Gaussian beam waist w0 */
+    double seed_focus;        /* lab coordinate of the reference point / focus (from the undulator entrance) */
+    double seed_offset;       /* c t0: the pulse centre passes the reference point at lab time t0 */
+    double seed_pulse_fwhm;   /* c tau (intensity FWHM); <= 0: continuous wave */
+    double seed_cep_deg;      /* carrier envelope phase */
 } orc_params;
 
 typedef struct orc_run orc_run;
@@ -121,6 +132,9 @@ void orc_external_field(const orc_run *r, double x, double y, double z, double t
 void orc_lab_field(const orc_run *r, double xl, double yl, double zeta, double tl,
                    double Ep[3], double Bp[3]);
 void orc_boris(double u[3], const double E[3], const double B[3], double dtb);
+/* Seed: the lab-frame transverse vector potential (Ax, Ay) of the seed at the rest-frame
+   event (x, y, z, t). */
+void orc_seed_potential(const orc_run *r, double x, double y, double z, double t, double A[2]);
 /* One Mur update of component `which` (0..3): writes boundary points of level n+2
    from levels n+2 (interior), n+1, n. */
 void orc_mur(orc_run *r, int which);

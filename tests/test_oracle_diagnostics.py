@@ -1,6 +1,6 @@
 """Pins of the oracle's spectrum sweep and bunch sampling (Sec. FEL-OUTPUT, radiation-power with
 minimum / maximum normalised frequency and number of frequency points; Sec. BUNCH,
-bunch-sampling).
+bunch-sampling); and the seed injected through TF/SF planes (Sec. "Seed Field").
 
 * spectrum: a forward plane wave in a transversely periodic NSFD box (c dt = dz, so the
   discrete wave is an exact one-cell shift per step) is a pure sampled cosine at the plane; the
@@ -12,7 +12,12 @@ bunch-sampling).
   transverse normalised
   momenta and the lab Lorentz factor reproduce the lab input bunch's statistics (the last one
   inverts the boost), the mean position advances by n c dt <beta> and the position spreads grow
-  as the spread of r_0 + n c dt beta.
+  as the spread of r_0 + n c dt beta;
+* seed: in one dimension (transversely periodic NSFD at c dt = dz, first-order Mur at normal
+  incidence, both exact) a plane-wave pulse leaves the scattered-field planes at zero and the
+  total-field region equal to the incident potential to rounding -- the test that fixes the
+  signs of the TF/SF corrections; a paraxial Gaussian pulse in 3D leaks below 2 % into the
+  scattered-field planes and follows the incident potential on the axis.
 """
 import math
 
@@ -115,3 +120,69 @@ def test_bunch_sampling_free_streaming():
         rn = r0 + (5 * i) * v
         assert np.max(np.abs(row[1:4] - rn.mean(axis=0))) < 1e-12 * np.max(np.abs(rn))
         assert np.max(np.abs(row[7:10] - rn.std(axis=0)) / rn.std(axis=0)) < 1e-9
+
+
+# ---- seed through TF/SF planes (Sec. "Seed Field") --------------------------------------------
+
+def _seed_box(nx, ny, nz, seed_type, lam_cells, periodic, **kw):
+    dz = 1.0e-4
+    w = vacuum(nx, ny, nz, 2.0e-4, 2.0e-4, dz, solver=0, space_charge=0, mur_order=kw.pop("mur_order", 1))
+    w = workloads.scaled(w, seed_type=seed_type, seed_a0=1e-3, seed_lambda=lam_cells * dz, **kw)
+    return oracle.Run(oracle.params_from(w, periodic=periodic)), w
+
+
+def test_plane_wave_seed_exact_in_one_dimension():
+    """NSFD at c dt = dz shifts a z-only field by exactly one cell per step and first-order Mur is
+    exact at normal incidence, so a plane-wave pulse injected through the TF/SF planes must leave
+    the scattered-field planes (z index 0, 1) at zero and make the total-field region equal to
+    the incident potential, node for node, to rounding."""
+    nz = 160
+    # the pulse centre starts 220 cells behind the domain, so the incident field inside the
+    # domain at t = 0 is below 1e-32 of its amplitude (the run starts from zero fields)
+    r, w = _seed_box(4, 4, nz, 0, 20, (1, 1, 0), seed_pulse_fwhm=30 * 1.0e-4,
+                     seed_offset=300 * 1.0e-4, seed_pol_deg=30.0, seed_cep_deg=40.0)
+    inf = r.info()
+    assert inf["gamma0"] == 1.0 and inf["T0"] == 0.0
+    A0 = 1e-3 * 9.1093837015e-31 * C0 / 1.602176634e-19
+    peak = 0.0
+    for s in range(1, 25):
+        r.step(20)
+        t = (r.info()["dt"]) * (20 * s + 1)     # level n+1 after 20 s steps
+        for c in (0, 1):
+            a = r.field(c, 1)
+            z = inf["z0"] + np.arange(nz) * inf["dz"]
+            f = np.array([r.seed_potential(inf["x0"] + 0.5 * inf["dx"] * (c == 0), inf["y0"], zz, t)[c]
+                          for zz in z])
+            assert np.max(np.abs(a[:2])) <= 1e-12 * A0
+            assert np.max(np.abs(a[2:] - f[2:, None, None])) <= 1e-11 * A0, (s, c)
+            peak = max(peak, float(np.max(np.abs(f))))
+    assert peak > 0.5 * A0 * math.sin(math.radians(30.0))
+
+
+def test_gaussian_seed_enters_the_total_field_region():
+    """A paraxial Gaussian-beam pulse (k w0 = 4 pi, focus at the middle of the box) through the
+    TF/SF planes: the scattered-field planes see only what the transverse boundaries and the
+    omitted longitudinal potential leave (below 2 % of the incident amplitude), and the total
+    field on the axis follows the incident potential within 10 % of its amplitude: at 8 cells
+    per wavelength the NSFD dispersion scales the transverse (diffraction) term by
+    1 - 4 A sin^2(k dz / 2) = 0.85, which shifts the Gouy phase by a few hundredths of a radian
+    over the box (the exact one-dimensional pin above carries the injection's signs, time levels
+    and coefficients)."""
+    nx = ny = 40
+    nz = 120
+    dz = 1.0e-4
+    r, w = _seed_box(nx, ny, nz, 1, 8, (0, 0, 0), seed_waist=16 * 2.0e-4, seed_focus=0.0,
+                     seed_pulse_fwhm=30 * dz, seed_offset=220 * dz, mur_order=2)
+    inf = r.info()
+    A0 = 1e-3 * 9.1093837015e-31 * C0 / 1.602176634e-19
+    r.step(220)
+    t = inf["dt"] * 221
+    a = r.field(0, 1)
+    i0, j0 = nx // 2, ny // 2
+    z = inf["z0"] + np.arange(nz) * inf["dz"]
+    x = inf["x0"] + (i0 + 0.5) * inf["dx"]
+    y = inf["y0"] + j0 * inf["dy"]
+    f = np.array([r.seed_potential(x, y, zz, t)[0] for zz in z])
+    assert np.max(np.abs(f)) > 0.5 * A0
+    assert np.max(np.abs(a[:2])) < 0.02 * A0
+    assert np.max(np.abs(a[4:nz - 4, j0, i0] - f[4:nz - 4])) < 0.10 * A0

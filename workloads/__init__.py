@@ -86,6 +86,15 @@ class Workload:
     nf_max: float = 0.0
     nf_points: int = 0   # number of spectrum frequencies (0: no spectrum)
     bunch_every: int = 0 # bunch sampling every this many steps (0: off)
+    seed_type: int = -1  # seed through TF/SF planes: -1 none, 0 plane wave, 1 Gaussian beam (+z)
+    seed_a0: float = 0.0
+    seed_lambda: float = 1.0
+    seed_pol_deg: float = 0.0
+    seed_waist: float = 0.0
+    seed_focus: float = 0.0      # lab position of the seed's reference point / focus
+    seed_offset: float = 0.0     # c t0
+    seed_pulse_fwhm: float = 0.0 # c tau; <= 0: continuous
+    seed_cep_deg: float = 0.0
 
 
 def lab_bunch(w: Workload, n: Optional[int] = None, seed: Optional[int] = None) -> np.ndarray:
