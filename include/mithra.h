@@ -107,6 +107,21 @@ typedef struct mithra_bunch {
                                     gamma*beta_x, gamma*beta_y, gamma*beta_z; lab frame at t' = 0 */
 } mithra_bunch;
 
+/* Seed injected through total-field / scattered-field planes (Sec. "Seed Field"; Sec. FIELD,
+   field-initialization): a beam propagating along +z, given in the laboratory frame. */
+typedef struct mithra_seed {
+    int32_t type;              /* -1 none, 0 plane wave, 1 Gaussian beam (paraxial) */
+    double a0;                 /* strength a0 = e A0 / (m_e c) (Sec. FIELD, strength-parameter) */
+    double lambda;             /* wavelength (> 0) */
+    double pol_deg;            /* polarisation angle from the x axis, degrees */
+    double waist;              /* Gaussian beam waist w0 (> 0 for type 1) */
+    double focus;              /* lab position of the reference point / focus, measured like the
+                                  undulator: from the (first) undulator entrance */
+    double offset;             /* c t0: the pulse centre passes the reference point at lab time t0 */
+    double pulse_fwhm;         /* c tau, intensity FWHM (Eq. signalTypes, modulated Gaussian); <= 0: continuous */
+    double cep_deg;            /* carrier envelope phase, degrees */
+} mithra_seed;
+
 /* Install the device allocator used by every later mithra_create (process-wide).
    alloc(ctx, bytes) returns a device pointer or NULL; free(ctx, ptr).  Pass NULLs to restore
    cudaMalloc/cudaFree.  Runs created earlier keep the allocator they were created with. */
@@ -123,6 +138,17 @@ int mithra_set_allocator(mithra_alloc_fn alloc, mithra_free_fn free_fn, void *ct
    Errors: EINVAL (sizes, non-finite values, kinds), ENOMEM, ECUDA. */
 int mithra_create(const mithra_grid *grid, double dt_lab, const mithra_undulator *und,
                   const mithra_bunch *bunch, mithra_t *out);
+
+/* Inject `seed` (copied) through the TF/SF planes of the run: node plane 1 of the z axis is the
+   scattered-field plane and plane 2 the total-field plane of the transverse vector potential
+   A_x, A_y.  After every potential update the update terms that cross the two planes are
+   corrected by the seed's lab-frame transverse vector potential (unchanged by the boost) at
+   the lattice points and the time of the level the update read: the scattered-field plane
+   subtracts and the total-field plane adds them.  The seed's longitudinal potential
+   (order 1/(k w0) of a paraxial beam) is not injected.  Call before the first step; a type of
+   -1 removes the seed.  Errors: EINVAL (after the first step, non-finite or out-of-range
+   values). */
+int mithra_set_seed(mithra_t run, const mithra_seed *seed);
 
 /* Use `stream` (a cudaStream_t) for all later work of the run. */
 int mithra_set_stream(mithra_t run, void *stream);

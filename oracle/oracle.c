@@ -314,7 +314,7 @@ void orc_stencil(orc_run *r, int c)
    value.  Plane wave: A0 f(tau, 0); Gaussian beam (paraxial, waist w0 at the reference point):
    A0 (w0/w(l)) exp(-r^2/w(l)^2) f(tau, atan(l/z_R) - k r^2 l / (2 (l^2 + z_R^2))), with l the
    distance travelled past the reference point and tau = t' - t0 - (zeta - zeta_f)/c the retarded
-   lab time; f the modulated Gaussian of Eq. signalTypes (continuous for a non-positive pulse
+   lab time (t' - zeta/c = (t - z/c) / (g0 (1 + b0)) for the rest-frame event); f the modulated Gaussian of Eq. signalTypes (continuous for a non-positive pulse
    length) with the carrier envelope phase.  The polarisation angle rotates A in the xy-plane. */
 void orc_seed_potential(const orc_run *r, double x, double y, double z, double t, double A[2])
 {
@@ -323,10 +323,13 @@ void orc_seed_potential(const orc_run *r, double x, double y, double z, double t
     if (p->seed_type < 0) return;
     const double g0 = r->gamma0, b0 = r->beta0;
     const double zeta = g0 * (z + b0 * C0 * t);
-    const double tl = g0 * (t + b0 * z / C0);
     const double k = 2.0 * PI / p->seed_lambda, w = C0 * k;
     const double A0 = p->seed_a0 * ME * C0 / QE;
-    const double tau = tl - p->seed_offset / C0 - (zeta - p->seed_focus) / C0;
+    /* retarded lab time t' - zeta/c of the +z beam, written as (t - z/c) / (g0 (1 + b0)): the
+       same quantity as the boosted t' and zeta (Eq. LorentzTransformR2L) without the
+       cancellation of two nearly equal lab times (a factor 2 g0^2 on a carrier phase of
+       thousands of radians) */
+    const double tau = (t - z / C0) / (g0 * (1.0 + b0)) - p->seed_offset / C0 + p->seed_focus / C0;
     const double cep = p->seed_cep_deg * PI / 180.0;
     double amp = 1.0, ph = 0.0;
     if (p->seed_type == 1) {

@@ -48,6 +48,12 @@ class Undulator(C.Structure):
                 ("gap", C.c_double), ("n_modules", C.c_int32), ("taper", C.c_double)]
 
 
+class Seed(C.Structure):
+    _fields_ = [("type", C.c_int32), ("a0", C.c_double), ("lambda_", C.c_double), ("pol_deg", C.c_double),
+                ("waist", C.c_double), ("focus", C.c_double), ("offset", C.c_double),
+                ("pulse_fwhm", C.c_double), ("cep_deg", C.c_double)]
+
+
 class Bunch(C.Structure):
     _fields_ = [("n", C.c_int64), ("charge_e", C.c_double), ("gamma", C.c_double),
                 ("sig_z", C.c_double), ("lab_particles", C.POINTER(C.c_double))]
@@ -82,6 +88,7 @@ def load(rebuild: bool = False):
     L.mithra_set_particles.argtypes = [vp, dp, C.c_size_t]
     L.mithra_radiated_power.argtypes = [vp, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_onaxis_field.argtypes = [vp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.mithra_set_seed.argtypes = [vp, C.POINTER(Seed)]
     L.mithra_power_spectrum.argtypes = [vp, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_bunch_series.argtypes = [vp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_diag.argtypes = [vp, dp, dp]
@@ -242,6 +249,14 @@ def grid_from(w, precision=None, sort_every=0) -> Grid:
     return g
 
 
+def seed_from(w) -> Seed:
+    s = Seed()
+    s.type, s.a0, s.lambda_, s.pol_deg = w.seed_type, w.seed_a0, w.seed_lambda, w.seed_pol_deg
+    s.waist, s.focus, s.offset = w.seed_waist, w.seed_focus, w.seed_offset
+    s.pulse_fwhm, s.cep_deg = w.seed_pulse_fwhm, w.seed_cep_deg
+    return s
+
+
 def undulator_from(w) -> Undulator:
     u = Undulator()
     u.kind, u.K, u.lambda_, u.n_periods = w.und_kind, w.K, w.lambda_u, w.n_periods
@@ -281,7 +296,12 @@ class Run:
         b, keep = bunch_from(w, lab6)
         r = cls(grid_from(w, precision, sort_every), undulator_from(w), b, stream=stream)
         r._keep = keep
+        if getattr(w, "seed_type", -1) >= 0:
+            r.set_seed(seed_from(w))
         return r
+
+    def set_seed(self, seed: Seed):
+        _check(self.L.mithra_set_seed(self.h, C.byref(seed)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -175,6 +175,42 @@ __host__ __device__ inline void lab_field(const ExtField& f, double xl, double y
     }
 }
 
+// Seed beam along +z (Sec. "Seed Field"; Sec. FIELD, field-initialization), lab parameters.
+struct SeedField {
+    int type;               // -1 none, 0 plane wave, 1 Gaussian beam
+    double g0, b0;          // rest frame
+    double A0;              // a0 m c / e
+    double k, w;            // lab wavenumber and angular frequency
+    double zr, w0;          // Rayleigh length and waist (Gaussian beam)
+    double focus, t0;       // lab reference point and the time its pulse centre passes it
+    double tp;              // pulse length tau (s); <= 0: continuous
+    double cep, cpol, spol;
+};
+
+// The seed's transverse vector potential at the rest-frame event (x, y, z, t): the lab value at
+// the boosted event (a transverse potential is unchanged by a boost along z).
+__host__ __device__ inline void seed_potential(const SeedField& s, double x, double y, double z, double t,
+                                               double* ax, double* ay)
+{
+    const double zeta = s.g0 * fma(s.b0 * kC, t, z);
+    // retarded lab time t' - t0 - (zeta - focus)/c of the +z beam; t' - zeta/c written in rest
+    // variables, (t - z/c) / (g0 (1 + b0)), avoids cancelling two nearly equal lab times
+    const double tau = (t - z / kC) / (s.g0 * (1.0 + s.b0)) - s.t0 + s.focus / kC;
+    double amp = 1.0, ph = 0.0;
+    if (s.type == 1) {
+        const double l = zeta - s.focus, lz = l / s.zr;
+        const double wl = s.w0 * sqrt(1.0 + lz * lz);
+        const double r2 = x * x + y * y;
+        amp = (s.w0 / wl) * exp(-r2 / (wl * wl));
+        ph = atan(lz) - s.k * r2 * l / (2.0 * (l * l + s.zr * s.zr));
+    }
+    double f = cos(s.w * tau + ph + s.cep);
+    if (s.tp > 0.0) f *= exp(-2.0 * 0.69314718055994530942 * (tau * tau) / (s.tp * s.tp));
+    const double a = s.A0 * amp * f;
+    *ax = a * s.cpol;
+    *ay = a * s.spol;
+}
+
 // External field at a rest-frame event (x, y, z, t): lab event, lab field, then the field
 // transform to the frame moving with beta0 along z.
 __host__ __device__ inline void external_field(const ExtField& f, double x, double y, double z, double t,

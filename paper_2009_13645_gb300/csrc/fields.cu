@@ -598,6 +598,81 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// Seed through TF/SF planes.
+// ---------------------------------------------------------------------------------------
+// The seed potential of component c (0: A_x at (i + 1/2) dx, 1: A_y at (j + 1/2) dy) at nodes
+// (i, j) of z planes 1 and 2: fbuf[((c * 2 + plane - 1) * ny + j) * nx + i].
+__global__ void k_seed_eval(SeedField s, Geom g, const StepDev* sd, double T0, double* __restrict__ fbuf)
+{
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 2 * plane) return;
+    const int k = 1 + (int)(q / plane);
+    const int64_t pl = q % plane;
+    const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
+    const double t = T0 + ((double)sd->n + 1.0) * g.dt;
+    const double z = g.z0 + k * g.dz;
+    double ax, ay, bx, by;
+    seed_potential(s, g.x0 + (i + 0.5) * g.dx, g.y0 + j * g.dy, z, t, &ax, &ay);
+    seed_potential(s, g.x0 + i * g.dx, g.y0 + (j + 0.5) * g.dy, z, t, &bx, &by);
+    fbuf[(int64_t)(k - 1) * plane + pl] = ax;            // component 0
+    fbuf[(int64_t)(2 + k - 1) * plane + pl] = by;        // component 1
+}
+
+template <typename real>
+struct TfsfArgs {
+    real* out[2];
+    int ex[2], ey[2];
+    double A, a2, a4, a6;   // NSFD coefficient, (c dt/dx)^2, (c dt/dy)^2, alpha'_6 = alpha'_7
+};
+
+template <typename real>
+__global__ void k_tfsf(TfsfArgs<real> a, Geom g, const double* __restrict__ fbuf)
+{
+    const int c = blockIdx.y;
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+    if (q >= plane || i < 1 || i > a.ex[c] - 2 || j < 1 || j > a.ey[c] - 2) return;
+    const double* f1 = fbuf + (int64_t)(2 * c) * plane;
+    const double* f2 = f1 + plane;
+    auto F = [&](const double* f, int ii, int jj) { return f[(int64_t)jj * g.nx + ii]; };
+    const double sf = a.A * (a.a2 * (F(f2, i + 1, j) + F(f2, i - 1, j)) + a.a4 * (F(f2, i, j + 1) + F(f2, i, j - 1))) +
+                      a.a6 * F(f2, i, j);
+    const double tf = a.A * (a.a2 * (F(f1, i + 1, j) + F(f1, i - 1, j)) + a.a4 * (F(f1, i, j + 1) + F(f1, i, j - 1))) +
+                      a.a6 * F(f1, i, j);
+    real* o = a.out[c];
+    o[1 * g.sz + (int64_t)j * g.sy + i] -= (real)sf;
+    o[2 * g.sz + (int64_t)j * g.sy + i] += (real)tf;
+}
+
+template <typename real>
+cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf, const SeedField& s,
+                        const StepDev* sd, double T0, double* fbuf, cudaStream_t st)
+{
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    k_seed_eval<<<(unsigned)((2 * plane + 127) / 128), 128, 0, st>>>(s, g, sd, T0, fbuf);
+    TfsfArgs<real> a;
+    for (int c = 0; c < 2; ++c) {
+        a.out[c] = out[c];
+        a.ex[c] = g.nx - (c == 0);
+        a.ey[c] = g.ny - (c == 1);
+    }
+    a.A = cf.w;
+    a.a2 = cf.ax;
+    a.a4 = cf.ay;
+    a.a6 = cf.a6;
+    k_tfsf<real><<<dim3((unsigned)((plane + 127) / 128), 2), 128, 0, st>>>(a, g, fbuf);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tfsf<float>(float* const[2], const Geom&, const StencilCoef&, const SeedField&,
+                                        const StepDev*, double, double*, cudaStream_t);
+template cudaError_t launch_tfsf<double>(double* const[2], const Geom&, const StencilCoef&, const SeedField&,
+                                         const StepDev*, double, double*, cudaStream_t);
+
 template cudaError_t launch_stencil<float>(const FieldLevels<float>&, const Geom&, const StencilCoef&, int, cudaStream_t);
 template cudaError_t launch_stencil<double>(const FieldLevels<double>&, const Geom&, const StencilCoef&, int, cudaStream_t);
 template cudaError_t launch_mur<float>(const FieldLevels<float>&, const Geom&, int, int, bool, cudaStream_t);

@@ -57,6 +57,15 @@ constexpr bool tma_x_faces()
     return sizeof(real) == 4;
 }
 
+struct StepDev;
+// TF/SF planes of the seed (Sec. "Seed Field") on level n+1 of A_x and A_y: the seed potential
+// at the time of level n (T0 + (step + 1) dt) is evaluated once per node of z planes 1 and 2 into
+// `fbuf` (2 components x 2 planes x nx x ny, FP64), then the scattered-field plane 1 subtracts
+// and the total-field plane 2 adds the update terms that cross them.
+template <typename real>
+cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf, const SeedField& s,
+                        const StepDev* sd, double T0, double* fbuf, cudaStream_t st);
+
 // Mur boundary values of level n+1: the faces, then the edges, then the corners.  With
 // x_faces_done the TMA stencil of this step has already written the x faces.
 template <typename real>

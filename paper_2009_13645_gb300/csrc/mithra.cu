@@ -146,6 +146,7 @@ struct mithra_run {
     virtual int diag(double* fe, double* b3) = 0;
     virtual int series(int which, double* out, size_t cap, size_t* n_out) = 0;
     virtual int spectrum(double* h, double* p, size_t cap, size_t* n_steps) = 0;
+    virtual int set_seed(const mithra_seed& s) = 0;
     virtual int bunch_samples(double* out, size_t cap_rows, size_t* n_rows) = 0;
     virtual int sync() = 0;
     virtual int64_t graph_steps() const = 0;
@@ -228,6 +229,9 @@ struct RunT final : mithra_run {
     double* spec_phase = nullptr;
     double* spec_partial = nullptr;
     double* ser_s = nullptr;   // ser_cap x nf
+    // seed through TF/SF planes (seed.type < 0: none)
+    SeedField seed{-1};
+    double* seed_buf = nullptr;   // the seed potential on z planes 1, 2 (2 components)
     // bunch sampling (bunch_every = 0: off)
     int bunch_every = 0;
     double bunch_shift_g = 1.0;
@@ -552,13 +556,19 @@ struct RunT final : mithra_run {
         if (tma) {
             real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
             real* prevp[4] = {pot[lev(0)][0], pot[lev(0)][1], pot[lev(0)][2], pot[lev(0)][3]};
-            CU(launch_stencil_tma<real>(tma, outp, prevp, &murc, lev(1), lev(0), g, cf, ncomp, err_word, stream));
+            // with a seed the Mur x faces must see the TF/SF-corrected planes: no fused faces
+            CU(launch_stencil_tma<real>(tma, outp, prevp, seed.type < 0 ? &murc : nullptr, lev(1), lev(0), g, cf,
+                                        ncomp, err_word, stream));
         } else {
             CU(launch_stencil<real>(L, g, cf, ncomp, stream));
         }
+        if (seed.type >= 0) {
+            real* outs[2] = {pot[lev(2)][0], pot[lev(2)][1]};
+            CU(launch_tfsf<real>(outs, g, cf, seed, sd, d.T0, seed_buf, stream));
+        }
         pend(MITHRA_K_STENCIL, e0);
         pbeg(MITHRA_K_MUR, &e0);
-        CU(launch_mur<real>(L, g, mur_order, ncomp, tma != nullptr && tma_x_faces<real>(), stream));
+        CU(launch_mur<real>(L, g, mur_order, ncomp, tma != nullptr && tma_x_faces<real>() && seed.type < 0, stream));
         pend(MITHRA_K_MUR, e0);
         pbeg(MITHRA_K_POWER, &e0);
         {
@@ -792,6 +802,38 @@ struct RunT final : mithra_run {
             CU(cudaMemcpyAsync(out, ser_e, (size_t)nstep * 8, cudaMemcpyDeviceToHost, stream));
         }
         CU(cudaStreamSynchronize(stream));
+        return MITHRA_OK;
+    }
+
+    int set_seed(const mithra_seed& in) override
+    {
+        if (nstep > 0) return fail(MITHRA_EINVAL, "set_seed: the run has already stepped");
+        if (in.type < -1 || in.type > 1) return fail(MITHRA_EINVAL, "set_seed: unknown seed type");
+        for (double v : {in.a0, in.lambda, in.pol_deg, in.waist, in.focus, in.offset, in.pulse_fwhm, in.cep_deg})
+            if (!std::isfinite(v)) return fail(MITHRA_EINVAL, "set_seed: non-finite value");
+        if (in.type >= 0 && !(in.lambda > 0.0)) return fail(MITHRA_EINVAL, "set_seed: lambda must be > 0");
+        if (in.type == 1 && !(in.waist > 0.0)) return fail(MITHRA_EINVAL, "set_seed: waist must be > 0");
+        graph_reset();   // the captured steps do not hold the TF/SF kernels
+        SeedField s{};
+        s.type = in.type;
+        if (in.type >= 0) {
+            s.g0 = d.g0;
+            s.b0 = d.b0;
+            s.A0 = in.a0 * kMe * kC / kQe;
+            s.k = 2.0 * kPi / in.lambda;
+            s.w = kC * s.k;
+            s.w0 = in.type == 1 ? in.waist : 0.0;
+            s.zr = in.type == 1 ? kPi * in.waist * in.waist / in.lambda : 1.0;
+            s.focus = in.focus;
+            s.t0 = in.offset / kC;
+            s.tp = in.pulse_fwhm / kC;
+            s.cep = in.cep_deg * kPi / 180.0;
+            s.cpol = std::cos(in.pol_deg * kPi / 180.0);
+            s.spol = std::sin(in.pol_deg * kPi / 180.0);
+            if (!seed_buf && !(seed_buf = (double*)mem.get((size_t)4 * g.nx * g.ny * 8)))
+                return fail(MITHRA_ENOMEM, "device allocation failed (seed planes)");
+        }
+        seed = s;
         return MITHRA_OK;
     }
 
@@ -1143,6 +1185,12 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
     }
     if (gr->bunch_every > 0) t += up(14 * 304 * 8) + 2 * up((cap / gr->bunch_every + 1) * 15 * 8);
     return t;
+}
+
+extern "C" int mithra_set_seed(mithra_t r, const mithra_seed* s)
+{
+    if (!r || !s) return fail(MITHRA_EINVAL, "set_seed: null argument");
+    return r->set_seed(*s);
 }
 
 extern "C" int mithra_set_stream(mithra_t r, void* stream)

@@ -95,6 +95,7 @@ class Workload:
     seed_offset: float = 0.0     # c t0
     seed_pulse_fwhm: float = 0.0 # c tau; <= 0: continuous
     seed_cep_deg: float = 0.0
+    uniform: int = 0     # longitudinal profile: 0 Gaussian (rms sig_z), 1 uniform over [-sig_z, sig_z]
 
 
 def lab_bunch(w: Workload, n: Optional[int] = None, seed: Optional[int] = None) -> np.ndarray:
@@ -104,7 +105,14 @@ def lab_bunch(w: Workload, n: Optional[int] = None, seed: Optional[int] = None) 
     out = np.empty((n, 6), dtype=np.float64)
     out[:, 0] = rng.standard_normal(n) * w.sig_x
     out[:, 1] = rng.standard_normal(n) * w.sig_y
-    if w.quiet:
+    if w.uniform:
+        # uniform current over [-sig_z, sig_z] (sig_z is half the bunch length, Sec. BUNCH)
+        if w.quiet:
+            z = w.sig_z * (2.0 * (np.arange(n, dtype=np.float64) + 0.5) / n - 1.0)
+            z = z[rng.permutation(n)]
+        else:
+            z = rng.uniform(-w.sig_z, w.sig_z, n)
+    elif w.quiet:
         # evenly spaced quantiles of the Gaussian current profile (quiet start)
         from scipy.special import erfinv
         q = (np.arange(n, dtype=np.float64) + 0.5) / n
@@ -179,6 +187,20 @@ WORKLOADS = {
         charge_e=100e-12 / 1.602176634e-19, n_particles=2_000_000,
         lambda_r=1.782e-6, shot_noise=1, quiet=1,
         plane_dist=0.3 * 512 * 9.900980e-8, steps=2000, seed=1240, precision=1),
+    # Seeded UV FEL (Example 2 job file): 2500 x 2500 x 165 um at 30 x 30 x 0.02 um, 4 194 304
+    # particles of a uniform 150 um bunch (55 pC, gamma 391.36, 1e-4 energy spread), planar
+    # undulator K = 1.95, 2.8 cm; a 10 kW Gaussian seed at 0.265187 um (a0 = 9.857e-7, waist
+    # 183.74 um, focus 0.7 m), continuous.
+    "seeded_uv_84x84x8250": _w(
+        name="seeded_uv_84x84x8250", nx=84, ny=84, nz=8250,
+        dx=30e-6, dy=30e-6, dz=0.02e-6, space_charge=0,
+        und_kind=0, K=1.95, lambda_u=0.028, n_periods=536, dist_head=0.056,
+        gamma=391.36, rel_espread=1e-4, sig_x=95.3e-6, sig_y=95.3e-6, sig_z=75.0e-6, uniform=1,
+        sig_ux=0.0105, sig_uy=0.0105, quiet=1,
+        charge_e=3.4332e8, n_particles=4_194_304,
+        seed_type=1, seed_a0=9.857e-7, seed_lambda=0.265187e-6, seed_waist=183.74e-6,
+        seed_focus=0.7, seed_offset=0.7, seed_pulse_fwhm=0.0,
+        plane_dist=78e-6, steps=200, seed=1241, precision=1),
     # Large single run: 256x256x1024, 32M particles, helical undulator, 1% bunching.
     "helical_256x256x1024": _w(
         name="helical_256x256x1024", nx=256, ny=256, nz=1024,
