@@ -223,96 +223,88 @@ cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g,
 }
 
 // ---- radiated-power spectrum ------------------------------------------------------------
-__global__ void k_spec_phase(SpecStep s)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= s.nf) return;
-    const int64_t n = s.sd->n;
-    double sn, cn, so, co;
-    sincos(s.omega[k] * ((double)n + 0.5) * s.dt, &sn, &cn);
-    sincos(s.omega[k] * ((double)(n - s.M[k]) + 0.5) * s.dt, &so, &co);
-    s.phase[4 * k + 0] = cn;
-    s.phase[4 * k + 1] = sn;
-    s.phase[4 * k + 2] = co;
-    s.phase[4 * k + 3] = so;
-}
-
-// Every plane point updates the accumulators of every frequency (adding its new sample, and
-// once the frequency's window is full subtracting the sample of step n - M[k] from the ring),
-// then stores its new sample; one partial flux per block and frequency.
+// One block per (256 plane points, frequency k): the block's first thread forms the frequency's
+// phases of the step; every point updates the accumulators of frequency k (adding its new
+// sample, and once the window is full subtracting the sample of step n - M[k] from the ring);
+// one partial flux per block.  The new sample enters the ring afterwards (k_spec_ring), once
+// every frequency has read its leaving sample.
 template <typename real>
 __global__ void __launch_bounds__(kRedThreads) k_spec_step(Fields6<real> eb, Geom g, SpecStep s,
                                                            double* __restrict__ partial)
 {
     __shared__ double sh[32];
+    __shared__ double ph[4];
+    const int k = blockIdx.y;
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = s.sd->n;
-    const bool in = pl < plane;
-    double x[4] = {0.0, 0.0, 0.0, 0.0};
-    bool interior = false;
-    if (in) {
+    const int Mk = s.M[k];
+    if (threadIdx.x == 0) {
+        sincos(s.omega[k] * ((double)n + 0.5) * s.dt, &ph[1], &ph[0]);
+        sincos(s.omega[k] * ((double)(n - Mk) + 0.5) * s.dt, &ph[3], &ph[2]);
+    }
+    __syncthreads();
+    const bool full = n >= Mk, emit = n + 1 >= Mk;
+    double contrib = 0.0;
+    if (pl < plane) {
         const int64_t id = (int64_t)s.kp * g.sz + pl;
-        x[0] = (double)eb.c[0][id];
-        x[1] = (double)eb.c[1][id];
-        x[2] = (double)eb.c[3][id];
-        x[3] = (double)eb.c[4][id];
-        const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
-        interior = i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2;
-    }
-    for (int k = 0; k < s.nf; ++k) {
-        const int Mk = s.M[k];
-        const bool full = n >= Mk, emit = n + 1 >= Mk;
-        double contrib = 0.0;
-        if (in) {
-            const double cn = s.phase[4 * k], sn = s.phase[4 * k + 1];
-            const double co = s.phase[4 * k + 2], so = s.phase[4 * k + 3];
-            const double* ro = s.ring + (full ? (int64_t)((n - Mk) % s.Mh) : 0) * 4 * plane + pl;
-            double* ac = s.acc + (int64_t)k * 8 * plane + pl;
-            double re[4], im[4];
+        const double x[4] = {(double)eb.c[0][id], (double)eb.c[1][id], (double)eb.c[3][id], (double)eb.c[4][id]};
+        const double cn = ph[0], sn = ph[1], co = ph[2], so = ph[3];
+        const double* ro = s.ring + (full ? (int64_t)((n - Mk) % s.Mh) : 0) * 4 * plane + pl;
+        double* ac = s.acc + (int64_t)k * 8 * plane + pl;
+        double re[4], im[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                double a = ac[(2 * q) * plane], b = ac[(2 * q + 1) * plane];
-                a += x[q] * cn;
-                b -= x[q] * sn;
-                if (full) {
-                    const double o = ro[q * plane];
-                    a -= o * co;
-                    b += o * so;
-                }
-                ac[(2 * q) * plane] = a;
-                ac[(2 * q + 1) * plane] = b;
-                re[q] = a;
-                im[q] = b;
+        for (int q = 0; q < 4; ++q) {
+            double a = ac[(2 * q) * plane], b = ac[(2 * q + 1) * plane];
+            a += x[q] * cn;
+            b -= x[q] * sn;
+            if (full) {
+                const double o = ro[q * plane];
+                a -= o * co;
+                b += o * so;
             }
-            if (emit && interior) contrib = (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
+            ac[(2 * q) * plane] = a;
+            ac[(2 * q + 1) * plane] = b;
+            re[q] = a;
+            im[q] = b;
         }
-        const double tot = block_sum(contrib, sh);
-        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * s.nf + k] = tot;
+        const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
+        if (emit && i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2)
+            contrib = (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
     }
-    // the leaving samples of every frequency were read above: the new one may take a slot now
-    if (in) {
-        double* r = s.ring + (int64_t)(n % s.Mh) * 4 * plane + pl;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) r[q * plane] = x[q];
-    }
+    const double tot = block_sum(contrib, sh);
+    if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = tot;
 }
 
+template <typename real>
+__global__ void k_spec_ring(Fields6<real> eb, Geom g, SpecStep s)
+{
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pl >= plane) return;
+    const int64_t id = (int64_t)s.kp * g.sz + pl;
+    double* r = s.ring + (int64_t)(s.sd->n % s.Mh) * 4 * plane + pl;
+    r[0] = (double)eb.c[0][id];
+    r[plane] = (double)eb.c[1][id];
+    r[2 * plane] = (double)eb.c[3][id];
+    r[3 * plane] = (double)eb.c[4][id];
+}
+
+// One block per frequency: compensated sum of its partials.
 __global__ void k_spec_final(const double* __restrict__ partial, int npartial, SpecStep s, double* __restrict__ series)
 {
     __shared__ double sh[32];
+    const int k = blockIdx.x;
     const int64_t n = s.sd->n;
-    for (int k = 0; k < s.nf; ++k) {
-        double sum = 0.0, comp = 0.0;
-        for (int i = threadIdx.x; i < npartial; i += blockDim.x) {
-            const double v = partial[(int64_t)i * s.nf + k];
-            const double t = sum + v;
-            comp += (fabs(sum) >= fabs(v)) ? (sum - t) + v : (v - t) + sum;
-            sum = t;
-        }
-        const double tot = block_sum(sum + comp, sh);
-        if (threadIdx.x == 0) series[n * s.nf + k] = (n + 1 >= s.M[k]) ? tot * s.scale[k] : 0.0;
+    double sum = 0.0, comp = 0.0;
+    for (int i = threadIdx.x; i < npartial; i += blockDim.x) {
+        const double v = partial[(int64_t)k * npartial + i];
+        const double t = sum + v;
+        comp += (fabs(sum) >= fabs(v)) ? (sum - t) + v : (v - t) + sum;
+        sum = t;
     }
+    const double tot = block_sum(sum + comp, sh);
+    if (threadIdx.x == 0) series[n * s.nf + k] = (n + 1 >= s.M[k]) ? tot * s.scale[k] : 0.0;
 }
 
 template <typename real>
@@ -322,42 +314,52 @@ cudaError_t launch_spectrum_step(const Fields6<real>& eb, const Geom& g, const S
     const int64_t plane = (int64_t)g.nx * g.ny;
     const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
     if ((int)nb > npartial || s.nf < 1) return cudaErrorInvalidValue;
-    k_spec_phase<<<(s.nf + 127) / 128, 128, 0, st>>>(s);
-    k_spec_step<real><<<nb, kRedThreads, 0, st>>>(eb, g, s, partial);
-    k_spec_final<<<1, kRedThreads, 0, st>>>(partial, (int)nb, s, series);
+    k_spec_step<real><<<dim3(nb, s.nf), kRedThreads, 0, st>>>(eb, g, s, partial);
+    k_spec_ring<real><<<nb, kRedThreads, 0, st>>>(eb, g, s);
+    k_spec_final<<<s.nf, kRedThreads, 0, st>>>(partial, (int)nb, s, series);
     count_launches(3);
     return cudaGetLastError();
 }
 
 // ---- bunch sampling ------------------------------------------------------------------------
+// Per-thread sums of the shifted values and their squares: FP64 on the FP64 path; on the
+// FP32-mixed path FP32 per particle and per thread (positions are FP32 offsets there; the
+// shifted values are formed without cancellation: x - centre from the cell index relative to the
+// centre cell, gamma_lab - gamma_ref from gamma - 1 = u^2 / (1 + gamma)), FP64 across threads.
 template <typename real>
 __global__ void __launch_bounds__(kRedThreads) k_bunch_moments(Particles<real> P, int64_t np, Geom g, BunchSample b,
                                                                double* __restrict__ partial)
 {
     __shared__ double sh[32];
     if (b.sd->n % b.every != 0) return;
-    double s1[7] = {0, 0, 0, 0, 0, 0, 0}, s2[7] = {0, 0, 0, 0, 0, 0, 0};
+    real s1[7], s2[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) s1[c] = s2[c] = (real)0;
+    const real cx = (real)(0.5 * (g.nx - 1)), cy = (real)(0.5 * (g.ny - 1)), cz = (real)(0.5 * (g.nz - 1));
+    const real dx = (real)g.dx, dy = (real)g.dy, dz = (real)g.dz;
+    const real g0 = (real)b.g0, gb0 = (real)(b.g0 * b.b0), goff = (real)(b.g0 - b.shift[6]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-        const double ux = P.ux[p], uy = P.uy[p], uz = P.uz[p];
-        double v[7];
-        v[0] = g.x0 + ((double)P.ix[p] + (double)P.fx[p]) * g.dx;
-        v[1] = g.y0 + ((double)P.iy[p] + (double)P.fy[p]) * g.dy;
-        v[2] = g.z0 + ((double)P.iz[p] + (double)P.fz[p]) * g.dz;
-        v[3] = ux;
-        v[4] = uy;
-        v[5] = uz;
-        v[6] = b.g0 * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) + b.b0 * uz);
+        const real ux = (real)P.ux[p], uy = (real)P.uy[p], uz = (real)P.uz[p];
+        const real u2 = ux * ux + uy * uy + uz * uz;
+        const real gm1 = u2 / ((real)1 + sqrt((real)1 + u2));
+        real d[7];
+        d[0] = ((real)(P.ix[p] - (int)cx) - (cx - (real)(int)cx) + P.fx[p]) * dx;
+        d[1] = ((real)(P.iy[p] - (int)cy) - (cy - (real)(int)cy) + P.fy[p]) * dy;
+        d[2] = ((real)(P.iz[p] - (int)cz) - (cz - (real)(int)cz) + P.fz[p]) * dz;
+        d[3] = ux;
+        d[4] = uy;
+        d[5] = uz;
+        d[6] = g0 * gm1 + gb0 * uz + goff;   // gamma0 (gamma + beta0 u_z) - gamma_ref
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
-            const double d = v[c] - b.shift[c];
-            s1[c] += d;
-            s2[c] += d * d;
+            s1[c] += d[c];
+            s2[c] += d[c] * d[c];
         }
     }
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
-        const double t1 = block_sum(s1[c], sh);
-        const double t2 = block_sum(s2[c], sh);
+        const double t1 = block_sum((double)s1[c], sh);
+        const double t2 = block_sum((double)s2[c], sh);
         if (threadIdx.x == 0) {
             partial[(int64_t)blockIdx.x * 14 + c] = t1;
             partial[(int64_t)blockIdx.x * 14 + 7 + c] = t2;

@@ -97,6 +97,7 @@ struct MurArgs {
     int ncomp;
     int order;
     int face0;           // first face handled (2: the TMA stencil wrote the x faces)
+    int kmin, kmax;      // z range of the x faces (1 .. ez-2 unless restricted)
     // face coefficients per normal axis, in the storage type: first order beta_0 (= beta_4),
     // beta_1 (= beta_3); second order gamma_0, gamma_1 and the tangential gammas of the axes
     // (a+1)%3 and (a+2)%3
@@ -116,13 +117,14 @@ __global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
     const int ax = f >> 1, sd = f & 1;
     const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
     const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;   // tangential axes, u before v
-    const int nu = e[u] - 2, nv = e[v] - 2;
+    const int v0 = ax == 0 ? a.kmin : 1, v1 = ax == 0 ? min(a.kmax, e[v] - 2) : e[v] - 2;
+    const int nu = e[u] - 2, nv = v1 - v0 + 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nu * nv) return;
+    if (nv <= 0 || t >= nu * nv) return;
     int p[3];
     p[ax] = sd ? e[ax] - 1 : 0;
     p[u] = 1 + t % nu;
-    p[v] = 1 + t / nu;
+    p[v] = v0 + t / nu;
     const int64_t st[3] = {1, sy, sz};
     const int64_t ib = lin(p[0], p[1], p[2], sy, sz);
     const int64_t iq = ib + (sd ? -st[ax] : st[ax]);   // inward neighbour
@@ -528,6 +530,8 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
 {
     MurArgs<real> a;
     a.face0 = x_faces_done ? 2 : 0;
+    a.kmin = 1;
+    a.kmax = g.nz;
     for (int c = 0; c < 4; ++c) {
         a.n1[c] = L.out[c];
         a.n0[c] = L.n1[c];
@@ -567,6 +571,39 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     count_launches(nl + 2);
     return cudaGetLastError();
 }
+
+template <typename real>
+cudaError_t launch_mur_tfsf_xfaces(const FieldLevels<real>& L, const Geom& g, int order, cudaStream_t st)
+{
+    MurArgs<real> a;
+    a.face0 = 0;
+    a.kmin = 1;
+    a.kmax = 2;
+    for (int c = 0; c < 4; ++c) {
+        a.n1[c] = L.out[c];
+        a.n0[c] = L.n1[c];
+        a.nm[c] = L.n0[c];
+        a.ex[c] = g.nx - (c == 0);
+        a.ey[c] = g.ny - (c == 1);
+        a.ez[c] = g.nz - (c == 2);
+    }
+    a.ncomp = 2;   // A_x, A_y
+    a.order = order;
+    const MurFaceCoef m = mur_face_coef(g, order);
+    for (int ax = 0; ax < 3; ++ax) {
+        a.f0[ax] = (real)m.f0[ax];
+        a.f1[ax] = (real)m.f1[ax];
+        a.ft[ax][0] = (real)m.ft[ax][0];
+        a.ft[ax][1] = (real)m.ft[ax][1];
+    }
+    const int64_t pts = 2 * (int64_t)g.ny;
+    k_mur_faces<real><<<dim3((unsigned)((pts + 127) / 128), 2, 2), 128, 0, st>>>(a, g.sy, g.sz);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_mur_tfsf_xfaces<float>(const FieldLevels<float>&, const Geom&, int, cudaStream_t);
+template cudaError_t launch_mur_tfsf_xfaces<double>(const FieldLevels<double>&, const Geom&, int, cudaStream_t);
 
 template <typename real>
 cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, const EmitBox& bx,

@@ -66,6 +66,11 @@ template <typename real>
 cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf, const SeedField& s,
                         const StepDev* sd, double T0, double* fbuf, cudaStream_t st);
 
+// Mur values of the x-face nodes of z planes 1 and 2 of A_x and A_y again, after the TF/SF
+// correction changed their inward neighbours (the FP32 TMA stencil wrote them before it).
+template <typename real>
+cudaError_t launch_mur_tfsf_xfaces(const FieldLevels<real>& L, const Geom& g, int order, cudaStream_t st);
+
 // Mur boundary values of level n+1: the faces, then the edges, then the corners.  With
 // x_faces_done the TMA stencil of this step has already written the x faces.
 template <typename real>
@@ -193,7 +198,6 @@ struct SpecStep {
     const double* scale;    // device, nf: lab factor x (2 / M)^2 x dx dy / (2 mu0)
     double* ring;           // Mh x 4 x plane samples (Ex, Ey, Bx, By)
     double* acc;            // nf x 8 x plane accumulators
-    double* phase;          // nf x 4: cos, sin of w t_n and of w t_{n-M}
 };
 // The powers of step n go to series[n * nf + k] (zero until a frequency's window is complete).
 template <typename real>

@@ -226,7 +226,6 @@ struct RunT final : mithra_run {
     double* spec_scale = nullptr;
     double* spec_ring = nullptr;
     double* spec_acc = nullptr;
-    double* spec_phase = nullptr;
     double* spec_partial = nullptr;
     double* ser_s = nullptr;   // ser_cap x nf
     // seed through TF/SF planes (seed.type < 0: none)
@@ -349,11 +348,10 @@ struct RunT final : mithra_run {
             spec_omega = (double*)mem.get((size_t)nf * 8);
             spec_M = (int*)mem.get((size_t)nf * 4);
             spec_scale = (double*)mem.get((size_t)nf * 8);
-            spec_phase = (double*)mem.get((size_t)nf * 4 * 8);
             spec_ring = (double*)mem.get((size_t)Mh * 4 * plane * 8);
             spec_acc = (double*)mem.get((size_t)nf * 8 * plane * 8);
             spec_partial = (double*)mem.get((size_t)nf * npartial * 8);
-            if (!spec_omega || !spec_M || !spec_scale || !spec_phase || !spec_ring || !spec_acc || !spec_partial)
+            if (!spec_omega || !spec_M || !spec_scale || !spec_ring || !spec_acc || !spec_partial)
                 return fail(MITHRA_ENOMEM, "device allocation failed (spectrum)");
             CU(cudaMemcpyAsync(spec_omega, om.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, stream));
             CU(cudaMemcpyAsync(spec_M, Mv.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, stream));
@@ -556,19 +554,20 @@ struct RunT final : mithra_run {
         if (tma) {
             real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
             real* prevp[4] = {pot[lev(0)][0], pot[lev(0)][1], pot[lev(0)][2], pot[lev(0)][3]};
-            // with a seed the Mur x faces must see the TF/SF-corrected planes: no fused faces
-            CU(launch_stencil_tma<real>(tma, outp, prevp, seed.type < 0 ? &murc : nullptr, lev(1), lev(0), g, cf,
-                                        ncomp, err_word, stream));
+            CU(launch_stencil_tma<real>(tma, outp, prevp, &murc, lev(1), lev(0), g, cf, ncomp, err_word, stream));
         } else {
             CU(launch_stencil<real>(L, g, cf, ncomp, stream));
         }
+        const bool xf = tma != nullptr && tma_x_faces<real>();   // the stencil wrote the Mur x faces
         if (seed.type >= 0) {
             real* outs[2] = {pot[lev(2)][0], pot[lev(2)][1]};
             CU(launch_tfsf<real>(outs, g, cf, seed, sd, d.T0, seed_buf, stream));
+            // the x-face nodes next to the corrected planes see their new inward neighbours
+            if (xf) CU(launch_mur_tfsf_xfaces<real>(L, g, mur_order, stream));
         }
         pend(MITHRA_K_STENCIL, e0);
         pbeg(MITHRA_K_MUR, &e0);
-        CU(launch_mur<real>(L, g, mur_order, ncomp, tma != nullptr && tma_x_faces<real>() && seed.type < 0, stream));
+        CU(launch_mur<real>(L, g, mur_order, ncomp, xf, stream));
         pend(MITHRA_K_MUR, e0);
         pbeg(MITHRA_K_POWER, &e0);
         {
@@ -596,7 +595,6 @@ struct RunT final : mithra_run {
                 sp.scale = spec_scale;
                 sp.ring = spec_ring;
                 sp.acc = spec_acc;
-                sp.phase = spec_phase;
                 CU(launch_spectrum_step<real>(E6, g, sp, spec_partial, npartial, ser_s, stream));
             }
         }
