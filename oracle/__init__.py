@@ -60,6 +60,13 @@ class Params(C.Structure):
     ]
 
 
+class Ellipsoid(C.Structure):
+    _fields_ = [("uniform", C.c_int32), ("gamma", C.c_double), ("sig", C.c_double * 3),
+                ("sig_u", C.c_double * 3), ("cse_sigma", C.c_double), ("lambda_r", C.c_double),
+                ("bunching", C.c_double), ("bunching_phase", C.c_double), ("shot_noise", C.c_int32),
+                ("charge_e", C.c_double)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -87,6 +94,9 @@ def _load():
             lib.orc_external_field.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp, dp]
             lib.orc_lab_field.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp, dp]
             lib.orc_boris.argtypes = [dp, dp, dp, C.c_double]
+            lib.orc_halton.restype = C.c_double
+            lib.orc_halton.argtypes = [C.c_uint, C.c_uint]
+            lib.orc_ellipsoid_bunch.argtypes = [C.POINTER(Ellipsoid), C.c_int64, dp]
             lib.orc_seed_potential.argtypes = [C.c_void_p] + [C.c_double] * 4 + [dp]
             lib.orc_mur.argtypes = [C.c_void_p, C.c_int]
             lib.orc_stencil.argtypes = [C.c_void_p, C.c_int]
@@ -120,6 +130,17 @@ def params_from(w, periodic=(0, 0, 0)) -> Params:
     p.seed_waist, p.seed_focus, p.seed_offset = w.seed_waist, w.seed_focus, w.seed_offset
     p.seed_pulse_fwhm, p.seed_cep_deg = w.seed_pulse_fwhm, w.seed_cep_deg
     return p
+
+
+def halton(i: int, j: int) -> float:
+    return _load().orc_halton(i, j)
+
+
+def ellipsoid_bunch(e: Ellipsoid, n: int) -> np.ndarray:
+    out = np.zeros((n, 6))
+    if n:
+        _load().orc_ellipsoid_bunch(C.byref(e), n, _dp(out))
+    return out
 
 
 INFO_KEYS = ("gamma0", "beta0", "dx", "dy", "dz", "dt", "dtb", "A", "x0", "y0", "z0", "T0",

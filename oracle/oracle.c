@@ -1235,3 +1235,92 @@ void orc_diag(const orc_run *r, double *field_energy, double *bunching)
         bunching[2] = im / n;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Quasi-random bunch loading (Sec. "Electron Bunch Generation": Halton       */
+/* numbers, Eqs. uniform1D, gaussian1D, gaussian2D, bunchingFactor,           */
+/* negativeExponential; CSE edges of the uniform profile).                    */
+/* ------------------------------------------------------------------------- */
+
+static const unsigned PRIMES[20] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61, 67, 71};
+
+double orc_halton(unsigned i, unsigned j)
+{
+    const unsigned p = PRIMES[i];
+    double x = 0.0, scale = 1.0 / p;
+    while (j > 0) {
+        x += (double)(j % p) * scale;   /* digit d_m of j lands at p^-(m+1) */
+        j /= p;
+        scale /= p;
+    }
+    return 1.0 - x;
+}
+
+/* Base assignment (the manual leaves it open): transverse positions (Eq. gaussian2D) from the
+   bases 2 and 3, transverse momenta from 5 and 7, the longitudinal position from 11 (and 13 for
+   a Gaussian profile, Eq. gaussian1D), the longitudinal momentum spread from 17 and 19, the
+   shot-noise amplitude and phase of slice s from 23 and 29 at index s + 1.  Particle p uses
+   index p + 1 (index 0 is the same point in every base).  Uniform profile with CSE edges: of
+   the n particles, n_u = round(n L / (L + sqrt(2 pi) w)) fill [-sig_z, sig_z] (L = 2 sig_z) by
+   Eq. uniform1D, the others form a Gaussian of rms w with the same peak line density whose lower
+   half is moved to the tail (-sig_z + z) and upper half to the head (sig_z + z). */
+void orc_ellipsoid_bunch(const orc_ellipsoid *e, int64_t n, double *out6)
+{
+    const double L = 2.0 * e->sig[2];
+    int64_t nu = n;
+    if (e->uniform && e->cse_sigma > 0.0) nu = (int64_t)llround((double)n * L / (L + sqrt(2.0 * PI) * e->cse_sigma));
+    const double uz0 = sqrt(e->gamma * e->gamma - 1.0);
+    for (int64_t p = 0; p < n; ++p) {
+        const unsigned j = (unsigned)(p + 1);
+        double *q = out6 + 6 * p;
+        const double r1 = sqrt(-2.0 * log(orc_halton(0, j))), a1 = 2.0 * PI * orc_halton(1, j);
+        q[0] = e->sig[0] * r1 * cos(a1);
+        q[1] = e->sig[1] * r1 * sin(a1);
+        const double r2 = sqrt(-2.0 * log(orc_halton(2, j))), a2 = 2.0 * PI * orc_halton(3, j);
+        q[3] = e->sig_u[0] * r2 * cos(a2);
+        q[4] = e->sig_u[1] * r2 * sin(a2);
+        double z;
+        if (!e->uniform) {
+            z = e->sig[2] * sqrt(-2.0 * log(orc_halton(4, j))) * cos(2.0 * PI * orc_halton(5, j));
+        } else if (p < nu) {
+            z = L * (orc_halton(4, j) - 0.5);
+        } else {
+            const unsigned je = (unsigned)(p - nu + 1);
+            const double ze = e->cse_sigma * sqrt(-2.0 * log(orc_halton(4, je))) * cos(2.0 * PI * orc_halton(5, je));
+            z = ze < 0.0 ? -e->sig[2] + ze : e->sig[2] + ze;
+        }
+        q[2] = z;
+        q[5] = uz0 + e->sig_u[2] * sqrt(-2.0 * log(orc_halton(6, j))) * cos(2.0 * PI * orc_halton(7, j));
+    }
+    /* bunching (Eq. bunchingFactor, read in the lab before the boost): z -> z - (2 b / k) sin(k z + phi) */
+    if (e->lambda_r > 0.0 && (e->bunching > 0.0 || e->shot_noise)) {
+        const double k = 2.0 * PI / e->lambda_r;
+        if (e->bunching > 0.0)
+            for (int64_t p = 0; p < n; ++p) {
+                double *z = out6 + 6 * p + 2;
+                *z -= (2.0 * e->bunching / k) * sin(k * *z + e->bunching_phase);
+            }
+        if (e->shot_noise && n > 0) {
+            /* slice s = floor(z / lambda_r) - s0: electrons N_e,s = charge_e n_s / n; amplitude
+               sqrt(-2 ln x_s) / sqrt(N_e,s) (Eq. negativeExponential), phase 2 pi y_s */
+            int64_t s0 = INT64_MAX, s1 = INT64_MIN;
+            for (int64_t p = 0; p < n; ++p) {
+                const int64_t s = (int64_t)floor(out6[6 * p + 2] / e->lambda_r);
+                if (s < s0) s0 = s;
+                if (s > s1) s1 = s;
+            }
+            const int64_t ns = s1 - s0 + 1;
+            int64_t *cnt = (int64_t *)calloc((size_t)ns, sizeof(int64_t));
+            for (int64_t p = 0; p < n; ++p) cnt[(int64_t)floor(out6[6 * p + 2] / e->lambda_r) - s0]++;
+            for (int64_t p = 0; p < n; ++p) {
+                double *z = out6 + 6 * p + 2;
+                const int64_t s = (int64_t)floor(*z / e->lambda_r) - s0;
+                const double ne = e->charge_e * (double)cnt[s] / (double)n;
+                const double b = sqrt(-2.0 * log(orc_halton(8, (unsigned)(s + 1)))) / sqrt(ne);
+                const double ph = 2.0 * PI * orc_halton(9, (unsigned)(s + 1));
+                *z -= (2.0 * b / k) * sin(k * *z + ph);
+            }
+            free(cnt);
+        }
+    }
+}

@@ -144,6 +144,27 @@ void orc_rotate_levels(orc_run *r);
 /* Deposition alone: J of the move old6 -> new6 (rest frame, n x 6) and rho at new6. */
 void orc_deposit_moves(orc_run *r, const double *old6, const double *new6, int64_t n);
 
+/* Quasi-random bunch loading (Sec. "Electron Bunch Generation"; Sec. BUNCH, ellipsoid). */
+typedef struct orc_ellipsoid {
+    int32_t uniform;          /* 0 Gaussian current profile, 1 uniform over [-sig_z, sig_z] */
+    double gamma;             /* mean Lorentz factor (momentum along +z) */
+    double sig[3];            /* position spreads (sig_z: half length when uniform) */
+    double sig_u[3];          /* spreads of gamma*beta_x, gamma*beta_y, gamma*beta_z */
+    double cse_sigma;         /* uniform profile: rms width of the Gaussian edges (<= 0: none) */
+    double lambda_r;          /* wavelength of the bunching and of the shot-noise slices */
+    double bunching;          /* bunching factor b_f at lambda_r */
+    double bunching_phase;    /* its phase (rad) */
+    int32_t shot_noise;       /* 1: shot-noise modulation per slice of length lambda_r */
+    double charge_e;          /* electrons in the bunch (shot-noise amplitude) */
+} orc_ellipsoid;
+
+/* The Halton number of index j in the i-th prime base (i < 20): one minus the radical inverse
+   of j (the digits of j in base p mirrored about the radix point). */
+double orc_halton(unsigned i, unsigned j);
+
+/* n lab-frame macro-particles (n x 6: x, y, z, gamma*beta_x, gamma*beta_y, gamma*beta_z). */
+void orc_ellipsoid_bunch(const orc_ellipsoid *e, int64_t n, double *out6);
+
 #ifdef __cplusplus
 }
 #endif
