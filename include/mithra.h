@@ -122,6 +122,37 @@ typedef struct mithra_seed {
     double cep_deg;            /* carrier envelope phase, degrees */
 } mithra_seed;
 
+/* An ellipsoid bunch loaded quasi-randomly (Sec. BUNCH, bunch-initialization of type ellipsoid;
+   Sec. "Electron Bunch Generation"). */
+typedef struct mithra_ellipsoid {
+    int32_t uniform;           /* 0 Gaussian current profile (rms sig[2]), 1 uniform over [-sig[2], sig[2]] */
+    double gamma;              /* mean Lorentz factor; the mean momentum points along +z */
+    double sig[3];             /* sigma-position: rms x, y (and z for a Gaussian profile), lab, m */
+    double sig_u[3];           /* sigma-momentum: rms gamma*beta_x, gamma*beta_y, gamma*beta_z */
+    double cse_sigma;          /* uniform profile: rms width of the Gaussian edges (<= 0: none) */
+    double lambda_r;           /* lab wavelength of the bunching and of the shot-noise slices */
+    double bunching;           /* bunching factor at lambda_r (0: none) */
+    double bunching_phase;     /* its phase, rad */
+    int32_t shot_noise;        /* 1: shot noise per slice of length lambda_r */
+    double charge_e;           /* electrons in the bunch (shot-noise amplitude) */
+} mithra_ellipsoid;
+
+/* Fill out6 (host, n x 6, caller-owned: x, y, z relative to the bunch centre, gamma*beta_x,y,z;
+   lab frame) with a quasi-random ellipsoid bunch, computed on the current device: particle p
+   takes the Halton numbers of index p + 1 (one minus the radical inverse of the index) in the
+   prime bases 2, 3 (x, y by Eq. gaussian2D), 5, 7 (transverse momenta), 11, 13 (z by Eq.
+   uniform1D or gaussian1D), 17, 19 (longitudinal momentum spread).  A uniform profile with
+   cse_sigma > 0 gives n L / (L + sqrt(2 pi) cse_sigma) particles to the flat part (L = 2 sig[2])
+   and the rest to a Gaussian of that rms and the same peak line density whose lower half is moved
+   to the tail and upper half to the head, against coherent emission from the profile's ends.
+   Bunching moves z by -(2 b / k) sin(k z + phase), k = 2 pi / lambda_r; shot noise does the same
+   per slice of length lambda_r with amplitude sqrt(-2 ln x_s) / sqrt(N_e,s) (Eq.
+   negativeExponential; N_e,s the slice's share of charge_e) and phase 2 pi y_s, x_s and y_s the
+   Halton numbers of the slice in bases 23 and 29.  Work is enqueued on `stream` (a cudaStream_t,
+   NULL: legacy default stream) and the call returns when out6 is filled.  Device scratch (48 B
+   per particle) comes from the installed allocator.  Errors: EINVAL, ENOMEM, ECUDA. */
+int mithra_ellipsoid_bunch(const mithra_ellipsoid *e, int64_t n, double *out6, void *stream);
+
 /* Install the device allocator used by every later mithra_create (process-wide).
    alloc(ctx, bytes) returns a device pointer or NULL; free(ctx, ptr).  Pass NULLs to restore
    cudaMalloc/cudaFree.  Runs created earlier keep the allocator they were created with. */

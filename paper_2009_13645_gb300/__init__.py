@@ -48,6 +48,13 @@ class Undulator(C.Structure):
                 ("gap", C.c_double), ("n_modules", C.c_int32), ("taper", C.c_double)]
 
 
+class Ellipsoid(C.Structure):
+    _fields_ = [("uniform", C.c_int32), ("gamma", C.c_double), ("sig", C.c_double * 3),
+                ("sig_u", C.c_double * 3), ("cse_sigma", C.c_double), ("lambda_r", C.c_double),
+                ("bunching", C.c_double), ("bunching_phase", C.c_double), ("shot_noise", C.c_int32),
+                ("charge_e", C.c_double)]
+
+
 class Seed(C.Structure):
     _fields_ = [("type", C.c_int32), ("a0", C.c_double), ("lambda_", C.c_double), ("pol_deg", C.c_double),
                 ("waist", C.c_double), ("focus", C.c_double), ("offset", C.c_double),
@@ -89,6 +96,7 @@ def load(rebuild: bool = False):
     L.mithra_radiated_power.argtypes = [vp, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_onaxis_field.argtypes = [vp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_set_seed.argtypes = [vp, C.POINTER(Seed)]
+    L.mithra_ellipsoid_bunch.argtypes = [C.POINTER(Ellipsoid), C.c_int64, dp, vp]
     L.mithra_power_spectrum.argtypes = [vp, dp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_bunch_series.argtypes = [vp, dp, C.c_size_t, C.POINTER(C.c_size_t)]
     L.mithra_diag.argtypes = [vp, dp, dp]
@@ -247,6 +255,15 @@ def grid_from(w, precision=None, sort_every=0) -> Grid:
     g.nf_min, g.nf_max, g.nf_points = w.nf_min, w.nf_max, w.nf_points
     g.bunch_every = w.bunch_every
     return g
+
+
+def ellipsoid_bunch(e: Ellipsoid, n: int, stream=None) -> np.ndarray:
+    """n lab-frame macro-particles (n x 6) of a quasi-random ellipsoid bunch, computed on the GPU."""
+    L = load()
+    out = np.zeros((int(n), 6))
+    _check(L.mithra_ellipsoid_bunch(C.byref(e), int(n), _dp(out) if n else None,
+                                    C.c_void_p(int(stream)) if stream is not None else None))
+    return out
 
 
 def seed_from(w) -> Seed:

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmithra.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mithra.cu", "fields.cu", "particles.cu", "sort.cu", "diag.cu", "noalloc.cu", "server.cu", "stencil_tma.cu"]
+SOURCES = ["mithra.cu", "fields.cu", "particles.cu", "sort.cu", "diag.cu", "noalloc.cu", "server.cu", "stencil_tma.cu",
+           "loading.cu"]
 
 
 def nvcc() -> str:
