@@ -231,8 +231,11 @@ __device__ __forceinline__ void split_pos(double X, int32_t* c, real* f)
 // shared memory, node (i, j, k) at (k - oz) sz + (j - oy) sy + (i - ox), accumulated in 32-bit
 // fixed point - shared-memory integer adds are native, floating-point ones are not - with a
 // scale per grid chosen so that no sum can overflow (see the push kernel).
+// Offsets are the target's own type: 64-bit in the grids, 32-bit in the tile (at most 4 x 1024
+// entries), whose adds address shared memory directly from the tile's shared-window base.
 template <typename real>
 struct GlobalTarget {
+    using off_t = int64_t;
     real* c[4];
     int64_t sy, sz;
     __device__ __forceinline__ int64_t at(int i, int j, int k) const { return (int64_t)k * sz + (int64_t)j * sy + i; }
@@ -240,18 +243,17 @@ struct GlobalTarget {
 };
 
 struct TileTarget {
+    using off_t = int;
     int* t;
+    unsigned base;   // shared-window address of t[0]
     int vol;
-    int64_t sy, sz;
+    int sy, sz;
     int ox, oy, oz;
     float scale[4];
-    __device__ __forceinline__ int64_t at(int i, int j, int k) const
+    __device__ __forceinline__ int at(int i, int j, int k) const { return (k - oz) * sz + (j - oy) * sy + (i - ox); }
+    __device__ __forceinline__ void add(int comp, int off, float v) const
     {
-        return (int64_t)(k - oz) * sz + (int64_t)(j - oy) * sy + (i - ox);
-    }
-    __device__ __forceinline__ void add(int comp, int64_t off, float v) const
-    {
-        const unsigned a = (unsigned)__cvta_generic_to_shared(t + comp * vol + off);
+        const unsigned a = base + 4u * (unsigned)(comp * vol + off);
         asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(__float2int_rn(v * scale[comp])) : "memory");
     }
 };
@@ -270,8 +272,9 @@ __device__ __forceinline__ void deposit_piece(const real a[3], const real b[3], 
         d[l] = b[l] - a[l];
         mid[l] = la[l] + (real)0.5 * d[l];
     }
-    const int64_t o = T.at(base[0] + cl[0], base[1] + cl[1], base[2] + cl[2]);
-    const int64_t st[3] = {1, T.sy, T.sz};
+    using off_t = typename Tgt::off_t;
+    const off_t o = T.at(base[0] + cl[0], base[1] + cl[1], base[2] + cl[2]);
+    const off_t st[3] = {1, (off_t)T.sy, (off_t)T.sz};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
         if (d[l] == (real)0) continue;
@@ -313,7 +316,7 @@ __device__ __forceinline__ void deposit_rho(const int c[3], const real fo[3], re
     const real wx[2] = {(real)1 - fo[0], fo[0]};
     const real wy[2] = {(real)1 - fo[1], fo[1]};
     const real wz[2] = {(real)1 - fo[2], fo[2]};
-    const int64_t o = T.at(c[0], c[1], c[2]);
+    const typename Tgt::off_t o = T.at(c[0], c[1], c[2]);
 #pragma unroll
     for (int K = 0; K < 2; ++K)
 #pragma unroll
@@ -605,9 +608,10 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 // most 1/2.
                 TileTarget T;
                 T.t = tile;
+                T.base = (unsigned)__cvta_generic_to_shared(tile);
                 T.vol = vol;
                 T.sy = tx;
-                T.sz = (int64_t)tx * ty;
+                T.sz = tx * ty;
                 T.ox = box[0];
                 T.oy = box[1];
                 T.oz = box[2];
