@@ -2,9 +2,11 @@
 // Mur absorbing boundaries (Sec. "Boundary Truncation") and E, B at nodes
 // (Sec. "Field Evaluation").
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace mithra {
 
@@ -238,32 +240,38 @@ struct EmitArgs {
     int kp;              // plane emitted in full (< 0: none)
     const int* box;      // cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit; null: whole grid
     int* box_reset;      // box the next push reduces into: reset to empty here (may be null)
+    int* err;            // set when a bounded wait on the tensor copies expired (may be null)
 };
 
 constexpr int EX = 32, EY = 8, EKZ = 8;              // tile and planes per block
-constexpr int RW = EX + 2, RH = EY + 2, RN = RW * RH; // region: columns i0-1 .. i0+32, rows j0-1 .. j0+8
-constexpr int EHALO = 2 * RW + 2 * EY;                // region positions outside the tile
+constexpr int RL = EX + 2, RH = EY + 2;               // region: columns i0-1 .. i0+32, rows j0-1 .. j0+8
+constexpr int RW = kEmitBoxW, RN = RW * RH;           // region rows are stored kEmitBoxW wide
+constexpr int EHALO = 2 * RL + 2 * EY;                // region positions outside the tile
 constexpr int ENT = EX * EY;                          // threads per block
 static_assert(EHALO <= ENT, "emit tile: one halo position per thread at most");
+static_assert(RW >= RL && RH == kEmitBoxH, "emit region inside the tensor-map box");
 
-// Shared memory of one block: raw[p % ENS] holds A_x^n, A_x^{n+1}, A_y^n, A_y^{n+1}, A_z^n,
-// A_z^{n+1}, phi of plane p over the region, filled by asynchronous copies ENS - 1 planes ahead;
-// sum[p & 1] the node-averaged sums S_x, S_y, S_z of plane p.
+// Shared memory of one block: raw[s] holds A_x^n, A_x^{n+1}, A_y^n, A_y^{n+1}, A_z^n, A_z^{n+1},
+// phi of plane p (s = (p - first plane) % ENS) over the region, filled ENS - 1 planes ahead;
+// sum[p & 1] the node-averaged sums S_x, S_y, S_z of plane p.  Each array of raw starts on a
+// 128-byte boundary (the tensor copies' destination alignment).
 constexpr int ENS = 4;
 template <typename real>
 struct EmitSmem {
-    real raw[ENS][7][RN];
+    static constexpr int RS = (RN * (int)sizeof(real) + 127) / 128 * 128 / (int)sizeof(real);
+    real raw[ENS][7][RS];
     real sum[2][3][RN];
+    uint64_t bar[ENS];
 };
 
 // Region position of halo entry h: the rows above and below the tile, then the columns left
 // and right of it.
 __device__ __forceinline__ int halo_pos(int h)
 {
-    if (h < RW) return h;
-    if (h < 2 * RW) return (RH - 1) * RW + (h - RW);
-    if (h < 2 * RW + EY) return (h - 2 * RW + 1) * RW;
-    return (h - 2 * RW - EY + 1) * RW + RW - 1;
+    if (h < RL) return h;
+    if (h < 2 * RL) return (RH - 1) * RW + (h - RL);
+    if (h < 2 * RL + EY) return (h - 2 * RL + 1) * RW;
+    return (h - 2 * RL - EY + 1) * RW + RL - 1;
 }
 
 // Asynchronous global -> shared copy of one value; n = 0 writes zero and reads nothing.
@@ -280,11 +288,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <typename real>
-__global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2) k_emit(EmitArgs<real> a, Geom g)
+// TM: the region of each plane arrives by seven tensor copies (one per array, issued by one
+// thread, completing on the stage's mbarrier); the tile grid then starts on a 16-byte boundary
+// of the row, one node left of the box's first interior column rounded down.  Otherwise every
+// thread copies its own node and halo position with per-element asynchronous copies.
+template <typename real, bool TM>
+__global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
+    k_emit(EmitArgs<real> a, Geom g, const __grid_constant__ EmitMaps em)
 {
-    extern __shared__ __align__(16) unsigned char emit_smem[];
-    EmitSmem<real>& sm = *reinterpret_cast<EmitSmem<real>*>(emit_smem);
+    extern __shared__ unsigned char emit_smem_raw[];
+    EmitSmem<real>& sm = *reinterpret_cast<EmitSmem<real>*>(
+        emit_smem_raw + ((128 - (mithra::su32(emit_smem_raw) & 127)) & 127));
     const int t = threadIdx.x, tx = t % EX, ty = t / EX;
     if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t < 6)
         a.box_reset[t] = t < 3 ? 0x7fffffff : (int)0x80000000;
@@ -308,8 +322,10 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2) k_emit(EmitArg
         kb = min((int)(blockIdx.z + 1) * EKZ, bh[2]);
     }
     // tiles start at the region's corner, so a box that is not aligned to the tile grid costs no
-    // extra tiles (the grid has enough blocks for the whole interior)
-    const int i0 = xl + (int)blockIdx.x * EX, j0 = yl + (int)blockIdx.y * EY;
+    // extra tiles (the grid has enough blocks for the whole interior); with tensor copies the
+    // corner is rounded down to a 16-byte boundary of the row
+    constexpr int AL = TM ? 16 / (int)sizeof(real) : 1;
+    const int i0 = (xl - 1) / AL * AL + 1 + (int)blockIdx.x * EX, j0 = yl + (int)blockIdx.y * EY;
     if (ka > kb || xl > xh || yl > yh || i0 > xh || j0 > yh) return;
     const int i = i0 + tx, j = j0 + ty;
     const bool emit = i >= xl && i <= xh && j >= yl && j <= yh;
@@ -324,8 +340,8 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2) k_emit(EmitArg
     const int qh = has_halo ? halo_pos(t) : qo;
     // which sums the halo position needs: S_x on the rows above / below the tile, S_y on the
     // columns left / right of it, S_z and phi on both
-    const bool hrow = has_halo && t < 2 * RW && (qh % RW) != 0;
-    const bool hcol = has_halo && t >= 2 * RW;
+    const bool hrow = has_halo && t < 2 * RL && (qh % RW) != 0;
+    const bool hcol = has_halo && t >= 2 * RL;
     auto offset = [&](int q, bool& in) -> int64_t {
         const int ii = i0 - 1 + q % RW, jj = j0 - 1 + q / RW;
         in = ii <= g.nx - 1 && jj <= g.ny - 1;
@@ -333,41 +349,78 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2) k_emit(EmitArg
     };
     bool in_o, in_h;
     const int64_t off_o = offset(qo, in_o), off_h = offset(qh, in_h);
-    const real* srcs[7] = {a.a0[0], a.a1[0], a.a0[1], a.a1[1], a.a0[2], a.a1[2], a.phi ? a.phi : a.a0[0]};
     const bool use_phi = a.phi != nullptr;
-    // copies of plane p into its stage, one commit group per plane (empty past the last plane)
+    const int pfirst = ka - 1, plast = kb + 1;
+    auto stage = [&](int p) { return (p - pfirst) % ENS; };
+    auto parity = [&](int p) { return (uint32_t)(((p - pfirst) / ENS) & 1); };
+
+    // copies of plane p into its stage: TM, by thread 0 (nothing past the last plane);
+    // otherwise one commit group per plane and thread (empty past the last plane)
+    int last_issued = pfirst - 1;
     auto issue = [&](int p) {
-        if (p <= kb + 1) {
-            real(*st)[RN] = sm.raw[p % ENS];
-            const int64_t pz = (int64_t)p * sz;
-#pragma unroll
-            for (int c = 0; c < 7; ++c) cp_async_val(&st[c][qo], srcs[c] + pz + off_o, in_o && (c < 6 || use_phi));
-            if (has_halo) {
+        if constexpr (TM) {
+            if (p <= plast) {
+                real(*st)[EmitSmem<real>::RS] = sm.raw[stage(p)];
+                uint64_t* bar = &sm.bar[stage(p)];
+                const int nc = use_phi ? 7 : 6;
+                mithra::mbar_expect_tx(bar, (uint32_t)(nc * RN * sizeof(real)));
+                for (int c = 0; c < nc; ++c) mithra::tma_load_3d(st[c], &em.m[c], i0 - 1, j0 - 1, p, bar);
+                last_issued = p;
+            }
+        } else {
+            if (p <= plast) {
+                const real* srcs[7] = {a.a0[0], a.a1[0], a.a0[1], a.a1[1], a.a0[2], a.a1[2], a.phi ? a.phi : a.a0[0]};
+                real(*st)[EmitSmem<real>::RS] = sm.raw[stage(p)];
+                const int64_t pz = (int64_t)p * sz;
 #pragma unroll
                 for (int c = 0; c < 7; ++c)
-                    cp_async_val(&st[c][qh], srcs[c] + pz + off_h, in_h && (c < 6 || use_phi));
+                    cp_async_val(&st[c][qo], srcs[c] + pz + off_o, in_o && (c < 6 || use_phi));
+                if (has_halo) {
+#pragma unroll
+                    for (int c = 0; c < 7; ++c)
+                        cp_async_val(&st[c][qh], srcs[c] + pz + off_h, in_h && (c < 6 || use_phi));
+                }
             }
+            cp_async_commit();
         }
-        cp_async_commit();
     };
     auto navg = [](real u, real w) { return (real)0.5 * (u + w); };
 
+    if constexpr (TM) {
+        if (t == 0) {
+            for (int s = 0; s < ENS; ++s) mithra::mbar_init(&sm.bar[s], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (t == 0)
+            for (int d = 0; d < ENS - 1; ++d) issue(pfirst + d);
+    } else {
 #pragma unroll
-    for (int d = 0; d < ENS - 1; ++d) issue(ka - 1 + d);
+        for (int d = 0; d < ENS - 1; ++d) issue(pfirst + d);
+    }
     // per-column state: A_z at plane p-1 (own and halo position); S_x, S_y, phi at planes p-2 (0)
     // and p-1 (1); the partial E, B of plane p-1
     real az0m = 0, az1m = 0, haz0m = 0, haz1m = 0;
     real sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0, ph0 = 0, ph1 = 0;
     real ex1 = 0, ey1 = 0, ez1 = 0, bz1 = 0, bxp1 = 0, byp1 = 0;
-    for (int p = ka - 1; p <= kb + 1; ++p) {
-        cp_async_wait<ENS - 2>();   // this thread's copies of plane p have landed
-        __syncthreads();            // everyone's have; everyone is done with plane p-1's stage
-        issue(p + ENS - 1);         // into the stage of plane p-1
-        const real(*r)[RN] = sm.raw[p % ENS];
+    bool ok = true;
+    int p = pfirst;
+    for (; p <= plast; ++p) {
+        if constexpr (TM) {
+            // plane p has landed; everyone is done with plane p-1's stage
+            ok = __syncthreads_and(mithra::mbar_wait(&sm.bar[stage(p)], parity(p))) != 0;
+            if (!ok) break;
+            if (t == 0) issue(p + ENS - 1);
+        } else {
+            cp_async_wait<ENS - 2>();   // this thread's copies of plane p have landed
+            __syncthreads();            // everyone's have; everyone is done with plane p-1's stage
+            issue(p + ENS - 1);         // into the stage of plane p-1
+        }
+        const real(*r)[EmitSmem<real>::RS] = sm.raw[stage(p)];
         const int b = p & 1;
         // node averages and sums of plane p at this thread's positions (A_z of the first plane
         // has no previous plane: its S_z and E_z are never read)
-        const real az0 = r[4][qo], az1 = r[5][qo], php = r[6][qo];
+        const real az0 = r[4][qo], az1 = r[5][qo], php = use_phi ? r[6][qo] : (real)0;
         const real nx0 = navg(r[0][qo], r[0][qo - 1]), nx1 = navg(r[1][qo], r[1][qo - 1]);
         const real ny0 = navg(r[2][qo], r[2][qo - RW]), ny1 = navg(r[3][qo], r[3][qo - RW]);
         const real nz0 = navg(az0, az0m), nz1 = navg(az1, az1m);
@@ -425,7 +478,15 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2) k_emit(EmitArg
         // sum[b] is next written two planes later, after the first barrier of the next plane,
         // which every thread reaches only once it is done with it
     }
-    cp_async_wait<0>();
+    if constexpr (TM) {
+        if (!ok && t == 0) {
+            // a wait expired: report it and let the copies still in flight land before exiting
+            if (a.err) atomicExch(a.err, 1);
+            for (int pp = p; pp <= last_issued; ++pp) mithra::mbar_wait(&sm.bar[stage(pp)], parity(pp));
+        }
+    } else {
+        cp_async_wait<0>();
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -625,12 +686,26 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     a.kp = bx.kp;
     a.box = bx.box;
     a.box_reset = bx.box_reset;
+    a.err = bx.err;
     a.nchunk = (g.nz - 2 + EKZ - 1) / EKZ;
-    const dim3 grd((g.nx - 2 + EX - 1) / EX, (g.ny - 2 + EY - 1) / EY, a.nchunk + (a.kp >= 1 ? 1 : 0));
-    static const cudaError_t attr = cudaFuncSetAttribute(k_emit<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)sizeof(EmitSmem<real>));
-    if (attr != cudaSuccess) return attr;
-    k_emit<real><<<grd, ENT, sizeof(EmitSmem<real>), st>>>(a, g);
+    constexpr int smem = (int)sizeof(EmitSmem<real>) + 128;
+    if (bx.maps) {
+        // tiles start up to 16 / sizeof(real) - 1 columns left of the region's first column
+        const dim3 grd((g.nx - 2 + 16 / (int)sizeof(real) - 1 + EX - 1) / EX, (g.ny - 2 + EY - 1) / EY,
+                       a.nchunk + (a.kp >= 1 ? 1 : 0));
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(k_emit<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (attr != cudaSuccess) return attr;
+        k_emit<real, true><<<grd, ENT, smem, st>>>(a, g, *bx.maps);
+    } else {
+        const dim3 grd((g.nx - 2 + EX - 1) / EX, (g.ny - 2 + EY - 1) / EY, a.nchunk + (a.kp >= 1 ? 1 : 0));
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(k_emit<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (attr != cudaSuccess) return attr;
+        EmitMaps none;
+        memset(&none, 0, sizeof none);
+        k_emit<real, false><<<grd, ENT, smem, st>>>(a, g, none);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,6 +1,8 @@
 // Launcher declarations shared by the translation units of libmithra.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace mithra {
@@ -76,12 +78,24 @@ cudaError_t launch_mur_tfsf_xfaces(const FieldLevels<real>& L, const Geom& g, in
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
                        cudaStream_t st);
+// Tensor maps of the seven arrays one E/B emission reads (A_x^n, A_x^{n+1}, A_y^n, A_y^{n+1},
+// A_z^n, A_z^{n+1}, phi^n), each with a box of kEmitBoxW x kEmitBoxH x 1 (the emission tile
+// plus a one-node halo, padded to whole 16-byte rows).
+constexpr int kEmitBoxW = 36, kEmitBoxH = 10;
+struct EmitMaps {
+    CUtensorMap m[7];
+};
+// The emission maps of ring levels lev_n (A^n, phi^n) and lev_n1 (A^{n+1}); false without TMA.
+bool emit_maps(const TmaMaps* maps, int lev_n, int lev_n1, EmitMaps* out);
+
 // Region of one E/B emission: box == null emits the whole interior and clears nothing.
 struct EmitBox {
     const int* box;      // device: cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit
     int* box_reset;      // device: box the next push reduces into, reset to empty by the emission
     int kp;              // plane always emitted in full (< 0: none)
     bool clear;          // clear the sources inside the box
+    const EmitMaps* maps = nullptr;   // TMA loads (null: per-element asynchronous copies)
+    int* err = nullptr;               // set when a bounded wait of the TMA loads expired
 };
 template <typename real>
 cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, const EmitBox& bx,

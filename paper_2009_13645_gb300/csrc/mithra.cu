@@ -279,6 +279,9 @@ struct RunT final : mithra_run {
         Fields6<real> E6;
         for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
         EmitBox bx{nullptr, nullptr, -1, false};
+        EmitMaps em;
+        if (emit_maps(tma, lev(2), lev(0), &em)) bx.maps = &em;
+        bx.err = err_word;
         CU(launch_emit<real>(L, E6, g, bx, stream));
         return MITHRA_OK;
     }
@@ -485,7 +488,10 @@ struct RunT final : mithra_run {
         FieldLevels<real> L = levels();
         cudaEvent_t e0 = nullptr;
         // E/B where the particles are (and on the power plane); clears the previous sources
-        const EmitBox bx{box[n % 2], box[(n + 1) % 2], (int)d.kp, true};
+        EmitBox bx{box[n % 2], box[(n + 1) % 2], (int)d.kp, true};
+        EmitMaps em;
+        if (emit_maps(tma, lev(0), lev(1), &em)) bx.maps = &em;
+        bx.err = err_word;
         pbeg(MITHRA_K_EMIT, &e0);
         CU(launch_emit<real>(L, E6, g, bx, stream));
         pend(MITHRA_K_EMIT, e0);

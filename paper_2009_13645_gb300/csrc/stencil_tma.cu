@@ -29,13 +29,13 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace mithra {
 
 namespace {
 
 constexpr int TX = 64, TY = 8, NST = 4, KZ = 32;
-constexpr uint32_t kSpinLimit = 1u << 20;
 
 template <typename real>
 struct Tile {
@@ -52,54 +52,13 @@ struct Tile {
     static constexpr int SMEM = NST * STAGE + 128;                 // + mbarriers
 };
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(su32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
-        : "memory");
-}
-
-// Bounded wait; false when the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    for (uint32_t s = 0; s < kSpinLimit; ++s)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
 }  // namespace
 
 struct TmaMaps {
     CUtensorMap halo[3][4];   // psi with halo box, per ring level and component
     CUtensorMap body[3][4];   // psi without halo (used as psi^{n-1})
     CUtensorMap src[4];
+    CUtensorMap emit[3][4];   // E/B emission region box (kEmitBoxW x kEmitBoxH), per level and component
 };
 
 template <typename real>
@@ -302,12 +261,14 @@ bool tma_supported(const Geom& g)
     return encode_fn() != nullptr && ((int64_t)g.nx * (int64_t)sizeof(real)) % 16 == 0;
 }
 
-static bool encode(CUtensorMap* m, void* base, const Geom& g, int elem, bool halo)
+// box: 0 the stencil's tile, 1 the stencil's tile with halo, 2 the emission region
+static bool encode(CUtensorMap* m, void* base, const Geom& g, int elem, int kind)
 {
     const int hx = 16 / elem;
     const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)g.nx * elem, (cuuint64_t)g.nx * g.ny * elem};
-    const cuuint32_t box[3] = {(cuuint32_t)(halo ? TX + 2 * hx : TX), (cuuint32_t)(halo ? TY + 2 : TY), 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(kind == 2 ? kEmitBoxW : (kind == 1 ? TX + 2 * hx : TX)),
+                               (cuuint32_t)(kind == 2 ? kEmitBoxH : (kind == 1 ? TY + 2 : TY)), 1};
     const cuuint32_t es[3] = {1, 1, 1};
     const CUresult r = encode_fn()(m, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
                                    base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -324,10 +285,11 @@ TmaMaps* make_tma_maps(real* const pot[3][4], real* const src[4], const Geom& g)
     bool ok = true;
     for (int l = 0; l < 3; ++l)
         for (int c = 0; c < 4; ++c) {
-            ok = ok && encode(&m->halo[l][c], pot[l][c], g, sizeof(real), true);
-            ok = ok && encode(&m->body[l][c], pot[l][c], g, sizeof(real), false);
+            ok = ok && encode(&m->halo[l][c], pot[l][c], g, sizeof(real), 1);
+            ok = ok && encode(&m->body[l][c], pot[l][c], g, sizeof(real), 0);
+            ok = ok && encode(&m->emit[l][c], pot[l][c], g, sizeof(real), 2);
         }
-    for (int c = 0; c < 4; ++c) ok = ok && encode(&m->src[c], src[c], g, sizeof(real), false);
+    for (int c = 0; c < 4; ++c) ok = ok && encode(&m->src[c], src[c], g, sizeof(real), 0);
     if (!ok) {
         delete m;
         return nullptr;
@@ -336,6 +298,17 @@ TmaMaps* make_tma_maps(real* const pot[3][4], real* const src[4], const Geom& g)
 }
 
 void free_tma_maps(TmaMaps* m) { delete m; }
+
+bool emit_maps(const TmaMaps* maps, int lev_n, int lev_n1, EmitMaps* out)
+{
+    if (!maps) return false;
+    for (int c = 0; c < 3; ++c) {
+        out->m[2 * c] = maps->emit[lev_n][c];
+        out->m[2 * c + 1] = maps->emit[lev_n1][c];
+    }
+    out->m[6] = maps->emit[lev_n][3];
+    return true;
+}
 
 template <typename real>
 cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* const prev[4], const MurFaceCoef* mur,
