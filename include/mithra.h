@@ -59,7 +59,7 @@ typedef struct mithra_grid {
     double courant;            /* FD only: dt = courant x CFL bound (Eq. CFLcondition); NSFD forces c dt = dz */
     int32_t mur_order;         /* 1 or 2 (Sec. "First/Second Order ABCs") */
     int32_t space_charge;      /* 0: phi == 0, no charge deposition (Sec. "FDTD for Scalar Potential") */
-    int32_t precision;         /* 0 FP64 everywhere; 1 FP32 fields/offsets, FP64 momentum, external field, diagnostics */
+    int32_t precision;         /* 0 FP64 everywhere; 1 FP32 fields/offsets, float-pair momentum, FP64 external field, diagnostics */
     int32_t substeps;          /* N in dt_b = dt/N (Sec. "Update Algorithm"); >= 1 */
     double power_plane_dist;   /* lab distance of the radiated-power plane ahead of the bunch (Sec. FEL-OUTPUT) */
     double norm_freq;          /* normalised frequency h of the radiated-power diagnostic */

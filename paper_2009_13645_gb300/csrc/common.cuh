@@ -303,7 +303,7 @@ __host__ __device__ inline void boris(double u[3], const double E[3], const doub
 }
 
 // The same Boris rotation in FP32 (Eq. BorisScheme); used by the FP32-mixed push, which adds
-// the resulting increment to the FP64 momentum.
+// the resulting increment to the momentum held as a pair of floats (mom_add).
 __host__ __device__ inline void boris_f32(float u[3], const float E[3], const float B[3], float dtb)
 {
     const float h = (float)(kQe / (2.0 * kMe * kC)) * dtb;
@@ -318,13 +318,48 @@ __host__ __device__ inline void boris_f32(float u[3], const float E[3], const fl
     u[2] = t1z + s * (t2x * B[1] - t2y * B[0]) - h * E[2];
 }
 
+// Stored momentum gamma*beta.  FP64 path: a double.  FP32-mixed path: an unevaluated sum of two
+// floats (hi, lo) with hi the float nearest to hi + lo, about 48 significant bits: the momentum
+// accumulates the FP32 Boris increments at well beyond FP32 precision without the FP64 pipe,
+// and the FP32 rotation reads hi, which is the momentum rounded to FP32.
+template <typename real>
+struct MomStore {
+    using type = double;
+};
+template <>
+struct MomStore<float> {
+    using type = float2;
+};
+template <typename real>
+using mom_t = typename MomStore<real>::type;
+
+__host__ __device__ inline double mom_value(double u) { return u; }
+__host__ __device__ inline double mom_value(float2 u) { return (double)u.x + (double)u.y; }
+__host__ __device__ inline void mom_set(double* dst, double v) { *dst = v; }
+__host__ __device__ inline void mom_set(float2* dst, double v)
+{
+    const float h = (float)v;
+    *dst = make_float2(h, (float)(v - (double)h));
+}
+// (hi, lo) + d: Knuth's two-sum of hi and d, the low parts added, then renormalised by a fast
+// two-sum (exact error terms under round-to-nearest; no products, so nothing is contracted).
+__host__ __device__ inline float2 mom_add(float2 u, float d)
+{
+    const float s = u.x + d;
+    const float bb = s - u.x;
+    const float e = (u.x - (s - bb)) + (d - bb);
+    const float t = u.y + e;
+    const float h = s + t;
+    return make_float2(h, t - (h - s));
+}
+
 // Particle arrays (structure of arrays).  Position = node 0 + (cell + offset) * spacing,
 // offset in [0, 1).  `real` is float for the FP32-mixed path, double for FP64.
 template <typename real>
 struct Particles {
     int32_t *ix, *iy, *iz;
     real *fx, *fy, *fz;
-    double *ux, *uy, *uz;
+    mom_t<real> *ux, *uy, *uz;
     int32_t *id;
 };
 

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bunch_moments(Particles<real> P
     const real dx = (real)g.dx, dy = (real)g.dy, dz = (real)g.dz;
     const real g0 = (real)b.g0, gb0 = (real)(b.g0 * b.b0), goff = (real)(b.g0 - b.shift[6]);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-        const real ux = (real)P.ux[p], uy = (real)P.uy[p], uz = (real)P.uz[p];
+        const real ux = (real)mom_value(P.ux[p]), uy = (real)mom_value(P.uy[p]), uz = (real)mom_value(P.uz[p]);
         const real u2 = ux * ux + uy * uy + uz * uz;
         const real gm1 = u2 / ((real)1 + sqrt((real)1 + u2));
         real d[7];

@@ -308,9 +308,9 @@ struct RunT final : mithra_run {
             Q->fx = (real*)mem.get(n * sizeof(real));
             Q->fy = (real*)mem.get(n * sizeof(real));
             Q->fz = (real*)mem.get(n * sizeof(real));
-            Q->ux = (double*)mem.get(n * 8);
-            Q->uy = (double*)mem.get(n * 8);
-            Q->uz = (double*)mem.get(n * 8);
+            Q->ux = (mom_t<real>*)mem.get(n * sizeof(mom_t<real>));
+            Q->uy = (mom_t<real>*)mem.get(n * sizeof(mom_t<real>));
+            Q->uz = (mom_t<real>*)mem.get(n * sizeof(mom_t<real>));
             Q->id = (int32_t*)mem.get(n * 4);
             if (!Q->ix || !Q->iy || !Q->iz || !Q->fx || !Q->fy || !Q->fz || !Q->ux || !Q->uy || !Q->uz || !Q->id)
                 return fail(MITHRA_ENOMEM, "device allocation failed (particles)");

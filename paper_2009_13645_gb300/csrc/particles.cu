@@ -386,7 +386,7 @@ __device__ __forceinline__ void box_merge(int lo[3], int hi[3], int* box_out)
 // move in cell units relative to cell ci, (nc, nf) = the new cell and offset.  Returns whether
 // the particle starts in an active cell (the gather and the deposit need its whole stencil).
 template <typename real>
-__device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3], double u[3], real b[3], int nc[3],
+__device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3], mom_t<real> u[3], real b[3], int nc[3],
                                          real nf[3], const Geom& g, const ExtField& ef, const Fields6<real>& eb,
                                          const PushConst& pc, double t_half, double Z0)
 {
@@ -445,22 +445,21 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
     real cdt[3];
     real um[3];   // the momentum the move uses, in the path's precision
     if constexpr (std::is_same<real, float>::value) {
-        // Boris rotation in FP32 on the momentum rounded to FP32; its increment is added to the
-        // FP64 momentum, and the move uses the rotated FP32 momentum
-        float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
+        // Boris rotation in FP32 on the momentum rounded to FP32 (the pair's high part); its
+        // increment is added to the pair, and the move uses the rotated FP32 momentum
+        float uf[3] = {u[0].x, u[1].x, u[2].x};
         const float Et[3] = {Ef[0] + s[0], Ef[1] + s[1], Ef[2] + s[2]};
         const float Bt[3] = {Bf[0] + s[3], Bf[1] + s[4], Bf[2] + s[5]};
         const float u0[3] = {uf[0], uf[1], uf[2]};
         boris_f32(uf, Et, Bt, pc.dtbf);
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
-            u[l] += (double)(uf[l] - u0[l]);
+            u[l] = mom_add(u[l], uf[l] - u0[l]);
             cdt[l] = pc.cdtbf[l];
             um[l] = uf[l];
         }
-        // gamma^2 = 1 + u.u accumulated in FP64 from the FP64 momentum; its reciprocal root only
-        // scales the FP32 move, so it is taken in FP32
-        ig = rsqrtf((float)fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
+        // 1/gamma only scales the FP32 move: FP32 from the updated momentum's high parts
+        ig = rsqrtf(fmaf(u[0].x, u[0].x, fmaf(u[1].x, u[1].x, fmaf(u[2].x, u[2].x, 1.f))));
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -520,7 +519,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
     const bool alive = p < np;
     int ci[3] = {-4, -4, -4};
     real f[3] = {0, 0, 0};
-    double u[3] = {0.0, 0.0, 0.0};
+    mom_t<real> u[3] = {};
     if (alive) {
         ci[0] = P.ix[p];
         ci[1] = P.iy[p];
@@ -698,9 +697,9 @@ __global__ void k_boost(const double* __restrict__ lab, int64_t np, Particles<re
     split_pos<real>((x - g.x0) / g.dx, P.ix + p, P.fx + p);
     split_pos<real>((y - g.y0) / g.dy, P.iy + p, P.fy + p);
     split_pos<real>((z - g.z0) / g.dz, P.iz + p, P.fz + p);
-    P.ux[p] = ux;
-    P.uy[p] = uy;
-    P.uz[p] = uz;
+    mom_set(P.ux + p, ux);
+    mom_set(P.uy + p, uy);
+    mom_set(P.uz + p, uz);
     P.id[p] = (int32_t)p;
 }
 
@@ -713,9 +712,9 @@ __global__ void k_set_rest(const double* __restrict__ r6, int64_t np, Particles<
     split_pos<real>((R[0] - g.x0) / g.dx, P.ix + p, P.fx + p);
     split_pos<real>((R[1] - g.y0) / g.dy, P.iy + p, P.fy + p);
     split_pos<real>((R[2] - g.z0) / g.dz, P.iz + p, P.fz + p);
-    P.ux[p] = R[3];
-    P.uy[p] = R[4];
-    P.uz[p] = R[5];
+    mom_set(P.ux + p, R[3]);
+    mom_set(P.uy + p, R[4]);
+    mom_set(P.uz + p, R[5]);
     P.id[p] = (int32_t)p;
 }
 
@@ -728,9 +727,9 @@ __global__ void k_get_rest(Particles<real> P, int64_t np, Geom g, double* __rest
     R[0] = g.x0 + ((double)P.ix[p] + (double)P.fx[p]) * g.dx;
     R[1] = g.y0 + ((double)P.iy[p] + (double)P.fy[p]) * g.dy;
     R[2] = g.z0 + ((double)P.iz[p] + (double)P.fz[p]) * g.dz;
-    R[3] = P.ux[p];
-    R[4] = P.uy[p];
-    R[5] = P.uz[p];
+    R[3] = mom_value(P.ux[p]);
+    R[4] = mom_value(P.uy[p]);
+    R[5] = mom_value(P.uz[p]);
 }
 
 static inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }

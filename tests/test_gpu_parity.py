@@ -8,8 +8,9 @@ Tolerances:
   with the particles in reverse order, no sorting, and lab momenta moved by two units in the last
   place (which also exposes how much the dynamics amplify rounding-level differences such as FMA
   contraction); the bound is 1e-11 + 4 x floor.
-* FP32-mixed path: fields stored in FP32 (unit round-off 6e-8), momentum, external field and
-  reductions in FP64: 1e-4 relative field energy and 1 % radiated power.
+* FP32-mixed path: fields stored in FP32 (unit round-off 6e-8), momentum accumulated as a pair
+  of floats (about 48 bits), external field and reductions in FP64: 1e-4 relative field energy
+  and 1 % radiated power.
 """
 import math
 
