@@ -290,13 +290,18 @@ __device__ __forceinline__ void deposit_piece(const real a[3], const real b[3], 
     }
 }
 
-// Umeda zigzag of the move A -> B (relative to the base cell, |B - A| <= 1 per axis).
+// Umeda zigzag of the move A -> B (relative to the base cell, |B - A| <= 1 per axis).  A move
+// that stays in its cell has the relay point at the midpoint, so its two pieces are the halves
+// of one straight segment in one cell; the path averages of the bilinear weights over the two
+// halves sum to the average over the whole segment, so that move is deposited as one piece
+// (same currents up to rounding, half the adds).
 template <typename real, typename Tgt>
 __device__ __forceinline__ void zigzag(const real A[3], const real B[3], const int base[3], const Tgt& T,
                                        const real qJ[3])
 {
     int c1[3], c2[3];
-    real R[3];
+    real R[3], E1[3];
+    bool cross = false;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
         c1[l] = (int)floor(A[l]);
@@ -304,9 +309,12 @@ __device__ __forceinline__ void zigzag(const real A[3], const real B[3], const i
         const real lo = (real)min(c1[l], c2[l]), hi = (real)max(c1[l], c2[l]);
         const real mid = (real)0.5 * (A[l] + B[l]);
         R[l] = fmin(lo + (real)1, fmax(hi, mid));
+        cross = cross || c1[l] != c2[l];
     }
-    deposit_piece(A, R, c1, base, T, qJ);
-    deposit_piece(R, B, c2, base, T, qJ);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) E1[l] = cross ? R[l] : B[l];
+    deposit_piece(A, E1, c1, base, T, qJ);
+    if (cross) deposit_piece(R, B, c2, base, T, qJ);
 }
 
 // Charge of one particle at cell c, offset fo, on the cell's eight nodes (linear weights).
