@@ -245,7 +245,8 @@ struct GlobalTarget {
 struct TileTarget {
     using off_t = int;
     int* t;
-    unsigned base;   // shared-window address of t[0]
+    unsigned base;   // shared-window address of this lane's copy of entry 0
+    int sh;          // log2 of the bytes between consecutive entries (4 bytes x copies)
     int vol;
     int sy, sz;
     int ox, oy, oz;
@@ -253,7 +254,7 @@ struct TileTarget {
     __device__ __forceinline__ int at(int i, int j, int k) const { return (k - oz) * sz + (j - oy) * sy + (i - ox); }
     __device__ __forceinline__ void add(int comp, int off, float v) const
     {
-        const unsigned a = base + 4u * (unsigned)(comp * vol + off);
+        const unsigned a = base + ((unsigned)(comp * vol + off) << sh);
         asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(__float2int_rn(v * scale[comp])) : "memory");
     }
 };
@@ -502,8 +503,8 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
 #define MITHRA_PUSH_MIN_BLOCKS_F64 5
 #endif
 
-// Nodes per grid of the FP32-mixed push's deposit tile in shared memory.
-constexpr int kTileNodes = 1024;
+// 32-bit entries of the FP32-mixed push's deposit tile in shared memory (all grids and copies).
+constexpr int kTileInts = 8192;
 
 // The push: one thread per particle, 128 per block, the particles in cell-sorted order.
 //
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
         const bool last = m == g.substeps - 1;
         const bool rho_t = simple && g.space_charge && last;
         if constexpr (std::is_same<real, float>::value) {
-            __shared__ int tile[4 * kTileNodes];
+            __shared__ __align__(16) int tile[kTileInts];
             int tlo[3], thi[3], box[6];
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
@@ -604,9 +605,13 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
             block_box(tlo, thi, box);
             const int tx = box[3] - box[0] + 1, ty = box[4] - box[1] + 1, tz = box[5] - box[2] + 1;
             const int ngrid = (g.space_charge && last) ? 4 : 3;
-            if (box[0] <= box[3] && (int64_t)tx * ty * tz <= kTileNodes) {
-                const int vol = tx * ty * tz;
-                for (int i = threadIdx.x; i < ngrid * vol; i += blockDim.x) tile[i] = 0;
+            if (box[0] <= box[3] && (int64_t)ngrid * tx * ty * tz <= kTileInts) {
+                const int vol = tx * ty * tz, nent = ngrid * vol;
+                // Up to four interleaved copies of every entry, lane l adding to copy l mod
+                // copies: the sorted lanes of a warp mostly share a cell, and the copies divide
+                // the number of lanes that meet in one address of an add
+                const int lc = 4 * nent <= kTileInts ? 2 : (2 * nent <= kTileInts ? 1 : 0);
+                for (int i = threadIdx.x; i < (nent << lc); i += blockDim.x) tile[i] = 0;
                 __syncthreads();
                 // A particle adds at most |qJ_l| to any node of J_l over its two pieces (the
                 // path-averaged weights lie in [0, 1] and the pieces' extents along l sum to at
@@ -615,7 +620,8 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 // most 1/2.
                 TileTarget T;
                 T.t = tile;
-                T.base = (unsigned)__cvta_generic_to_shared(tile);
+                T.base = (unsigned)__cvta_generic_to_shared(tile) + 4u * (threadIdx.x & ((1u << lc) - 1u));
+                T.sh = 2 + lc;
                 T.vol = vol;
                 T.sy = tx;
                 T.sz = tx * ty;
@@ -634,8 +640,17 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 // index -> (grid, k, j, i) with FP32 reciprocals: the quotients are below 2^12 and
                 // (index + 1/2) / divisor stays at least 1/(2 divisor) away from an integer
                 const float ivol = 1.f / (float)vol, itxy = 1.f / (float)(tx * ty), itx = 1.f / (float)tx;
-                for (int i = threadIdx.x; i < ngrid * vol; i += blockDim.x) {
-                    const int v = tile[i];
+                for (int i = threadIdx.x; i < nent; i += blockDim.x) {
+                    int v;
+                    if (lc == 2) {
+                        const int4 w = *reinterpret_cast<const int4*>(tile + 4 * i);
+                        v = (w.x + w.y) + (w.z + w.w);
+                    } else if (lc == 1) {
+                        const int2 w = *reinterpret_cast<const int2*>(tile + 2 * i);
+                        v = w.x + w.y;
+                    } else {
+                        v = tile[i];
+                    }
                     if (v != 0) {
                         const int c = (int)(((float)i + 0.5f) * ivol), r = i - c * vol;
                         const int k = (int)(((float)r + 0.5f) * itxy), r2 = r - k * tx * ty;
