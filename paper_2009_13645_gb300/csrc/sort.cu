@@ -1,6 +1,10 @@
-// Periodic counting sort of the particles by cell (x fastest), so that particles that share
-// a cell are neighbours in memory: the gather reads and deposit atomics of a warp then hit
-// the same few cache lines.  Particles outside the node range go to one last bin.
+// Periodic counting sort of the particles by cell, so that particles that share a cell are
+// neighbours in memory: the gather reads and deposit atomics of a warp then hit the same few
+// cache lines.  The cells are ordered as a serpentine: x runs backwards in every other row and y
+// in every other plane, so the last cell of a row (plane) touches the first of the next, and a
+// block of particles that straddles two rows still covers a compact box of cells (the push's
+// deposit tile).  The key is a permutation of the cell index; particles outside the node range
+// go to one last bin.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -18,9 +22,10 @@ __global__ void k_keys(Particles<real> P, int64_t np, Geom g, int32_t* __restric
     if (p >= np) return;
     const int i = P.ix[p], j = P.iy[p], k = P.iz[p];
     int32_t kk;
-    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz)
-        kk = (int32_t)((int64_t)k * g.sz + (int64_t)j * g.sy + i);
-    else
+    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) {
+        const int64_t row = (int64_t)k * g.ny + ((k & 1) ? g.ny - 1 - j : j);
+        kk = (int32_t)(row * g.nx + ((row & 1) ? g.nx - 1 - i : i));
+    } else
         kk = (int32_t)(nbins - 1);
     key[p] = kk;
     atomicAdd(count + kk, 1);
