@@ -133,6 +133,9 @@ struct PushConst {
     // bB0 cos} and {B0 sin, B0 cos, k_u u, k_u (u - L_u)} of the plane's undulator coordinate u,
     // evaluated in FP64 and rounded to FP32
     const float4* ptab32[2];
+    // undulator array, FP32-mixed path: per node plane {B_i, B_{i+1}, last module, 0} (null: no
+    // array)
+    const float4* ptab32a;
     double kz;            // gamma0 dz: zeta per cell along z
     double zstep;         // gamma0 beta0 c dt_b: zeta per sub-step
     float kdz, kzs;       // k_u kz and k_u zstep in FP32: the sub-cell rotation per offset and sub-step
@@ -142,6 +145,9 @@ struct PushConst {
     // rest-frame amplitudes of the static undulator field, gamma0 beta0 c B0, gamma0 B0 and B0,
     // evaluated in FP64 and rounded to FP32 (the fringe of the FP32-mixed path)
     float eB0f, bB0f, B0f;
+    // undulator array, FP32-mixed path: k_u g, pi / (k_u g) (the window's argument per k_u dz),
+    // gamma0 beta0 c and gamma0
+    float kugf, pwinf, egbf, gbf;
     // FP32-mixed deposit tile: fixed-point scale per source grid (2^30 / (128 |qJ_l|), 2^30 /
     // (128 |q|)) and its inverse
     float tscale[4], tunit[4];
@@ -150,7 +156,7 @@ struct PushConst {
 cudaError_t launch_phase_table(const ExtField& ef, const StepDev* sd, double kz, int nz, double2* t0, double2* t1,
                                cudaStream_t st);
 cudaError_t launch_phase_table32(const ExtField& ef, const StepDev* sd, double kz, int nz, float4* t0, float4* t1,
-                                 cudaStream_t st);
+                                 float4* ta, cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,

@@ -241,6 +241,7 @@ struct RunT final : mithra_run {
     int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
     double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables, FP64 path (one per planar field)
     float4* ptab32[2] = {nullptr, nullptr};  // FP32-mixed path: phase and edge distances rounded to FP32
+    float4* ptab32a = nullptr;               // FP32-mixed path, undulator array: module peak fields per plane
     TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
     MurFaceCoef murc{};        // Mur face coefficients (the FP32 TMA stencil writes the x faces)
     int* err_word = nullptr;   // set by a kernel whose bounded wait expired
@@ -373,6 +374,13 @@ struct RunT final : mithra_run {
                 else ptab32[b] = (float4*)mem.get((size_t)g.nz * 2 * sizeof(float4));
                 if (!ptab[b] && !ptab32[b]) return fail(MITHRA_ENOMEM, "device allocation failed (phase table)");
             }
+        }
+        if (ef.kind == 4 && sizeof(real) == 4) {
+            // FP32-mixed array: the planar table per module plus the modules' peak fields (the
+            // FP64 path evaluates the array directly)
+            ptab32[0] = (float4*)mem.get((size_t)g.nz * 2 * sizeof(float4));
+            ptab32a = (float4*)mem.get((size_t)g.nz * sizeof(float4));
+            if (!ptab32[0] || !ptab32a) return fail(MITHRA_ENOMEM, "device allocation failed (phase table)");
         }
         if (!(err_word = (int*)mem.get(sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (error word)");
         CU(cudaMemsetAsync(err_word, 0, sizeof(int), stream));
@@ -508,6 +516,11 @@ struct RunT final : mithra_run {
         pc.ptab[1] = ptab[1];
         pc.ptab32[0] = ptab32[0];
         pc.ptab32[1] = ptab32[1];
+        pc.ptab32a = ptab32a;
+        pc.kugf = (float)(ef.ku * ef.gap);
+        pc.pwinf = ef.gap > 0.0 ? (float)(kPi / (ef.ku * ef.gap)) : 0.f;
+        pc.egbf = (float)(ef.g0 * ef.b0 * kC);
+        pc.gbf = (float)ef.g0;
         pc.kz = d.g0 * d.dz;
         pc.zstep = d.g0 * d.b0 * kC * d.dtb;
         pc.kdz = (float)(ef.ku * pc.kz);
@@ -536,7 +549,7 @@ struct RunT final : mithra_run {
         pc.B0f = (float)ef.B0;
         pbeg(MITHRA_K_PUSH, &e0);
         if (ptab[0]) CU(launch_phase_table(ef, sd, pc.kz, g.nz, ptab[0], ptab[1], stream));
-        if (ptab32[0]) CU(launch_phase_table32(ef, sd, pc.kz, g.nz, ptab32[0], ptab32[1], stream));
+        if (ptab32[0]) CU(launch_phase_table32(ef, sd, pc.kz, g.nz, ptab32[0], ptab32[1], ptab32a, stream));
         CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
         pend(MITHRA_K_PUSH, e0);
         if (bunch_every > 0) {

@@ -115,14 +115,27 @@ __device__ __forceinline__ void coshsinh32(float x, float* ch, float* sh)
     }
 }
 
+// Window of a fringe inside a gap (Eq. fringingFieldGap) in FP32, at kd = k_u dz: cos 2a and
+// cos 3a from cos a by the double- and triple-angle identities.
+__device__ __forceinline__ float gap_window32(float kd, float pwin)
+{
+    const float c1 = cosf(kd * pwin);
+    const float c2 = fmaf(2.f * c1, c1, -1.f);
+    const float c3 = c1 * fmaf(2.f, c2, -1.f);
+    return 0.35875f + 0.48829f * c1 + 0.14128f * c2 + 0.01168f * c3;
+}
+
 // FP32-mixed variant.  The step's table holds, per node plane and planar field, the lab field
 // at the plane already Lorentz-transformed to the rest frame in FP64 (sin and cos of the plane's
-// undulator phase times the FP64 amplitudes gamma0 beta0 c B0, gamma0 B0, B0) and the phase
-// distances to both ends of the undulator, all rounded to FP32.  The transform is linear with
-// constant coefficients, so rotating the transformed plane values by the sub-cell angle equals
-// transforming the rotated ones; that rotation, the fringe factor outside [0, L_u] and cosh/sinh
-// of k_u y are evaluated in FP32, the precision of the self-field they are added to.
-__device__ __forceinline__ void static_field_mixed(const ExtField& f, const PushConst& pc, int iz, float fz, int m,
+// undulator phase times the FP64 amplitudes gamma0 beta0 c B, gamma0 B, B) and the phase
+// distances to both ends of the undulator (of an array: of the plane's module), all rounded to
+// FP32.  The transform is linear with constant coefficients, so rotating the transformed plane
+// values by the sub-cell angle equals transforming the rotated ones; that rotation, the fringe
+// factors outside [0, L_u] (with an array's gap windows) and cosh/sinh of k_u y are evaluated in
+// FP32, the precision of the self-field they are added to.  Returns false for a particle of an
+// array whose step reaches past the gap that follows the plane's module (a few node planes in
+// front of each module entrance): it takes the general FP64 evaluation.
+__device__ __forceinline__ bool static_field_mixed(const ExtField& f, const PushConst& pc, int iz, float fz, int m,
                                                    float x, float y, float E[3], float B[3])
 {
     E[0] = E[1] = E[2] = 0.f;
@@ -141,12 +154,39 @@ __device__ __forceinline__ void static_field_mixed(const ExtField& f, const Push
             eS = fmaf(t0.x, cd, t0.y * sd);
             bS = fmaf(t0.z, cd, t0.w * sd);
             zC = fmaf(t1.y, cd, -t1.x * sd);
-        } else {
+        } else if (f.kind != 4) {
             const float kd = ua < 0.f ? ua : ub;
             const float g = expf(-0.5f * kd * kd);
             eS = pc.eB0f * (kd * g);
             bS = pc.bB0f * (kd * g);
             zC = pc.B0f * g;
+        } else {
+            // array: the plane's module i has peak field Bi (t2.x); before the first module its
+            // undamped entrance fringe; after module i its exit fringe, undamped after the last
+            // module, otherwise windowed and joined by the windowed entrance fringe of module
+            // i + 1 (peak field t2.y) at distance k_u g further on
+            const float4 t2 = __ldg(pc.ptab32a + iz);
+            float Sv, Cv;
+            if (ua < 0.f) {
+                const float g = expf(-0.5f * ua * ua);
+                Sv = t2.x * (ua * g);
+                Cv = t2.x * g;
+            } else {
+                const bool last = t2.z != 0.f;
+                if (!last && ub >= pc.kugf) return false;
+                const float e1 = expf(-0.5f * ub * ub) * (last ? 1.f : gap_window32(ub, pc.pwinf));
+                Sv = t2.x * (ub * e1);
+                Cv = t2.x * e1;
+                if (!last) {
+                    const float kd2 = ub - pc.kugf;
+                    const float e2 = expf(-0.5f * kd2 * kd2) * gap_window32(kd2, pc.pwinf);
+                    Sv = fmaf(t2.y, kd2 * e2, Sv);
+                    Cv = fmaf(t2.y, e2, Cv);
+                }
+            }
+            eS = pc.egbf * Sv;
+            bS = pc.gbf * Sv;
+            zC = Cv;
         }
         float ch, sh;
         coshsinh32(pc.kuf * (c * y - s * x), &ch, &sh);
@@ -158,32 +198,49 @@ __device__ __forceinline__ void static_field_mixed(const ExtField& f, const Push
         B[1] += bS * c;
         B[2] += sh * zC;
     }
+    return true;
 }
 
 // FP32 table for the mixed path, two float4 per node plane and planar field: the sin and cos of
-// the plane's phase k_u u times the FP64 rest-frame amplitudes (gamma0 beta0 c B0, gamma0 B0, B0),
+// the plane's phase k_u u times the FP64 rest-frame amplitudes (gamma0 beta0 c B, gamma0 B, B),
 // and the distances k_u u, k_u (u - L_u) to both ends of the undulator; FP64 throughout, rounded
-// once.
-__global__ void k_phase_table32(ExtField f, const StepDev* sd, double kz, int nz, float4* t0, float4* t1)
+// once.  For an array (ta != null) u is counted from the entrance of the plane's module i (the
+// module whose entrance lies at or before the plane, as in the direct evaluation; before the
+// first module, from the first entrance), B is that module's peak field, and ta holds per plane
+// {B_i, B_{i+1} (0 after the last module), 1 for the last module, 0}.
+__global__ void k_phase_table32(ExtField f, const StepDev* sd, double kz, int nz, float4* t0, float4* t1, float4* ta)
 {
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
     if (iz >= nz) return;
     const double zn = fma(kz, (double)iz, sd->Z0);
-    const double eB0 = f.g0 * f.b0 * kC * f.B0, bB0 = f.g0 * f.B0;
+    double Bp = f.B0, org = 0.0;
+    if (ta) {
+        const double P = f.Lu + f.gap;
+        int i = (int)floor(zn / P);
+        i = i < -1 ? -1 : (i > f.nmod - 1 ? f.nmod - 1 : i);
+        if (i >= 0 && zn - i * P < 0.0) --i;
+        if (i < f.nmod - 1 && zn - (i + 1) * P >= 0.0) ++i;
+        const int im = i < 0 ? 0 : i;
+        Bp = f.B0 + im * f.dB0;
+        org = im * P;
+        const bool last = i == f.nmod - 1;
+        ta[iz] = make_float4((float)Bp, (float)((i >= 0 && !last) ? Bp + f.dB0 : 0.0), last ? 1.f : 0.f, 0.f);
+    }
+    const double eB = f.g0 * f.b0 * kC * Bp, bB = f.g0 * Bp;
     for (int j = 0; j < (t1 ? 2 : 1); ++j) {
-        const double ph = f.ku * (zn - (j ? f.qlam : 0.0));
+        const double ph = f.ku * (zn - (j ? f.qlam : org));
         double s, c;
         sincos(ph, &s, &c);
         float4* t = (j ? t1 : t0) + 2 * iz;
-        t[0] = make_float4((float)(eB0 * s), (float)(eB0 * c), (float)(bB0 * s), (float)(bB0 * c));
-        t[1] = make_float4((float)(f.B0 * s), (float)(f.B0 * c), (float)ph, (float)(ph - f.ku * f.Lu));
+        t[0] = make_float4((float)(eB * s), (float)(eB * c), (float)(bB * s), (float)(bB * c));
+        t[1] = make_float4((float)(Bp * s), (float)(Bp * c), (float)ph, (float)(ph - f.ku * f.Lu));
     }
 }
 
 cudaError_t launch_phase_table32(const ExtField& ef, const StepDev* sd, double kz, int nz, float4* t0, float4* t1,
-                                 cudaStream_t st)
+                                 float4* ta, cudaStream_t st)
 {
-    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, sd, kz, nz, t0, t1);
+    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, sd, kz, nz, t0, t1, ta);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -406,8 +463,7 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
         if (pc.ptab32[0] && ci[2] >= 0 && ci[2] < g.nz) {
             const float x = fmaf((float)ci[0] + f[0], pc.dxf, pc.x0f);
             const float y = fmaf((float)ci[1] + f[1], pc.dyf, pc.y0f);
-            static_field_mixed(ef, pc, ci[2], f[2], m, x, y, Ef, Bf);
-            tab = true;
+            tab = static_field_mixed(ef, pc, ci[2], f[2], m, x, y, Ef, Bf);
         }
     } else {
         if (pc.ptab[0] && ci[2] >= 0 && ci[2] < g.nz) {
