@@ -318,6 +318,26 @@ __host__ __device__ inline void boris_f32(float u[3], const float E[3], const fl
     u[2] = t1z + s * (t2x * B[1] - t2y * B[0]) - h * E[2];
 }
 
+#ifdef __CUDACC__
+// True in the last block of the grid to arrive (every block calls it once, with all its
+// threads, after its own global writes); the writes of every block are then visible to that
+// block, which reads them through L2 (__ldcg).  `counter` counts arrivals; the last block
+// resets it for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* counter)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        last = atomicAdd(counter, 1u) == total - 1;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+#endif
+
 // Stored momentum gamma*beta.  FP64 path: a double.  FP32-mixed path: an unevaluated sum of two
 // floats (hi, lo) with hi the float nearest to hi + lo, about 48 significant bits: the momentum
 // accumulates the FP32 Boris increments at well beyond FP32 precision without the FP64 pipe,

@@ -85,23 +85,22 @@ __global__ void __launch_bounds__(kRedThreads) k_power_step(Fields6<real> eb, Ge
     }
     const double tot = block_sum(contrib, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-// Compensated sum of the step's partials to series[n] once the window is complete.
-__global__ void k_power_final(const double* __restrict__ partial, int npartial, double scale, const StepDev* sd,
-                              double* __restrict__ series)
-{
-    __shared__ double sh[32];
-    if (!sd->emit) return;
-    double s = 0.0, comp = 0.0;
-    for (int i = threadIdx.x; i < npartial; i += blockDim.x) {
-        const double v = partial[i];
-        const double t = s + v;
-        comp += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
-        s = t;
+    // the last block to finish adds the partials (compensated, in a fixed order) to series[n]
+    // once the window is complete, and leaves the counter at zero for the next step
+    if (last_block(ps.counter)) {
+        if (sd.emit) {
+            double s = 0.0, comp = 0.0;
+            for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+                const double v = __ldcg(partial + i);
+                const double t = s + v;
+                comp += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+                s = t;
+            }
+            const double all = block_sum(s + comp, sh);
+            if (threadIdx.x == 0) ps.series[sd.n] = all * ps.scale;
+        }
+        if (threadIdx.x == 0) *ps.counter = 0;
     }
-    const double tot = block_sum(s + comp, sh);
-    if (threadIdx.x == 0) series[sd->n] = tot * scale;
 }
 
 template <typename real>
@@ -111,35 +110,14 @@ cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const Powe
     const int64_t plane = (int64_t)g.nx * g.ny;
     const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
     if ((int)nb > npartial) return cudaErrorInvalidValue;
-    k_power_step<real><<<nb, kRedThreads, 0, st>>>(eb, g, ps, partial);
-    k_power_final<<<1, kRedThreads, 0, st>>>(partial, (int)nb, scale, ps.sd, series);
-    count_launches(2);
-    return cudaGetLastError();
-}
-
-// Per-step values from the step counter (one thread).
-__global__ void k_step_begin(StepDev* sd, StepConst c)
-{
-    const int64_t n = sd->next;
-    StepDev v;
-    v.n = n;
-    v.next = n + 1;
-    v.t_half = c.T0 + ((double)n + 0.5) * c.dt;
-    v.Z0 = c.g0 * (c.z0 + c.b0 * kC * v.t_half);
-    v.slot = (int)(n % c.M);
-    v.full = n >= c.M ? 1 : 0;
-    v.emit = n + 1 >= c.M ? 1 : 0;
-    sincos(c.omega_h * ((double)n + 0.5) * c.dt, &v.sn, &v.cn);
-    sincos(c.omega_h * ((double)(n - c.M) + 0.5) * c.dt, &v.so, &v.co);
-    *sd = v;
-}
-
-cudaError_t launch_step_begin(StepDev* sd, const StepConst& c, cudaStream_t st)
-{
-    k_step_begin<<<1, 1, 0, st>>>(sd, c);
+    PowerStep p = ps;
+    p.scale = scale;
+    p.series = series;
+    k_power_step<real><<<nb, kRedThreads, 0, st>>>(eb, g, p, partial);
     count_launches(1);
     return cudaGetLastError();
 }
+
 template cudaError_t launch_power_step<float>(const Fields6<float>&, const Geom&, const PowerStep&, double, double*,
                                               int, double*, cudaStream_t);
 template cudaError_t launch_power_step<double>(const Fields6<double>&, const Geom&, const PowerStep&, double, double*,

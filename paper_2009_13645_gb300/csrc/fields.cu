@@ -154,14 +154,12 @@ struct MurEdgeCoef {
     real C[4];      // n values (all points alike)
 };
 
+// One edge (corners = false; t indexes the 12 edges' points) or corner (corners = true, t < 8)
+// point of component comp.  The corners read the new edge values of other blocks: through L2.
 template <typename real>
-__global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy, int64_t sz,
-                                                  int corners, int64_t maxpts)
+__device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeCoef<real>& cf, int64_t sy, int64_t sz,
+                                          int comp, bool corners, int64_t t)
 {
-    const int comp = blockIdx.y;
-    if (comp >= a.ncomp) return;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= maxpts) return;
     const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
     int p[3], sg[3], axes[3], ns = 0, cls = 3;
     if (corners) {
@@ -207,10 +205,26 @@ __global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<r
         for (int s = 0; s < ns; ++s)
             if ((ei >> s) & 1) q[axes[s]] += sg[s];
         const int64_t id = lin(q[0], q[1], q[2], sy, sz);
-        if (ei != 0) num += cf.A[cls][ei] * n1[id];
+        if (ei != 0) num += cf.A[cls][ei] * (corners ? __ldcg(n1 + id) : n1[id]);
         num += cf.B[cls][ei] * nm[id] + cf.C[cls] * n0[id];
     }
     n1[lin(p[0], p[1], p[2], sy, sz)] = num;
+}
+
+// The edges of every component (blockIdx.y), then, in the last block to finish, the 8 corners of
+// every component.
+template <typename real>
+__global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy, int64_t sz,
+                                                  int64_t maxpts, unsigned* counter)
+{
+    const int comp = blockIdx.y;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (comp < a.ncomp && t < maxpts) mur_point(a, cf, sy, sz, comp, false, t);
+    if (last_block(counter)) {
+        const int c = (int)threadIdx.x >> 3;
+        if (c < a.ncomp) mur_point(a, cf, sy, sz, c, true, (int64_t)(threadIdx.x & 7));
+        if (threadIdx.x == 0) *counter = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -241,6 +255,8 @@ struct EmitArgs {
     const int* box;      // cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit; null: whole grid
     int* box_reset;      // box the next push reduces into: reset to empty here (may be null)
     int* err;            // set when a bounded wait on the tensor copies expired (may be null)
+    StepDev* step;       // non-null: block 0 also starts the step (step_advance)
+    StepConst step_c;
 };
 
 constexpr int EX = 32, EY = 8, EKZ = 8;              // tile and planes per block
@@ -302,6 +318,8 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
     const int t = threadIdx.x, tx = t % EX, ty = t / EX;
     if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t < 6)
         a.box_reset[t] = t < 3 ? 0x7fffffff : (int)0x80000000;
+    // the step's state (no other block of the emission reads it; later kernels do)
+    if (a.step && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) step_advance(a.step, a.step_c);
     // nodes [lo - 1, hi + 2] around the cells of the last deposit: the particles gather at their
     // cells' nodes next step, and with sub-steps they move up to one cell during that step
     int bl[3] = {1, 1, 1}, bh[3] = {g.nx - 2, g.ny - 2, g.nz - 2};
@@ -587,7 +605,7 @@ static MurEdgeCoef<real> mur_edge_coef(const Geom& g)
 
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
-                       cudaStream_t st)
+                       unsigned* counter, cudaStream_t st)
 {
     MurArgs<real> a;
     a.face0 = x_faces_done ? 2 : 0;
@@ -627,9 +645,8 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     }
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
     const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
-    k_mur_edges<real><<<dim3((unsigned)((edges + 63) / 64), ncomp), 64, 0, st>>>(a, ec, g.sy, g.sz, 0, edges);
-    k_mur_edges<real><<<dim3(1, ncomp), 64, 0, st>>>(a, ec, g.sy, g.sz, 1, 8);
-    count_launches(nl + 2);
+    k_mur_edges<real><<<dim3((unsigned)((edges + 63) / 64), ncomp), 64, 0, st>>>(a, ec, g.sy, g.sz, edges, counter);
+    count_launches(nl + 1);
     return cudaGetLastError();
 }
 
@@ -687,6 +704,8 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     a.box = bx.box;
     a.box_reset = bx.box_reset;
     a.err = bx.err;
+    a.step = bx.step;
+    a.step_c = bx.step_c;
     a.nchunk = (g.nz - 2 + EKZ - 1) / EKZ;
     constexpr int smem = (int)sizeof(EmitSmem<real>) + 128;
     if (bx.maps) {
@@ -787,8 +806,10 @@ template cudaError_t launch_tfsf<double>(double* const[2], const Geom&, const St
 
 template cudaError_t launch_stencil<float>(const FieldLevels<float>&, const Geom&, const StencilCoef&, int, cudaStream_t);
 template cudaError_t launch_stencil<double>(const FieldLevels<double>&, const Geom&, const StencilCoef&, int, cudaStream_t);
-template cudaError_t launch_mur<float>(const FieldLevels<float>&, const Geom&, int, int, bool, cudaStream_t);
-template cudaError_t launch_mur<double>(const FieldLevels<double>&, const Geom&, int, int, bool, cudaStream_t);
+template cudaError_t launch_mur<float>(const FieldLevels<float>&, const Geom&, int, int, bool, unsigned*,
+                                      cudaStream_t);
+template cudaError_t launch_mur<double>(const FieldLevels<double>&, const Geom&, int, int, bool, unsigned*,
+                                       cudaStream_t);
 template cudaError_t launch_emit<float>(const FieldLevels<float>&, const Fields6<float>&, const Geom&, const EmitBox&,
                                         cudaStream_t);
 template cudaError_t launch_emit<double>(const FieldLevels<double>&, const Fields6<double>&, const Geom&,

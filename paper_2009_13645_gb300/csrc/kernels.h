@@ -73,11 +73,48 @@ cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf
 template <typename real>
 cudaError_t launch_mur_tfsf_xfaces(const FieldLevels<real>& L, const Geom& g, int order, cudaStream_t st);
 
-// Mur boundary values of level n+1: the faces, then the edges, then the corners.  With
-// x_faces_done the TMA stencil of this step has already written the x faces.
+// Per-step values derived on the device from the step counter, so that a captured sequence of
+// steps replays without host-side parameters.  The step's first kernel (the E/B emission) fills
+// it at the start of every step.
+struct StepDev {
+    int64_t n;        // the step being computed
+    int64_t next;     // the counter: the step after it
+    double t_half;    // rest-frame time of r^{n+1/2}: T0 + (n + 1/2) dt
+    double Z0;        // lab coordinate zeta of node plane 0 at t_half: gamma0 (z0 + beta0 c t_half)
+    int slot;         // power-plane ring slot of step n (the slot of step n - M is the same)
+    int full;         // the ring holds step n - M
+    int emit;         // the power window is complete
+    double cn, sn;    // cos, sin of w t_n
+    double co, so;    // cos, sin of w t_{n-M}
+};
+struct StepConst {
+    double T0, dt, g0, b0, z0, omega_h;
+    int M;
+};
+// The StepDev of the next step from the counter (one thread).
+__device__ __forceinline__ void step_advance(StepDev* sd, const StepConst& c)
+{
+    const int64_t n = sd->next;
+    StepDev v;
+    v.n = n;
+    v.next = n + 1;
+    v.t_half = c.T0 + ((double)n + 0.5) * c.dt;
+    v.Z0 = c.g0 * (c.z0 + c.b0 * kC * v.t_half);
+    v.slot = (int)(n % c.M);
+    v.full = n >= c.M ? 1 : 0;
+    v.emit = n + 1 >= c.M ? 1 : 0;
+    sincos(c.omega_h * ((double)n + 0.5) * c.dt, &v.sn, &v.cn);
+    sincos(c.omega_h * ((double)(n - c.M) + 0.5) * c.dt, &v.so, &v.co);
+    *sd = v;
+}
+
+// Mur boundary values of level n+1: the faces, then the edges, then the corners (the corners in
+// the last block of the edge launch to finish; `counter` is a zeroed device word that the launch
+// leaves zeroed).  With x_faces_done the TMA stencil of this step has already written the x
+// faces.
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
-                       cudaStream_t st);
+                       unsigned* counter, cudaStream_t st);
 // Tensor maps of the seven arrays one E/B emission reads (A_x^n, A_x^{n+1}, A_y^n, A_y^{n+1},
 // A_z^n, A_z^{n+1}, phi^n), each with a box of kEmitBoxW x kEmitBoxH x 1 (the emission tile
 // plus a one-node halo, padded to whole 16-byte rows).
@@ -96,29 +133,14 @@ struct EmitBox {
     bool clear;          // clear the sources inside the box
     const EmitMaps* maps = nullptr;   // TMA loads (null: per-element asynchronous copies)
     int* err = nullptr;               // set when a bounded wait of the TMA loads expired
+    StepDev* step = nullptr;          // non-null: the emission also starts the step (step_advance)
+    StepConst step_c{};
 };
 template <typename real>
 cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, const EmitBox& bx,
                         cudaStream_t st);
 
-// Per-step values derived on the device from the step counter, so that a captured sequence of
-// steps replays without host-side parameters.  k_step_begin fills it at the start of every step.
-struct StepDev {
-    int64_t n;        // the step being computed
-    int64_t next;     // the counter: the step after it
-    double t_half;    // rest-frame time of r^{n+1/2}: T0 + (n + 1/2) dt
-    double Z0;        // lab coordinate zeta of node plane 0 at t_half: gamma0 (z0 + beta0 c t_half)
-    int slot;         // power-plane ring slot of step n (the slot of step n - M is the same)
-    int full;         // the ring holds step n - M
-    int emit;         // the power window is complete
-    double cn, sn;    // cos, sin of w t_n
-    double co, so;    // cos, sin of w t_{n-M}
-};
-struct StepConst {
-    double T0, dt, g0, b0, z0, omega_h;
-    int M;
-};
-cudaError_t launch_step_begin(StepDev* sd, const StepConst& c, cudaStream_t st);
+
 
 // Particles.
 struct PushConst {
@@ -196,6 +218,9 @@ struct PowerStep {
     double* acc;            // 8 x plane accumulators (re, im of Ex, Ey, Bx, By)
     int64_t onaxis_id;
     double* onaxis_series;  // on-axis E_x of step n goes to entry n
+    unsigned* counter;      // zeroed device word: finds the last block (left zeroed)
+    double scale;           // set by launch_power_step
+    double* series;         // set by launch_power_step
 };
 // The power of step n goes to series[n] once the window is complete.
 template <typename real>

@@ -245,6 +245,7 @@ struct RunT final : mithra_run {
     TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
     MurFaceCoef murc{};        // Mur face coefficients (the FP32 TMA stencil writes the x faces)
     int* err_word = nullptr;   // set by a kernel whose bounded wait expired
+    unsigned* counters = nullptr;   // last-block counters (Mur edges, power), zero between launches
     StepDev* sd = nullptr;     // per-step values derived on the device from the step counter
     StepConst scst{};
     // captured steps: one graph of glen steps replayed from every aligned step
@@ -384,6 +385,9 @@ struct RunT final : mithra_run {
         }
         if (!(err_word = (int*)mem.get(sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (error word)");
         CU(cudaMemsetAsync(err_word, 0, sizeof(int), stream));
+        if (!(counters = (unsigned*)mem.get(2 * sizeof(unsigned))))
+            return fail(MITHRA_ENOMEM, "device allocation failed (counters)");
+        CU(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), stream));
         if (!(sd = (StepDev*)mem.get(sizeof(StepDev)))) return fail(MITHRA_ENOMEM, "device allocation failed (step state)");
         CU(cudaMemsetAsync(sd, 0, sizeof(StepDev), stream));   // the counter starts at step 0
         scst.T0 = d.T0;
@@ -489,7 +493,6 @@ struct RunT final : mithra_run {
         for (int c = 0; c < 4; ++c) S4.c[c] = src[c];
         int rc = MITHRA_OK;
         const int64_t n = nstep;
-        CU(launch_step_begin(sd, scst, stream));
         if (sort_every > 0 && n > 0 && n % sort_every == 0 && np > 1) {
             if ((rc = sort_now())) return rc;
         }
@@ -500,6 +503,8 @@ struct RunT final : mithra_run {
         EmitMaps em;
         if (emit_maps(tma, lev(0), lev(1), &em)) bx.maps = &em;
         bx.err = err_word;
+        bx.step = sd;   // the emission starts the step: nothing before it reads the step state
+        bx.step_c = scst;
         pbeg(MITHRA_K_EMIT, &e0);
         CU(launch_emit<real>(L, E6, g, bx, stream));
         pend(MITHRA_K_EMIT, e0);
@@ -586,7 +591,7 @@ struct RunT final : mithra_run {
         }
         pend(MITHRA_K_STENCIL, e0);
         pbeg(MITHRA_K_MUR, &e0);
-        CU(launch_mur<real>(L, g, mur_order, ncomp, xf, stream));
+        CU(launch_mur<real>(L, g, mur_order, ncomp, xf, counters, stream));
         pend(MITHRA_K_MUR, e0);
         pbeg(MITHRA_K_POWER, &e0);
         {
@@ -598,6 +603,7 @@ struct RunT final : mithra_run {
             ps.acc = acc;
             ps.onaxis_id = onaxis_id;
             ps.onaxis_series = ser_e;
+            ps.counter = counters + 1;
             const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
             const double scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
             if (!ring || !acc || !partial) return fail(MITHRA_EINVAL, "power diagnostic buffers missing");
