@@ -553,14 +553,17 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
 
 // Resident blocks of 128 threads per SM the push is compiled for (the register budget per thread).
 #ifndef MITHRA_PUSH_MIN_BLOCKS_F32
-#define MITHRA_PUSH_MIN_BLOCKS_F32 6
+#define MITHRA_PUSH_MIN_BLOCKS_F32 7
 #endif
 #ifndef MITHRA_PUSH_MIN_BLOCKS_F64
 #define MITHRA_PUSH_MIN_BLOCKS_F64 5
 #endif
 
 // 32-bit entries of the FP32-mixed push's deposit tile in shared memory (all grids and copies).
-constexpr int kTileInts = 8192;
+#ifndef MITHRA_PUSH_TILE_INTS
+#define MITHRA_PUSH_TILE_INTS 4096
+#endif
+constexpr int kTileInts = MITHRA_PUSH_TILE_INTS;
 
 // The push: one thread per particle, 128 per block, the particles in cell-sorted order.
 //
@@ -659,15 +662,21 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 thi[l] = simple ? max(ci[l], nc[l]) + 1 : (int)0x80000000;
             }
             block_box(tlo, thi, box);
-            const int tx = box[3] - box[0] + 1, ty = box[4] - box[1] + 1, tz = box[5] - box[2] + 1;
+            // the tile's rows start on a multiple of four nodes and hold whole quads of nodes, so
+            // that a quad of a row is added to the grid with one vector atomic
+            const int bx0 = box[0] & ~3;
+            const int tx = (box[3] - bx0 + 4) & ~3, ty = box[4] - box[1] + 1, tz = box[5] - box[2] + 1;
             const int ngrid = (g.space_charge && last) ? 4 : 3;
-            if (box[0] <= box[3] && (int64_t)ngrid * tx * ty * tz <= kTileInts) {
+            if (box[0] <= box[3] && (int64_t)ngrid * tx * ty * tz + 4 <= kTileInts) {
                 const int vol = tx * ty * tz, nent = ngrid * vol;
-                // Up to four interleaved copies of every entry, lane l adding to copy l mod
-                // copies: the sorted lanes of a warp mostly share a cell, and the copies divide
-                // the number of lanes that meet in one address of an add
-                const int lc = 4 * nent <= kTileInts ? 2 : (2 * nent <= kTileInts ? 1 : 0);
-                for (int i = threadIdx.x; i < (nent << lc); i += blockDim.x) tile[i] = 0;
+                // Up to four copies of the tile, lane l adding to copy l mod copies: the sorted
+                // lanes of a warp often share a cell, and the copies divide the number of lanes
+                // that meet in one address of an add.  The copies lie cs = nent + 4 entries
+                // apart, so that the copies of one entry sit in different banks.
+                const int cs = nent + 4;
+                const int lc = 4 * cs <= kTileInts ? 2 : (2 * cs <= kTileInts ? 1 : 0);
+                int4* tile4 = reinterpret_cast<int4*>(tile);
+                for (int i = threadIdx.x; i < (cs << lc) >> 2; i += blockDim.x) tile4[i] = make_int4(0, 0, 0, 0);
                 __syncthreads();
                 // A particle adds at most |qJ_l| to any node of J_l over its two pieces (the
                 // path-averaged weights lie in [0, 1] and the pieces' extents along l sum to at
@@ -676,12 +685,12 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 // most 1/2.
                 TileTarget T;
                 T.t = tile;
-                T.base = (unsigned)__cvta_generic_to_shared(tile) + 4u * (threadIdx.x & ((1u << lc) - 1u));
-                T.sh = 2 + lc;
+                T.base = (unsigned)__cvta_generic_to_shared(tile) + 4u * (unsigned)cs * (threadIdx.x & ((1u << lc) - 1u));
+                T.sh = 2;
                 T.vol = vol;
                 T.sy = tx;
                 T.sz = tx * ty;
-                T.ox = box[0];
+                T.ox = bx0;
                 T.oy = box[1];
                 T.oz = box[2];
                 T.scale[0] = pc.tscale[0];
@@ -693,27 +702,39 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                     if (rho_t) deposit_rho(nc, nf, q, T);
                 }
                 __syncthreads();
-                // index -> (grid, k, j, i) with FP32 reciprocals: the quotients are below 2^12 and
-                // (index + 1/2) / divisor stays at least 1/(2 divisor) away from an integer
-                const float ivol = 1.f / (float)vol, itxy = 1.f / (float)(tx * ty), itx = 1.f / (float)tx;
-                for (int i = threadIdx.x; i < nent; i += blockDim.x) {
-                    int v;
-                    if (lc == 2) {
-                        const int4 w = *reinterpret_cast<const int4*>(tile + 4 * i);
-                        v = (w.x + w.y) + (w.z + w.w);
-                    } else if (lc == 1) {
-                        const int2 w = *reinterpret_cast<const int2*>(tile + 2 * i);
-                        v = w.x + w.y;
-                    } else {
-                        v = tile[i];
+                // quad index -> (grid, k, j, quad of the row) with FP32 reciprocals: the quotients
+                // are below 2^10 and (index + 1/2) / divisor stays at least 1/(2 divisor) away from
+                // an integer.  With rows of the grids that are whole quads (nx a multiple of 4) a
+                // quad with a nonzero node is one float4 atomic (16-byte aligned), else one atomic
+                // per nonzero node.
+                const int qx = tx >> 2, vq = vol >> 2, nq = nent >> 2;
+                const float ivq = 1.f / (float)vq, iqxy = 1.f / (float)(qx * ty), iqx = 1.f / (float)qx;
+                const bool vec = (g.sy & 3) == 0 && (g.sz & 3) == 0;
+                for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+                    int4 v = tile4[i];
+                    for (int cp = 1; cp < (1 << lc); ++cp) {
+                        const int4 w = tile4[cp * (cs >> 2) + i];
+                        v.x += w.x;
+                        v.y += w.y;
+                        v.z += w.z;
+                        v.w += w.w;
                     }
-                    if (v != 0) {
-                        const int c = (int)(((float)i + 0.5f) * ivol), r = i - c * vol;
-                        const int k = (int)(((float)r + 0.5f) * itxy), r2 = r - k * tx * ty;
-                        const int j = (int)(((float)r2 + 0.5f) * itx), ii = r2 - j * tx;
+                    if ((v.x | v.y | v.z | v.w) != 0) {
+                        const int c = (int)(((float)i + 0.5f) * ivq), r = i - c * vq;
+                        const int k = (int)(((float)r + 0.5f) * iqxy), r2 = r - k * qx * ty;
+                        const int j = (int)(((float)r2 + 0.5f) * iqx), iq = r2 - j * qx;
                         const float inv = c == 0 ? pc.tunit[0] : c == 1 ? pc.tunit[1] : c == 2 ? pc.tunit[2] : pc.tunit[3];
-                        real* dst = c == 0 ? src.c[0] : c == 1 ? src.c[1] : c == 2 ? src.c[2] : src.c[3];
-                        atomicAdd(dst + G.at(box[0] + ii, box[1] + j, box[2] + k), (float)v * inv);
+                        real* dst = (c == 0 ? src.c[0] : c == 1 ? src.c[1] : c == 2 ? src.c[2] : src.c[3]) +
+                                    G.at(bx0 + 4 * iq, box[1] + j, box[2] + k);
+                        const float4 fv = make_float4((float)v.x * inv, (float)v.y * inv, (float)v.z * inv, (float)v.w * inv);
+                        if (vec) {
+                            atomicAdd(reinterpret_cast<float4*>(dst), fv);
+                        } else {
+                            if (v.x) atomicAdd(dst, fv.x);
+                            if (v.y) atomicAdd(dst + 1, fv.y);
+                            if (v.z) atomicAdd(dst + 2, fv.z);
+                            if (v.w) atomicAdd(dst + 3, fv.w);
+                        }
                     }
                 }
                 __syncthreads();   // the tile is reused by the next sub-step
