@@ -268,6 +268,25 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    def emitted_nodes(run, wl) -> int:
+        """Nodes one E/B emission writes: the deposit box of the particles' active cells widened
+        to nodes [lo - 1, hi + 2], plus the power plane outside it."""
+        inf = run.info()
+        P = run.particles()
+        c = [np.floor((P[:, d] - inf[o]) / inf[s_]).astype(np.int64)
+             for d, (o, s_) in enumerate((("x0", "dx"), ("y0", "dy"), ("z0", "dz")))]
+        n = (wl.nx, wl.ny, wl.nz)
+        act = np.ones(len(P), bool)
+        for d in range(3):
+            act &= (c[d] >= 1) & (c[d] <= n[d] - 3)
+        plane = (wl.nx - 2) * (wl.ny - 2)
+        if not act.any():
+            return plane
+        lo = [max(int(c[d][act].min()) - 1, 1) for d in range(3)]
+        hi = [min(int(c[d][act].max()) + 2, n[d] - 2) for d in range(3)]
+        ext = [hi[d] - lo[d] + 1 for d in range(3)]
+        return ext[0] * ext[1] * ext[2] + plane - (ext[0] * ext[1] if lo[2] <= int(inf["kp"]) <= hi[2] else 0)
+
     def timed_run(precision: int, steps: int, sample_clocks: bool, wl=None, labl=None):
         """K timed steps as a user runs them (captured graphs replayed), then K more steps with
         CUDA events around every kernel (launched one by one) for the per-kernel times."""
@@ -291,6 +310,7 @@ def main():
         barrier()
         clocks = clk.stop() if clk else None
         ms = ev0.elapsed_time(ev1)
+        nodes0 = emitted_nodes(run, wl)
         run.set_profiling(True)
         e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e2.record(stream)
@@ -300,6 +320,7 @@ def main():
         ms_prof = e2.elapsed_time(e3)
         stats = run.kernel_stats()
         info = run.info()
+        info["emitted_nodes"] = 0.5 * (nodes0 + emitted_nodes(run, wl))
         run.close()
         return ms, stats, launches, clocks, info, ms_prof
 
@@ -412,7 +433,7 @@ def main():
     # algorithmic bytes per launch (FP32-mixed)
     alg = {
         "stencil": 4 * 4 * 4 * ncell,                       # 4 potentials x (psi^n, psi^{n-1}, source, psi^{n+1})
-        "emit_eb": (3 + 3 + 1 + 6) * 4 * ncell,             # A^n, A^{n+1}, phi^n in; 6 components out
+        "emit_eb": 68 * info["emitted_nodes"],              # see emit_roof below
         "push_deposit": 2 * 48 * w.n_particles,             # particle state in and out (cell, offset, momentum)
         "clear_sources": 4 * 4 * ncell,
         "mur": 0,
@@ -434,6 +455,15 @@ def main():
         a = alg["stencil"] / (per_launch["stencil"] * 1e-3) / 1e9
         stencil_roof = {"achieved": a, "frac": a / hbm, "ms_per_launch": per_launch["stencil"],
                         "traffic": _ncu_traffic("stencil")}
+    emit_roof = None
+    if per_launch.get("emit_eb"):
+        # 68 B per emitted node: A^n, A^{n+1} (3 components each) and phi^n read, 6 E/B components
+        # written, 4 sources cleared; the box is the mean of the profiled steps' first and last
+        eb_bytes = 68 * info["emitted_nodes"]
+        a = eb_bytes / (per_launch["emit_eb"] * 1e-3) / 1e9
+        emit_roof = {"achieved": a, "frac": a / hbm, "ms_per_launch": per_launch["emit_eb"],
+                     "alg_bytes_per_launch": eb_bytes, "emitted_nodes": info["emitted_nodes"],
+                     "traffic": _ncu_traffic("emit_eb")}
 
     # ---- CPU baseline (oracle) and the error of the GPU path against it ----------------------
     cpu = None
@@ -485,6 +515,7 @@ def main():
         "bunch_loading": loading,
         "roofline": roof,
         "stencil_roofline": stencil_roof,
+        "emit_roofline": emit_roof,
         "cpu_baseline": cpu,
         "error_vs_oracle": err,
         "e2e": {"value": ws * cells * K / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / K,
