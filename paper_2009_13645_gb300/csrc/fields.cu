@@ -259,7 +259,10 @@ struct EmitArgs {
     StepConst step_c;
 };
 
-constexpr int EX = 32, EY = 8, EKZ = 8;              // tile and planes per block
+#ifndef MITHRA_EMIT_KZ
+#define MITHRA_EMIT_KZ 8
+#endif
+constexpr int EX = 32, EY = 8, EKZ = MITHRA_EMIT_KZ;  // tile and planes per block
 constexpr int RL = EX + 2, RH = EY + 2;               // region: columns i0-1 .. i0+32, rows j0-1 .. j0+8
 constexpr int RW = kEmitBoxW, RN = RW * RH;           // region rows are stored kEmitBoxW wide
 constexpr int EHALO = 2 * RL + 2 * EY;                // region positions outside the tile
