@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<r
 //
 // One block owns a 32 x 8 tile of node columns and marches a short run of z planes.  Each plane
 // of the six potentials and phi is read once, with a one-node halo, into shared memory; the
-// node-averaged sums S_c = <A_c^n> + <A_c^{n+1}> of the plane are formed once per node there;
+// sums S_c = 2 (<A_c^n> + <A_c^{n+1}>) of the node averages are formed once per node there (the
+// factors 1/2 live in the difference constants);
 // the z neighbours (S_x, S_y and phi at k -+ 1) stay in registers, so plane k is finished while
 // plane k+1 is being read.  The next plane's loads are issued before the current plane is
 // computed.
@@ -249,7 +250,10 @@ struct EmitArgs {
     const real* phi;     // phi^n (node), may be null when space charge is off
     real* eb[6];
     real* src[4];        // sources to clear inside the box (entries may be null)
-    real idt, i2dx, i2dy, i2dz;
+    // E from pair sums of the staggered values (0.5 / dt: the node average's 1/2 folded in), the
+    // gradient of phi (0.5 / d), B from sums of two pair sums (0.125 / d: the averages' 1/2 and
+    // the 1/2 of B's two time levels folded in; scaling by powers of two is exact)
+    real hdt, i2dx, i2dy, i2dz, b2dx, b2dy, b2dz;
     int nchunk;          // blocks along z covering the box; a further z slice emits plane kp
     int kp;              // plane emitted in full (< 0: none)
     const int* box;      // cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit; null: whole grid
@@ -272,7 +276,7 @@ static_assert(RW >= RL && RH == kEmitBoxH, "emit region inside the tensor-map bo
 
 // Shared memory of one block: raw[s] holds A_x^n, A_x^{n+1}, A_y^n, A_y^{n+1}, A_z^n, A_z^{n+1},
 // phi of plane p (s = (p - first plane) % ENS) over the region, filled ENS - 1 planes ahead;
-// sum[p & 1] the node-averaged sums S_x, S_y, S_z of plane p.  Each array of raw starts on a
+// sum[p & 1] the sums S_x, S_y, S_z of plane p.  Each array of raw starts on a
 // 128-byte boundary (the tensor copies' destination alignment).
 constexpr int ENS = 4;
 template <typename real>
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
             cp_async_commit();
         }
     };
-    auto navg = [](real u, real w) { return (real)0.5 * (u + w); };
+    auto pair = [](real u, real w) { return u + w; };   // twice the node average
 
     if constexpr (TM) {
         if (t == 0) {
@@ -442,9 +446,9 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
         // node averages and sums of plane p at this thread's positions (A_z of the first plane
         // has no previous plane: its S_z and E_z are never read)
         const real az0 = r[4][qo], az1 = r[5][qo], php = use_phi ? r[6][qo] : (real)0;
-        const real nx0 = navg(r[0][qo], r[0][qo - 1]), nx1 = navg(r[1][qo], r[1][qo - 1]);
-        const real ny0 = navg(r[2][qo], r[2][qo - RW]), ny1 = navg(r[3][qo], r[3][qo - RW]);
-        const real nz0 = navg(az0, az0m), nz1 = navg(az1, az1m);
+        const real nx0 = pair(r[0][qo], r[0][qo - 1]), nx1 = pair(r[1][qo], r[1][qo - 1]);
+        const real ny0 = pair(r[2][qo], r[2][qo - RW]), ny1 = pair(r[3][qo], r[3][qo - RW]);
+        const real nz0 = pair(az0, az0m), nz1 = pair(az1, az1m);
         const real sxp = nx0 + nx1, syp = ny0 + ny1;
         sm.sum[b][0][qo] = sxp;
         sm.sum[b][1][qo] = syp;
@@ -452,40 +456,40 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
         az0m = az0;
         az1m = az1;
         if (has_halo) {
-            if (hrow) sm.sum[b][0][qh] = navg(r[0][qh], r[0][qh - 1]) + navg(r[1][qh], r[1][qh - 1]);
-            if (hcol) sm.sum[b][1][qh] = navg(r[2][qh], r[2][qh - RW]) + navg(r[3][qh], r[3][qh - RW]);
+            if (hrow) sm.sum[b][0][qh] = pair(r[0][qh], r[0][qh - 1]) + pair(r[1][qh], r[1][qh - 1]);
+            if (hcol) sm.sum[b][1][qh] = pair(r[2][qh], r[2][qh - RW]) + pair(r[3][qh], r[3][qh - RW]);
             const real h0 = r[4][qh], h1 = r[5][qh];
-            sm.sum[b][2][qh] = navg(h0, haz0m) + navg(h1, haz1m);
+            sm.sum[b][2][qh] = pair(h0, haz0m) + pair(h1, haz1m);
             haz0m = h0;
             haz1m = h1;
         }
         __syncthreads();
         const real(*S)[RN] = sm.sum[b];
         const int q = qo;
-        real ex = (nx0 - nx1) * a.idt;
-        real ey = (ny0 - ny1) * a.idt;
-        const real ez = (nz0 - nz1) * a.idt;
+        real ex = (nx0 - nx1) * a.hdt;
+        real ey = (ny0 - ny1) * a.hdt;
+        const real ez = (nz0 - nz1) * a.hdt;
         if (use_phi) {
             ex -= (r[6][q + 1] - r[6][q - 1]) * a.i2dx;
             ey -= (r[6][q + RW] - r[6][q - RW]) * a.i2dy;
         }
-        const real bz = (S[1][q + 1] - S[1][q - 1]) * a.i2dx - (S[0][q + RW] - S[0][q - RW]) * a.i2dy;
-        const real bxp = (S[2][q + RW] - S[2][q - RW]) * a.i2dy;
-        const real byp = (S[2][q + 1] - S[2][q - 1]) * a.i2dx;
+        const real bz = (S[1][q + 1] - S[1][q - 1]) * a.b2dx - (S[0][q + RW] - S[0][q - RW]) * a.b2dy;
+        const real bxp = (S[2][q + RW] - S[2][q - RW]) * a.b2dy;
+        const real byp = (S[2][q + 1] - S[2][q - 1]) * a.b2dx;
         // plane k = p - 1 has its z neighbours now
         const int k = p - 1;
         if (k >= ka && emit && !(skip_xy && k >= bl[2] && k <= bh[2])) {
             const int64_t id = (int64_t)k * sz + off_o;
-            const real bx = bxp1 - (syp - sy0) * a.i2dz;
-            const real by = (sxp - sx0) * a.i2dz - byp1;
+            const real bx = bxp1 - (syp - sy0) * a.b2dz;
+            const real by = (sxp - sx0) * a.b2dz - byp1;
             real ezk = ez1;
             if (use_phi) ezk -= (php - ph0) * a.i2dz;
             a.eb[0][id] = ex1;
             a.eb[1][id] = ey1;
             a.eb[2][id] = ezk;
-            a.eb[3][id] = (real)0.5 * bx;
-            a.eb[4][id] = (real)0.5 * by;
-            a.eb[5][id] = (real)0.5 * bz1;
+            a.eb[3][id] = bx;
+            a.eb[4][id] = by;
+            a.eb[5][id] = bz1;
             if (clear) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
@@ -699,10 +703,13 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     for (int c = 0; c < 6; ++c) a.eb[c] = eb.c[c];
     for (int c = 0; c < 4; ++c) a.src[c] = (bx.box && bx.clear) ? (real*)L.src[c] : nullptr;
     if (!g.space_charge) a.src[3] = nullptr;
-    a.idt = (real)(1.0 / g.dt);
+    a.hdt = (real)(1.0 / g.dt) * (real)0.5;
     a.i2dx = (real)(0.5 / g.dx);
     a.i2dy = (real)(0.5 / g.dy);
     a.i2dz = (real)(0.5 / g.dz);
+    a.b2dx = a.i2dx * (real)0.25;
+    a.b2dy = a.i2dy * (real)0.25;
+    a.b2dz = a.i2dz * (real)0.25;
     a.kp = bx.kp;
     a.box = bx.box;
     a.box_reset = bx.box_reset;
