@@ -8,6 +8,10 @@
 * external field: Lorentz invariants E.B and E^2 - c^2 B^2 of the transformed field, the
   rest-frame on-axis values, div B' = 0 everywhere and curl B' = 0 inside the undulator,
   the Gaussian beam tending to the plane wave for a large waist;
+* zigzag current of a move that stays in its cell: on each of the cell's 12 edges the current
+  is q D_l / (V dt) times the path average of the two transverse linear weights along the
+  straight move, the average taken here by Gauss-Legendre quadrature (the relay point of such a
+  move is its midpoint, so the two zigzag pieces are the halves of one segment);
 * particle boost: the inverse Lorentz transform recovers the lab particles;
 * Lorentz gauge: with charge-conserving deposition the gauge residual G evolves as a
   source-free field (the manual's claim that the gauge holds automatically).
@@ -103,6 +107,51 @@ def test_charge_continuity_and_current_moment(maxmove):
         expect = q * np.sum(new[:, l] - old[:, l]) / dt
         assert abs(moment - expect) < 1e-11 * abs(q * maxmove * D[l] * n / dt)
     assert abs(np.sum(rho1) * vol - q * n) < 1e-12 * abs(q * n)
+
+
+def test_zigzag_current_of_a_move_inside_one_cell():
+    nx, ny, nz = 12, 11, 13
+    D = np.array([1.1e-3, 0.9e-3, 1.3e-3])
+    w = vacuum(nx, ny, nz, *D, solver=1, courant=0.5)
+    w = workloads.scaled(w, charge_e=1e6)
+    r = oracle.Run(oracle.params_from(w), np.zeros((1, 6)))
+    inf = r.info()
+    org = np.array([inf["x0"], inf["y0"], inf["z0"]])
+    q, dt, vol = inf["q"], inf["dt"], float(np.prod(D))
+    tq, wq = np.polynomial.legendre.leggauss(4)   # exact for the quadratic integrands
+    tq, wq = 0.5 * (tq + 1.0), 0.5 * wq
+    rng = np.random.default_rng(5)
+    names = ("Jx", "Jy", "Jz")
+    for trial in range(20):
+        cell = rng.integers(4, 7, 3)
+        fa = rng.uniform(0.02, 0.98, 3)
+        fb = np.clip(fa + rng.uniform(-0.5, 0.5, 3), 0.01, 0.99)
+        old = np.zeros((1, 6))
+        new = np.zeros((1, 6))
+        old[0, :3] = org + (cell + fa) * D
+        new[0, :3] = org + (cell + fb) * D
+        r.deposit_moves(old, new)
+        J = [r.field(n) for n in names]
+        path = fa[None, :] + tq[:, None] * (fb - fa)[None, :]   # offsets along the move
+        for l in range(3):
+            m, n = (l + 1) % 3, (l + 2) % 3
+            pre = q * (fb[l] - fa[l]) * D[l] / (vol * dt)
+            got = np.zeros((2, 2))
+            want = np.zeros((2, 2))
+            for sm in (0, 1):
+                for sn in (0, 1):
+                    wm = path[:, m] if sm else 1.0 - path[:, m]
+                    wn = path[:, n] if sn else 1.0 - path[:, n]
+                    want[sm, sn] = pre * np.sum(wq * wm * wn)
+                    idx = [0, 0, 0]
+                    idx[l] = cell[l]
+                    idx[m] = cell[m] + sm
+                    idx[n] = cell[n] + sn
+                    got[sm, sn] = J[l][idx[2], idx[1], idx[0]]
+            scale = abs(pre)
+            assert np.max(np.abs(got - want)) <= 1e-12 * scale, (trial, l, got, want)
+            # nothing else on that grid
+            assert abs(np.sum(J[l]) - np.sum(got)) <= 1e-12 * scale
 
 
 def _undulator_run(kind, K=1.2, gamma=30.0, lu=0.02, **kw):
