@@ -71,6 +71,7 @@ struct TmaArgs {
     int ex[4], ey[4], ez[4];
     int ncomp;
     real a1, ax, ay, a6, w, w0, s[4];
+    real axw, axw0, ayw, ayw0;   // ax w, ax w0, ay w, ay w0 (products taken in FP64)
     int* err;
 };
 
@@ -139,28 +140,30 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     auto hrow = [&](int p, int dy) -> const real* {
         return (const real*)(smem + ((p - pfirst) % NST) * T::STAGE) + (ty + 1 + dy) * T::W + cx + T::HX;
     };
-    // registers of planes k-1 (0), k (1), k+1 (2): the pair (ca, cb), x-1 (xm), x+2 (xq), the rows
-    // below (ya, yb) and above (za, zb)
-    real ca0, ca1, ca2, cb0, cb1, cb2, xm0, xm1, xm2, xq0, xq1, xq2;
-    real ya0, ya1, ya2, yb0, yb1, yb2, za0, za1, za2, zb0, zb1, zb2;
-    auto load = [&](int p, real& ca, real& cb, real& xm, real& xq, real& ya, real& yb, real& za, real& zb) {
+    // registers of planes k-1 (0), k (1), k+1 (2): the pair (ca, cb), and the sums of each cell's
+    // two x neighbours (XA = x-1 + x+1 of the first cell, XB of the second) and of its two y
+    // neighbours (YA, YB), formed once per plane and used in three updates; x+2 alone (xq) for the
+    // Mur x face
+    real ca0, ca1, ca2, cb0, cb1, cb2, xq0, xq1, xq2;
+    real XA0, XA1, XA2, XB0, XB1, XB2, YA0, YA1, YA2, YB0, YB1, YB2;
+    auto load = [&](int p, real& ca, real& cb, real& xq, real& XA, real& XB, real& YA, real& YB) {
         const real* r = hrow(p, 0);
         const V2 c = *(const V2*)r;
         ca = c.x;
         cb = c.y;
-        xm = r[-1];
+        const real xm = r[-1];
         xq = r[2];
         const V2 m = *(const V2*)hrow(p, -1);
-        ya = m.x;
-        yb = m.y;
         const V2 q = *(const V2*)hrow(p, 1);
-        za = q.x;
-        zb = q.y;
+        XA = cb + xm;
+        XB = xq + ca;
+        YA = q.x + m.x;
+        YB = q.y + m.y;
     };
     wait_plane(pfirst);
     wait_plane(pfirst + 1);
-    load(pfirst, ca0, cb0, xm0, xq0, ya0, yb0, za0, zb0);
-    load(pfirst + 1, ca1, cb1, xm1, xq1, ya1, yb1, za1, zb1);
+    load(pfirst, ca0, cb0, xq0, XA0, XB0, YA0, YB0);
+    load(pfirst + 1, ca1, cb1, xq1, XA1, XB1, YA1, YB1);
     ok = __syncthreads_and(ok) != 0;
     if (ok && threadIdx.x == 0 && pfirst + NST <= plast) {
         issue(pfirst + NST);
@@ -171,19 +174,16 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     int k = k0;
     for (; k <= k1 && ok; ++k) {
         wait_plane(k + 1);
-        load(k + 1, ca2, cb2, xm2, xq2, ya2, yb2, za2, zb2);
+        load(k + 1, ca2, cb2, xq2, XA2, XB2, YA2, YB2);
         const unsigned char* stk = smem + ((k - pfirst) % NST) * T::STAGE;
         const V2 pm = *(const V2*)((const real*)(stk + T::OFF_PREV) + ty * TX + cx);
         const V2 sr = *(const V2*)((const real*)(stk + T::OFF_SRC) + ty * TX + cx);
         if ((mineA || mineB) && ok) {
-            const real bxpA = a.w * (cb0 + cb2) + a.w0 * cb1, bxmA = a.w * (xm0 + xm2) + a.w0 * xm1;
-            const real bypA = a.w * (za0 + za2) + a.w0 * za1, bymA = a.w * (ya0 + ya2) + a.w0 * ya1;
-            const real vA = a.a1 * ca1 - pm.x + a.ax * (bxpA + bxmA) + a.ay * (bypA + bymA) + a.a6 * (ca0 + ca2) +
-                            s * sr.x;
-            const real bxpB = a.w * (xq0 + xq2) + a.w0 * xq1, bxmB = a.w * (ca0 + ca2) + a.w0 * ca1;
-            const real bypB = a.w * (zb0 + zb2) + a.w0 * zb1, bymB = a.w * (yb0 + yb2) + a.w0 * yb1;
-            const real vB = a.a1 * cb1 - pm.y + a.ax * (bxpB + bxmB) + a.ay * (bypB + bymB) + a.a6 * (cb0 + cb2) +
-                            s * sr.y;
+            // ax (w (N^{k-1} + N^{k+1}) + w0 N^k) over the two x neighbours, likewise along y
+            const real vA = a.a1 * ca1 - pm.x + a.axw * (XA0 + XA2) + a.axw0 * XA1 + a.ayw * (YA0 + YA2) +
+                            a.ayw0 * YA1 + a.a6 * (ca0 + ca2) + s * sr.x;
+            const real vB = a.a1 * cb1 - pm.y + a.axw * (XB0 + XB2) + a.axw0 * XB1 + a.ayw * (YB0 + YB2) +
+                            a.ayw0 * YB1 + a.a6 * (cb0 + cb2) + s * sr.y;
             const int64_t row = (int64_t)k * sz + (int64_t)y * sy;
             if (mineA && mineB) {
                 V2 v;
@@ -199,24 +199,22 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
                 // Mur x faces (the formula and the summation order of k_mur_faces)
                 const bool o2 = a.mur != 1;
                 if (x == 0 && mineB)   // b = x (this pair's first cell), q = x + 1
-                    o[row] = a.mf0 * (pm.x + vB) + a.mf1 * (ca1 + cb1) - pm.y +
-                             a.mfy * (o2 ? za1 + ya1 + zb1 + yb1 : (real)0) +
+                    o[row] = a.mf0 * (pm.x + vB) + a.mf1 * (ca1 + cb1) - pm.y + a.mfy * (o2 ? YA1 + YB1 : (real)0) +
                              a.mfz * (o2 ? ca2 + ca0 + cb2 + cb0 : (real)0);
                 if (mineA && x == ex - 2)   // q = x, b = x + 1 (this pair's second cell)
                     o[row + x + 1] = a.mf0 * (pm.y + vA) + a.mf1 * (cb1 + ca1) - pm.x +
-                                     a.mfy * (o2 ? zb1 + yb1 + za1 + ya1 : (real)0) +
-                                     a.mfz * (o2 ? cb2 + cb0 + ca2 + ca0 : (real)0);
+                                     a.mfy * (o2 ? YB1 + YA1 : (real)0) + a.mfz * (o2 ? cb2 + cb0 + ca2 + ca0 : (real)0);
                 if (mineB && x + 1 == ex - 2) {   // q = x + 1, b = x + 2 (the next pair's first cell)
                     const real nmb = cx + 2 < TX ? ((const real*)(stk + T::OFF_PREV))[ty * TX + cx + 2]
                                                  : a.prev[comp][row + x + 2];
                     o[row + x + 2] = a.mf0 * (nmb + vB) + a.mf1 * (xq1 + cb1) - pm.y +
-                                     a.mfy * (o2 ? hrow(k, 1)[2] + hrow(k, -1)[2] + zb1 + yb1 : (real)0) +
+                                     a.mfy * (o2 ? hrow(k, 1)[2] + hrow(k, -1)[2] + YB1 : (real)0) +
                                      a.mfz * (o2 ? xq2 + xq0 + cb2 + cb0 : (real)0);
                 }
             }
         }
-        ca0 = ca1, ca1 = ca2, cb0 = cb1, cb1 = cb2, xm0 = xm1, xm1 = xm2, xq0 = xq1, xq1 = xq2;
-        ya0 = ya1, ya1 = ya2, yb0 = yb1, yb1 = yb2, za0 = za1, za1 = za2, zb0 = zb1, zb1 = zb2;
+        ca0 = ca1, ca1 = ca2, cb0 = cb1, cb1 = cb2, xq0 = xq1, xq1 = xq2;
+        XA0 = XA1, XA1 = XA2, XB0 = XB1, XB1 = XB2, YA0 = YA1, YA1 = YA2, YB0 = YB1, YB1 = YB2;
         ok = __syncthreads_and(ok) != 0;
         if (ok && threadIdx.x == 0 && k + NST <= plast) {
             issue(k + NST);
@@ -340,6 +338,10 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* co
     a.a6 = (real)cf.a6;
     a.w = (real)cf.w;
     a.w0 = (real)cf.w0;
+    a.axw = (real)(cf.ax * cf.w);
+    a.axw0 = (real)(cf.ax * cf.w0);
+    a.ayw = (real)(cf.ay * cf.w);
+    a.ayw0 = (real)(cf.ay * cf.w0);
     a.err = err;
     a.mur = (mur && tma_x_faces<real>()) ? ((mur->ft[0][0] != 0.0 || mur->ft[0][1] != 0.0) ? 2 : 1) : 0;
     a.mf0 = mur ? (real)mur->f0[0] : (real)0;
