@@ -155,7 +155,9 @@ int mithra_ellipsoid_bunch(const mithra_ellipsoid *e, int64_t n, double *out6, v
 
 /* Install the device allocator used by every later mithra_create (process-wide).
    alloc(ctx, bytes) returns a device pointer or NULL; free(ctx, ptr).  Pass NULLs to restore
-   cudaMalloc/cudaFree.  Runs created earlier keep the allocator they were created with. */
+   cudaMalloc/cudaFree.  Runs created earlier keep the allocator they were created with.  Any
+   alignment is accepted: the library asks for 256 bytes more than it needs and aligns its
+   arrays to 256 bytes itself. */
 typedef void *(*mithra_alloc_fn)(void *ctx, size_t bytes);
 typedef void (*mithra_free_fn)(void *ctx, void *ptr);
 int mithra_set_allocator(mithra_alloc_fn alloc, mithra_free_fn free_fn, void *ctx);

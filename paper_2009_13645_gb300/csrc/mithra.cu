@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -84,34 +85,44 @@ extern "C" const char* mithra_kernel_name(int id)
 // ---------------------------------------------------------------------------------------
 // the run
 // ---------------------------------------------------------------------------------------
+// Device memory of one run.  Every array starts on a 256-byte boundary: the tensor maps, the
+// 16-byte vector atomics of the deposit flush and the vector loads rely on it.  cudaMalloc
+// guarantees it; a caller-installed allocator may return any alignment, so its blocks are
+// requested 256 bytes longer and aligned here (the original pointer is what gets freed).
 struct DevMem {
+    struct Block {
+        void* p;      // the aligned pointer handed out
+        size_t bytes; // bytes taken from the allocator
+        void* raw;    // the pointer the allocator returned
+    };
     Allocator a;
-    std::vector<std::pair<void*, size_t>> blocks;
+    std::vector<Block> blocks;
     size_t total = 0;
     void* get(size_t bytes)
     {
         if (bytes == 0) bytes = 16;
         bytes = (bytes + 255) & ~(size_t)255;
-        void* p = nullptr;
+        void* raw = nullptr;
         if (a.alloc) {
-            p = a.alloc(a.ctx, bytes);
-        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            bytes += 256;
+            raw = a.alloc(a.ctx, bytes);
+        } else if (cudaMalloc(&raw, bytes) != cudaSuccess) {
             cudaGetLastError();
-            p = nullptr;
+            raw = nullptr;
         }
-        if (p) {
-            blocks.emplace_back(p, bytes);
-            total += bytes;
-        }
+        if (!raw) return nullptr;
+        void* p = (void*)(((uintptr_t)raw + 255) & ~(uintptr_t)255);
+        blocks.push_back(Block{p, bytes, raw});
+        total += bytes;
         return p;
     }
     void release(void* p)
     {
         for (size_t i = 0; i < blocks.size(); ++i)
-            if (blocks[i].first == p) {
-                total -= blocks[i].second;
-                if (a.free_fn) a.free_fn(a.ctx, p);
-                else cudaFree(p);
+            if (blocks[i].p == p) {
+                total -= blocks[i].bytes;
+                if (a.free_fn) a.free_fn(a.ctx, blocks[i].raw);
+                else cudaFree(blocks[i].raw);
                 blocks.erase(blocks.begin() + (long)i);
                 return;
             }
@@ -119,8 +130,8 @@ struct DevMem {
     void release_all()
     {
         for (auto& b : blocks) {
-            if (a.free_fn) a.free_fn(a.ctx, b.first);
-            else cudaFree(b.first);
+            if (a.free_fn) a.free_fn(a.ctx, b.raw);
+            else cudaFree(b.raw);
         }
         blocks.clear();
         total = 0;
@@ -1207,6 +1218,9 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
              2 * up(cap * nf * 8);
     }
     if (gr->bunch_every > 0) t += up(14 * 304 * 8) + 2 * up((cap / gr->bunch_every + 1) * 15 * 8);
+    // the small buffers (step state, counters, error word, seed planes' bookkeeping) and the 256
+    // bytes of alignment slack every allocation takes from a caller's allocator (at most 128)
+    t += 128 * 256;
     return t;
 }
 
