@@ -7,6 +7,8 @@
 * initial bunching factor of a bunch modulated at the resonance equals the modulation;
 * radiated-power diagnostic: cycle-averaged flux a^2/(2 mu0 c) of a plane wave, the Doppler
   factor gamma0^2 (1 + beta0)^2 to the lab, and coherent N^2 scaling;
+* absolute radiated power: one electron in a weak undulator is, in the rest frame, a harmonic
+  dipole, and the power through the sampling plane equals the dipole's flux through it;
 * source signs and factors (Eqs. WaveA, WaveF): the potential around an electron is negative
   and a slowly moving charge has A_z / phi = v_z / c^2.
 """
@@ -178,6 +180,65 @@ def test_power_coherent_n_squared():
     assert sel.sum() > 50
     ratio = out[1][sel] / out[0][sel]
     assert np.max(np.abs(ratio - 4.0)) < 1e-3
+
+
+def test_undulator_radiation_power_equals_dipole_flux():
+    """One electron in a weak planar undulator (K = 0.1) oscillates harmonically in the rest frame
+    at w* = gamma0 beta0 c k_u with amplitude x0, a dipole p0 = q x0.  The time-averaged Poynting
+    vector of a harmonic dipole is radial with magnitude mu0 p0^2 w^4 sin^2(psi) / (32 pi^2 c r^2)
+    at every distance (the near-field terms carry no mean power), psi the angle to the dipole
+    axis.  Integrated over the sampling plane's interior (two rest-frame wavelengths
+    downstream, 6 x 6 wavelengths), it must give the diagnostic's rest-frame power, the lab
+    series over the Doppler factor gamma0^2 (1 + beta0)^2 (pinned by the plane-wave test).  x0
+    comes from the velocity over one period (a constant drift from the undulator entrance drops
+    out) and is checked against K / (gamma k_u).  The grid has 10 cells per rest-frame wavelength
+    and a period of exactly 20 steps, so the static Coulomb field does not leak into the DFT;
+    what remains is the discretisation and the Mur boundaries, 2 to 3 % here."""
+    gamma, K, lu, cpl = 20.0, 0.1, 0.03, 10
+    g0 = gamma / math.sqrt(1 + K * K / 2)
+    b0 = math.sqrt(1 - 1 / g0 ** 2)
+    lam = lu / g0
+    nt = 6 * cpl
+    base = workloads.WORKLOADS["undulator_24x24x96"]
+    # FD Courant number such that one period is 2 cpl steps
+    w = workloads.scaled(base, n_particles=1, charge_e=1.0, gamma=gamma, K=K, lambda_u=lu, n_periods=60,
+                         space_charge=1, nx=nt, ny=nt, nz=8 * cpl, dx=lam / cpl, dy=lam / cpl,
+                         dz=lam / (cpl * g0), solver=1, courant=math.sqrt(3) / (2 * b0), rel_espread=0.0,
+                         sig_x=0.0, sig_y=0.0, sig_z=0.0, plane_dist=2 * lam / g0, dist_head=0.0)
+    lab = np.array([[0.0, 0.0, 0.0, 0.0, 0.0, math.sqrt(gamma * gamma - 1)]])
+    r = oracle.Run(oracle.params_from(w), lab)
+    inf = r.info()
+    M, dt, om = int(inf["M"]), inf["dt"], inf["omega_h"]
+    assert M == 2 * cpl and abs(2 * math.pi / (om * dt) - M) < 1e-9
+    steps = 10 * M
+    xs, zs, vs = np.zeros(steps), np.zeros(steps), np.zeros(steps)
+    for n in range(steps):
+        r.step(1)
+        P = r.particles()[0]
+        xs[n], zs[n] = P[0], P[2]
+        vs[n] = C0 * P[3] / math.sqrt(1 + P[3] ** 2 + P[4] ** 2 + P[5] ** 2)
+    p, _, _ = r.series()
+    prest = p / (inf["gamma0"] ** 2 * (1 + inf["beta0"]) ** 2)
+    zp = inf["z0"] + inf["kp"] * inf["dz"]
+    q = abs(inf["q"])
+    dx, dy = inf["dx"], inf["dy"]
+    sub = (np.arange(8) + 0.5) / 8 - 0.5            # 8 x 8 midpoints in every node's dx dy
+    xn = (inf["x0"] + np.arange(1, nt - 1)[:, None] * dx + sub[None, :] * dx).ravel()
+    yn = (inf["y0"] + np.arange(1, nt - 1)[:, None] * dy + sub[None, :] * dy).ravel()
+    ratios = []
+    for n in range(6 * M, steps, M // 2):
+        win = np.arange(n - M + 1, n + 1)
+        t = inf["T0"] + (win + 1.5) * dt
+        x0 = abs((2 / M) * np.sum(vs[win] * np.exp(-1j * om * t))) / om
+        assert abs(x0 / (K / (gamma * 2 * math.pi / lu)) - 1) < 0.03
+        X, Y = np.meshgrid(xn - xs[win].mean(), yn, indexing="ij")
+        d = zp - zs[win].mean()
+        R = np.sqrt(X ** 2 + Y ** 2 + d ** 2)
+        Sz = MU0 * (q * x0) ** 2 * om ** 4 / (32 * math.pi ** 2 * C0) * (1 - (X / R) ** 2) / R ** 2 * (d / R)
+        ratios.append(prest[n] / (Sz.sum() * dx * dy / 64))
+    ratios = np.array(ratios)
+    assert len(ratios) >= 8
+    assert np.all(np.abs(ratios - 1) < 0.08), ratios
 
 
 def test_source_signs_coulomb_and_vector_potential():
