@@ -12,9 +12,10 @@ namespace mithra {
 
 // ---------------------------------------------------------------------------------------
 // Stencil.  Each thread owns one (i, j) column of one component lattice and marches a
-// chunk of z planes, keeping the three planes k-1, k, k+1 of its own column and of its four
-// transverse neighbours in registers, so that every psi^n value is loaded once per column
-// that needs it (the 4 neighbour loads per plane hit L1/L2).
+// chunk of z planes, keeping the three planes k-1, k, k+1 of its own column and the sums of its
+// two x neighbours and of its two y neighbours in registers, so that every psi^n value is loaded
+// once per column that needs it (the 4 neighbour loads per plane hit L1/L2) and each sum is
+// formed once for the three updates that read it.
 // ---------------------------------------------------------------------------------------
 template <typename real>
 struct StencilArgs {
@@ -23,6 +24,7 @@ struct StencilArgs {
     const real* src[4];  // J_x, J_y, J_z, rho
     real* out[4];        // psi^{n+1}
     real a1, ax, ay, a6, w, w0, s[4];   // coefficients; w = A, w0 = 1 - 2A; s = (c dt)^2 mu0 | (c dt)^2 / eps0
+    real axw, axw0, ayw, ayw0;          // ax w, ax w0, ay w, ay w0 (products taken in FP64)
     int ex[4], ey[4], ez[4];            // extents of each component lattice
     int ncomp;
     int kchunk;
@@ -46,37 +48,31 @@ __global__ void __launch_bounds__(256) k_stencil(StencilArgs<real> a, int64_t sy
     real* __restrict__ o = a.out[comp];
     const real s = a.s[comp];
     const int64_t col = (int64_t)j * sy + i;
-    // registers: [0] = k-1, [1] = k, [2] = k+1
-    real c0, c1, c2, xp0, xp1, xp2, xm0, xm1, xm2, yp0, yp1, yp2, ym0, ym1, ym2;
+    // registers: [0] = k-1, [1] = k, [2] = k+1; X = x-1 + x+1, Y = y-1 + y+1
+    real c0, c1, c2, X0, X1, X2, Y0, Y1, Y2;
     {
         const int64_t b0 = col + (int64_t)(k0 - 1) * sz, b1 = b0 + sz;
-        c0 = __ldg(p + b0); c1 = __ldg(p + b1);
-        xp0 = __ldg(p + b0 + 1); xp1 = __ldg(p + b1 + 1);
-        xm0 = __ldg(p + b0 - 1); xm1 = __ldg(p + b1 - 1);
-        yp0 = __ldg(p + b0 + sy); yp1 = __ldg(p + b1 + sy);
-        ym0 = __ldg(p + b0 - sy); ym1 = __ldg(p + b1 - sy);
+        c0 = __ldg(p + b0);
+        c1 = __ldg(p + b1);
+        X0 = __ldg(p + b0 + 1) + __ldg(p + b0 - 1);
+        X1 = __ldg(p + b1 + 1) + __ldg(p + b1 - 1);
+        Y0 = __ldg(p + b0 + sy) + __ldg(p + b0 - sy);
+        Y1 = __ldg(p + b1 + sy) + __ldg(p + b1 - sy);
     }
     for (int k = k0; k <= k1; ++k) {
         const int64_t b = col + (int64_t)k * sz;
         const int64_t b2 = b + sz;
         c2 = __ldg(p + b2);
-        xp2 = __ldg(p + b2 + 1);
-        xm2 = __ldg(p + b2 - 1);
-        yp2 = __ldg(p + b2 + sy);
-        ym2 = __ldg(p + b2 - sy);
-        // z-averaged transverse neighbours (Eq. NSFDtrick)
-        const real bxp = a.w * (xp0 + xp2) + a.w0 * xp1;
-        const real bxm = a.w * (xm0 + xm2) + a.w0 * xm1;
-        const real byp = a.w * (yp0 + yp2) + a.w0 * yp1;
-        const real bym = a.w * (ym0 + ym2) + a.w0 * ym1;
-        const real v = a.a1 * c1 - __ldg(pm + b) + a.ax * (bxp + bxm) + a.ay * (byp + bym) + a.a6 * (c0 + c2)
-                     + s * __ldg(S + b);
+        X2 = __ldg(p + b2 + 1) + __ldg(p + b2 - 1);
+        Y2 = __ldg(p + b2 + sy) + __ldg(p + b2 - sy);
+        // z-averaged transverse neighbours (Eq. NSFDtrick): ax (w (N^{k-1} + N^{k+1}) + w0 N^k)
+        // over the two x neighbours, likewise along y
+        const real v = a.a1 * c1 - __ldg(pm + b) + a.axw * (X0 + X2) + a.axw0 * X1 + a.ayw * (Y0 + Y2) +
+                       a.ayw0 * Y1 + a.a6 * (c0 + c2) + s * __ldg(S + b);
         o[b] = v;
-        c0 = c1; c1 = c2;
-        xp0 = xp1; xp1 = xp2;
-        xm0 = xm1; xm1 = xm2;
-        yp0 = yp1; yp1 = yp2;
-        ym0 = ym1; ym1 = ym2;
+        c0 = c1, c1 = c2;
+        X0 = X1, X1 = X2;
+        Y0 = Y1, Y1 = Y2;
     }
 }
 
@@ -538,6 +534,10 @@ cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const Sten
     a.a6 = (real)cf.a6;
     a.w = (real)cf.w;
     a.w0 = (real)cf.w0;
+    a.axw = (real)(cf.ax * cf.w);
+    a.axw0 = (real)(cf.ax * cf.w0);
+    a.ayw = (real)(cf.ay * cf.w);
+    a.ayw0 = (real)(cf.ay * cf.w0);
     a.ncomp = ncomp;
     a.kchunk = 32;
     const dim3 blk(32, 8);
