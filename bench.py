@@ -107,10 +107,20 @@ class ClockSampler:
 
 
 def _source_hash(files):
+    """Hash of the sources a capture was taken from: a path stands for the whole file; a dict
+    {"file": path, "sections": [[from, to], ...]} for the text from each `from` marker up to the
+    next `to` marker (the kernel's own code in a file that holds several kernels)."""
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        if isinstance(f, dict):
+            with open(os.path.join(ROOT, f["file"]), encoding="utf-8") as fh:
+                text = fh.read()
+            for a, b in f["sections"]:
+                i = text.index(a)
+                h.update(text[i:text.index(b, i)].encode())
+        else:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
