@@ -42,6 +42,29 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max_over_ranks(x: float, ws: int, device: str) -> float:
+    """The maximum of x over the ranks (the job's time is its slowest rank's)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier_ranks(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def whole_job_rate(ws: int, units_per_rank_step: float, steps: int, ms_max: float) -> float:
+    """Units per second of the whole job: every rank processes its own replica's units each
+    step (weak scaling), over the slowest rank's time."""
+    return ws * units_per_rank_step * steps / (ms_max * 1e-3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -267,16 +290,11 @@ def main():
     K, W = args.steps, max(args.warmup, 3)
 
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+        barrier_ranks(ws)
         torch.cuda.synchronize()
 
     def reduce_max(x: float) -> float:
-        if ws == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max_over_ranks(x, ws, "cuda")
 
     def emitted_nodes(run, wl) -> int:
         """Nodes one E/B emission writes: the deposit box of the particles' active cells widened
@@ -342,8 +360,8 @@ def main():
         K64 = max(10, K // 2)
         ms64, stats64, _, _, _, _ = timed_run(0, K64, False)
         ms64 = reduce_max(ms64)
-        res64 = {"value": ws * cells * K64 / (ms64 * 1e-3), "unit": "cell-updates/s",
-                 "particle_pushes_per_s": ws * w.n_particles * K64 / (ms64 * 1e-3), "ms_per_step": ms64 / K64,
+        res64 = {"value": whole_job_rate(ws, cells, K64, ms64), "unit": "cell-updates/s",
+                 "particle_pushes_per_s": whole_job_rate(ws, w.n_particles, K64, ms64), "ms_per_step": ms64 / K64,
                  "steps": K64, "kernel_ms_per_step": {k: v[0] / K64 for k, v in stats64.items() if v[1]}}
 
     # ---- the same step through an undulator line (modules, gaps, taper) ----------------------
@@ -354,8 +372,8 @@ def main():
         msa, statsa, _, _, _, _ = timed_run(1, K, False, wa, laba)
         msa = reduce_max(msa)
         ca = wa.nx * wa.ny * wa.nz
-        arr = {"workload": wa.name, "value": ws * ca * K / (msa * 1e-3), "unit": "cell-updates/s",
-               "particle_pushes_per_s": ws * wa.n_particles * K / (msa * 1e-3), "ms_per_step": msa / K,
+        arr = {"workload": wa.name, "value": whole_job_rate(ws, ca, K, msa), "unit": "cell-updates/s",
+               "particle_pushes_per_s": whole_job_rate(ws, wa.n_particles, K, msa), "ms_per_step": msa / K,
                "steps": K, "precision": "fp32-mixed",
                "undulator": f"{wa.n_modules} modules x {wa.n_periods:g} periods, gap {wa.gap:g} m, "
                             f"K = {wa.K:g} + i x {wa.taper:g}",
@@ -369,7 +387,7 @@ def main():
         msd, statsd, _, _, _, _ = timed_run(1, K, False, wd, lab)
         msd = reduce_max(msd)
         diag = {"ms_per_step": msd / K, "overhead_ms_per_step": (msd - ms32) / K,
-                "value": ws * cells * K / (msd * 1e-3), "unit": "cell-updates/s",
+                "value": whole_job_rate(ws, cells, K, msd), "unit": "cell-updates/s",
                 "what": "radiated power at 32 normalised frequencies 0.5 .. 3.5 (own DFT window each) and "
                         "bunch moments after every step, FP32-mixed",
                 "kernel_ms_per_step": {k: v[0] / K for k, v in statsd.items() if v[1]}}
@@ -383,8 +401,8 @@ def main():
         mss, statss, _, _, _, _ = timed_run(1, Ks, False, wsd, labs)
         mss = reduce_max(mss)
         cs = wsd.nx * wsd.ny * wsd.nz
-        seeded = {"workload": wsd.name, "value": ws * cs * Ks / (mss * 1e-3), "unit": "cell-updates/s",
-                  "particle_pushes_per_s": ws * wsd.n_particles * Ks / (mss * 1e-3), "ms_per_step": mss / Ks,
+        seeded = {"workload": wsd.name, "value": whole_job_rate(ws, cs, Ks, mss), "unit": "cell-updates/s",
+                  "particle_pushes_per_s": whole_job_rate(ws, wsd.n_particles, Ks, mss), "ms_per_step": mss / Ks,
                   "steps": Ks, "precision": "fp32-mixed",
                   "seed": "Gaussian beam, a0 9.857e-7 (10 kW) at 0.265187 um, waist 183.74 um, TF/SF planes",
                   "kernel_ms_per_step": {k: v[0] / Ks for k, v in statss.items() if v[1]}}
@@ -502,7 +520,7 @@ def main():
         served = serving_run(m, workloads, False, args.serving_requests, 4.0)
         served["fp64_path"] = serving_run(m, workloads, True, args.serving_requests, 4.0)
 
-    value = ws * cells * K / (ms32 * 1e-3)
+    value = whole_job_rate(ws, cells, K, ms32)
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -513,7 +531,7 @@ def main():
                    "l2": f"inputs larger than L2 (fields {22 * cells * 4 / 1e9:.2f} GB + particles "
                          f"{w.n_particles * 96 / 1e9:.2f} GB resident)",
                    "parallelism": f"{ws} independent replica(s)", "sort_every": 20},
-        "particle_pushes_per_s": ws * w.n_particles * K / (ms32 * 1e-3),
+        "particle_pushes_per_s": whole_job_rate(ws, w.n_particles, K, ms32),
         "kernel_ms_per_step": {k: v[0] / K for k, v in stats32.items() if v[1]},
         "kernel_ms_per_launch": {k: v[0] / v[1] for k, v in stats32.items() if v[1]},
         "kernel_times": f"CUDA events around each kernel over {K} further steps launched one by one "
@@ -528,7 +546,7 @@ def main():
         "emit_roofline": emit_roof,
         "cpu_baseline": cpu,
         "error_vs_oracle": err,
-        "e2e": {"value": ws * cells * K / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / K,
+        "e2e": {"value": whole_job_rate(ws, cells, K, t_e2e * 1e3), "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K, "what": "mithra_create from pinned host particles (H2D), "
                 f"{K} steps, power series + diagnostics to host (D2H)"},
         "served": served,
