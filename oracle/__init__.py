@@ -57,6 +57,7 @@ class Params(C.Structure):
         ("seed_type", C.c_int32), ("seed_a0", C.c_double), ("seed_lambda", C.c_double),
         ("seed_pol_deg", C.c_double), ("seed_waist", C.c_double), ("seed_focus", C.c_double),
         ("seed_offset", C.c_double), ("seed_pulse_fwhm", C.c_double), ("seed_cep_deg", C.c_double),
+        ("optimize_position", C.c_int32),
     ]
 
 
@@ -129,6 +130,7 @@ def params_from(w, periodic=(0, 0, 0)) -> Params:
     p.seed_type, p.seed_a0, p.seed_lambda, p.seed_pol_deg = w.seed_type, w.seed_a0, w.seed_lambda, w.seed_pol_deg
     p.seed_waist, p.seed_focus, p.seed_offset = w.seed_waist, w.seed_focus, w.seed_offset
     p.seed_pulse_fwhm, p.seed_cep_deg = w.seed_pulse_fwhm, w.seed_cep_deg
+    p.optimize_position = w.optimize
     return p
 
 

@@ -52,6 +52,7 @@ struct orc_run {
     double dx, dy, dz, dt, dtb, cdt, A;
     double x0, y0, z0;
     double T0, zeta_ref, z_ref;
+    double shift;   /* optimize-bunch-position: z shift of the mesh and the power plane */
     double q;
     double B0, ku, Lu;
     double E0, kL, zeta_f, t_f;
@@ -193,6 +194,22 @@ orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np)
     r->y0 = p->cy - 0.5 * (p->ny - 1) * r->dy;
     r->z0 = r->z_ref + g0 * p->cz - 0.5 * (p->nz - 1) * r->dz;
 
+    /* optimize-bunch-position (Sec. MESH): the bunch is to sit at its placed position once it
+       has passed the undulator entrance.  Before the entrance the reference particle (on axis,
+       Lorentz factor gamma) moves in the rest frame with v = (beta - beta0) / (1 - beta beta0)
+       (velocity addition); the entrance moves with -beta0 c and, at the reference's time T0,
+       lies g0 zeta_ref (beta0^2 - 1) = -zeta_ref / g0 ahead of it.  They meet after
+       t = (-zeta_ref / g0) / ((v + beta0) c), by which the reference has moved v c t: the mesh
+       and the power plane move by that distance. */
+    r->shift = 0.0;
+    if (p->optimize_position && (p->und_kind == 0 || p->und_kind == 1 || p->und_kind == 4)) {
+        const double beta = sqrt(1.0 - 1.0 / (p->gamma * p->gamma));
+        const double v = (beta - r->beta0) / (1.0 - beta * r->beta0);
+        const double t = (-r->zeta_ref / g0) / ((v + r->beta0) * C0);
+        r->shift = v * C0 * t;
+    }
+    r->z0 += r->shift;
+
     for (int l = 0; l < 3; ++l)
         for (int c = 0; c < 4; ++c) r->lev[l][c] = (double *)calloc((size_t)r->ncell, sizeof(double));
     for (int c = 0; c < 4; ++c) r->src[c] = (double *)calloc((size_t)r->ncell, sizeof(double));
@@ -214,7 +231,7 @@ orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np)
 
     /* power diagnostic */
     {
-        const double zp = r->z_ref + g0 * p->plane_dist;
+        const double zp = r->z_ref + r->shift + g0 * p->plane_dist;
         long kp = lround((zp - r->z0) / r->dz);
         if (kp < 1) kp = 1;
         if (kp > p->nz - 2) kp = p->nz - 2;

@@ -81,6 +81,10 @@ typedef struct orc_params {
     double seed_offset;       /* c t0: the pulse centre passes the reference point at lab time t0 */
     double seed_pulse_fwhm;   /* c tau (intensity FWHM); <= 0: continuous wave */
     double seed_cep_deg;      /* carrier envelope phase */
+    /* optimize-bunch-position (Sec. MESH): static undulators only; 1 shifts the mesh and the
+       power plane along z by the rest-frame drift of the bunch reference before the undulator
+       entrance reaches it, so that the bunch sits at its placed position inside the undulator */
+    int32_t optimize_position;
 } orc_params;
 
 typedef struct orc_run orc_run;

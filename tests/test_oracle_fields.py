@@ -7,8 +7,12 @@
 * CFL bound (Eq. CFLcondition) and the NSFD mesh adjustment;
 * Mur: exact 1D absorption at c dt = dz, the printed beta/gamma coefficients agree
   with the printed finite-difference discretisation, and the discrete reflection
-  coefficient follows the Engquist-Majda curves of first and second order.
+  coefficient follows the Engquist-Majda curves of first and second order;
+* Mur edges and corners (reading G19): the boundary value solves the first-order outgoing
+  conditions of the meeting faces, summed; a field that satisfies each of those conditions and
+  is quadratic in space and time is reproduced exactly at every edge and corner node.
 """
+import itertools
 import math
 
 import numpy as np
@@ -210,3 +214,57 @@ def test_mur_reflection_engquist_majda(deg):
         r1 = (1 - math.cos(th)) / (1 + math.cos(th))
         expect = r1 if order == 1 else r1 * r1
         assert abs(abs(R) - expect) < 0.03 * expect + 2e-5, (order, deg, abs(R), expect)
+
+
+@pytest.mark.parametrize("comp", [3, 0, 2])
+@pytest.mark.parametrize("corner", list(itertools.product((0, 1), repeat=3)))
+def test_mur_edges_and_corners_solve_the_summed_first_order_conditions(comp, corner):
+    """Reading G19: an edge (corner) node takes the value that satisfies the sum of the first-order
+    outgoing conditions d psi/d n_in - (1/c) d psi/dt = 0 of its two (three) faces, discretised
+    at the centre of the square (cube) it spans with its inward neighbours.  The field
+    psi = F(sum_s sigma_s x_s + c t), sigma_s = +1 at a low face and -1 at a high one, satisfies
+    the outgoing condition of each face that meets at the chosen corner of the box, hence their
+    sum; with F quadratic the centred differences are exact, so the boundary update of a level
+    ring filled with psi must return psi at t + dt at every edge and corner node next to that
+    corner (and at its face nodes, first order).  A wrong sign, a wrong count of the summed time
+    terms or a wrong averaging factor of the face differences breaks the equality."""
+    nx, ny, nz = 7, 8, 9
+    D = (1.1e-3, 1.3e-3, 0.9e-3)
+    w = vacuum(nx, ny, nz, *D, solver=1, courant=0.9, mur_order=1)
+    r = oracle.Run(oracle.params_from(w))
+    dt = r.info()["dt"]
+    stag = {0: (0.5, 0, 0), 1: (0, 0.5, 0), 2: (0, 0, 0.5), 3: (0, 0, 0)}[comp]
+    ext = [n - (1 if comp == a else 0) for a, n in enumerate((nx, ny, nz))]
+    z, y, x = np.meshgrid((np.arange(nz) + stag[2]) * D[2], (np.arange(ny) + stag[1]) * D[1],
+                          (np.arange(nx) + stag[0]) * D[0], indexing="ij")
+    sig = [1.0 if c == 0 else -1.0 for c in corner]
+    L = 1e-3
+
+    def F(t):
+        xi = (sig[0] * x + sig[1] * y + sig[2] * z + C0 * t) / L
+        return 0.3 + 0.7 * xi - 0.05 * xi * xi
+
+    for lev, t in ((0, -dt), (1, 0.0), (2, dt)):
+        r.set_field(comp, lev, F(t))
+    r.mur(comp)
+    got = r.field(comp, 2)
+    exp = F(dt)
+    checked = {1: 0, 2: 0, 3: 0}
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                ijk = (i, j, k)
+                if any(ijk[a] >= ext[a] for a in range(3)):
+                    continue
+                sides = []
+                for a in range(3):
+                    if ijk[a] == 0:
+                        sides.append((a, 0))
+                    elif ijk[a] == ext[a] - 1:
+                        sides.append((a, 1))
+                if not sides or any(corner[a] != sd for a, sd in sides):
+                    continue
+                assert abs(got[k, j, i] - exp[k, j, i]) <= 1e-12 * np.max(np.abs(exp)), (ijk, got[k, j, i], exp[k, j, i])
+                checked[len(sides)] += 1
+    # the corner, the three edges leaving it (their far ends are other corners) and the faces
+    assert checked[3] == 1 and checked[2] == sum(e - 2 for e in ext) and checked[1] > 0

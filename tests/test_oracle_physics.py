@@ -3,7 +3,9 @@
 * single electron in a planar undulator: transverse amplitude K/(gamma k_u), constant
   lab energy, zero mean rest-frame drift (the rest frame of Sec. "Lorentz Transformation");
 * on-axis spectrum: the rest-frame field at the sampling plane peaks at w* = gamma0 beta0 c k_u,
-  i.e. at the lab resonance lambda_u (1 + K^2/2) / (2 gamma^2) after the Doppler factor;
+  i.e. at the lab resonance lambda_u (1 + K^2/2) / (2 gamma^2) after the Doppler factor (helical:
+  1 + K^2); an optical undulator gives the inverse-Compton lambda_L (1 + a0^2/2) / (4 gamma^2);
+* optimize-bunch-position: the mesh shift equals the drift of the reference before it enters;
 * initial bunching factor of a bunch modulated at the resonance equals the modulation;
 * radiated-power diagnostic: cycle-averaged flux a^2/(2 mu0 c) of a plane wave, the Doppler
   factor gamma0^2 (1 + beta0)^2 to the lab, and coherent N^2 scaling;
@@ -22,10 +24,10 @@ import workloads
 from tests.helpers import C0, EPS0, MU0, QE, ME, vacuum
 
 
-def _single_electron(gamma=20.0, K=1.0, lu=0.03, steps=440, substeps=1):
+def _single_electron(gamma=20.0, K=1.0, lu=0.03, steps=440, substeps=1, optimize=0):
     base = workloads.WORKLOADS["undulator_24x24x96"]
     w = workloads.scaled(base, n_particles=1, charge_e=1.0, gamma=gamma, K=K, lambda_u=lu,
-                         space_charge=0, substeps=substeps)
+                         space_charge=0, substeps=substeps, optimize=optimize)
     lab = np.array([[0.0, 0.0, 0.0, 0.0, 0.0, math.sqrt(gamma * gamma - 1)]])
     r = oracle.Run(oracle.params_from(w), lab)
     traj = []
@@ -72,18 +74,46 @@ def test_single_electron_undulator_trajectory():
     assert abs(drift) < 5e-3, drift
 
 
-def test_on_axis_spectrum_peaks_at_resonance():
+def test_optimize_bunch_position_centres_the_reference_inside_the_undulator():
+    """optimize-bunch-position (Sec. MESH): the shift of the mesh is the rest-frame drift of the
+    reference particle before the undulator entrance reaches it.  The electron's own trajectory
+    (external field only) decides where it ends up: inside the undulator its period-averaged
+    rest-frame position must be the mesh centre, up to the part of the drift that the entrance
+    fringe takes away (the electron slows down over the fringe, not at the entrance).  Without
+    the option it sits the whole drift ahead of the centre."""
     gamma, K, lu = 20.0, 1.0, 0.03
-    base = workloads.WORKLOADS["undulator_24x24x96"]
-    w = workloads.scaled(base, n_particles=64, sig_x=1e-6, sig_y=1e-6, sig_z=1e-6, rel_espread=0.0,
-                         space_charge=0)
-    lab = workloads.lab_bunch(w)
-    r = oracle.Run(oracle.params_from(w), lab)
-    steps = 480
+    res = {}
+    for opt in (0, 1):
+        r, w, tr = _single_electron(gamma, K, lu, steps=320, optimize=opt)
+        inf = r.info()
+        g0, b0, dt, dz = inf["gamma0"], inf["beta0"], inf["dt"], inf["dz"]
+        n = np.arange(len(tr)) + 1
+        t = inf["T0"] + (n + 0.5) * dt
+        zeta = g0 * (tr[:, 2] + b0 * C0 * t)
+        inside = np.nonzero(zeta > 2 * lu)[0]
+        period = int(round(lu / g0 / (b0 * C0) / dt))
+        assert len(inside) > 3 * period
+        sel = inside[: (len(inside) // period) * period]
+        centre = inf["z0"] + 0.5 * (w.nz - 1) * dz
+        res[opt] = (np.mean(tr[sel, 2]) - centre) / dz, inf["z0"] / dz
+    off0, z00 = res[0]
+    off1, z01 = res[1]
+    shift = z01 - z00                      # cells the option moved the mesh
+    beta = math.sqrt(1 - 1 / gamma ** 2)
+    assert shift > 5.0
+    assert abs(off1) < 0.25 * shift, (off1, shift)
+    assert abs(off0 - shift) < 0.25 * shift, (off0, shift)
+    assert abs(off1 - (off0 - shift)) < 1e-6
+
+
+def _spectrum_peak(w, steps, skip):
+    """Rest-frame angular frequency of the largest peak of the on-axis E_x series (Hann window,
+    zero-padded FFT, parabolic interpolation of the peak bin) after `skip` steps."""
+    r = oracle.Run(oracle.params_from(w), workloads.lab_bunch(w))
     r.step(steps)
     inf = r.info()
     _, _, ex = r.series()
-    seg = ex[160:]
+    seg = ex[skip:]
     seg = (seg - seg.mean()) * np.hanning(len(seg))
     nfft = 1 << 15
     spec = np.abs(np.fft.rfft(seg, nfft))
@@ -91,13 +121,50 @@ def test_on_axis_spectrum_peaks_at_resonance():
     i = int(np.argmax(spec[1:])) + 1
     a, b, c = spec[i - 1], spec[i], spec[i + 1]
     di = 0.5 * (a - c) / (a - 2 * b + c)
-    om = 2 * math.pi * (f[i] + di * (f[1] - f[0]))
+    return 2 * math.pi * (f[i] + di * (f[1] - f[0])), inf
+
+
+@pytest.mark.parametrize("kind", ["planar", "helical"])
+def test_on_axis_spectrum_peaks_at_resonance(kind):
+    """A cold, point-like bunch of little charge (so that its own fields do not shift its
+    motion) in a 30-period static undulator radiates, in the rest frame, at w* = gamma0 beta0 c k_u;
+    after the Doppler factor gamma0 (1 + beta0) the lab wavelength is the textbook resonance
+    lambda_u (1 + K^2/2) / (2 gamma^2) (planar) or lambda_u (1 + K^2) / (2 gamma^2) (helical: two
+    planar undulators 90 degrees and a quarter period apart, reading G9), up to O(1/gamma^2)."""
+    gamma, K, lu = 20.0, 1.0, 0.03
+    base = workloads.WORKLOADS["undulator_24x24x96"]
+    w = workloads.scaled(base, und_kind=0 if kind == "planar" else 1, n_periods=30, n_particles=64,
+                         sig_x=1e-6, sig_y=1e-6, sig_z=1e-6, rel_espread=0.0, space_charge=0, charge_e=1e3)
+    om, inf = _spectrum_peak(w, 640, 160)
     g0, b0 = inf["gamma0"], inf["beta0"]
     ku = 2 * math.pi / lu
-    assert abs(om / (g0 * b0 * C0 * ku) - 1) < 0.03
+    assert abs(om / (g0 * b0 * C0 * ku) - 1) < 0.005
     lam_lab = 2 * math.pi * C0 / (om * g0 * (1 + b0))
-    lam_res = lu * (1 + K * K / 2) / (2 * gamma * gamma)
-    assert abs(lam_lab / lam_res - 1) < 0.03
+    lam_res = lu * (1 + (K * K / 2 if kind == "planar" else K * K)) / (2 * gamma * gamma)
+    assert abs(lam_lab / lam_res - 1) < 0.01
+
+
+def test_optical_undulator_spectrum_peaks_at_inverse_compton_resonance():
+    """Optical undulator (Sec. "Optical Undulator"): a counter-propagating plane wave of
+    wavelength lambda_L and strength a0 (flat-top, reached after a short rise).  In the rest frame
+    (gamma0 = gamma / sqrt(1 + a0^2/2)) the bunch radiates at w* = gamma0 (1 + beta0) c k_L, which
+    the Doppler factor turns into the inverse-Compton wavelength lambda_L (1 + a0^2/2) / (4 gamma^2)
+    in the lab.  The run is short: about 18 periods inside the wave, so the tolerance is 2 %."""
+    gamma, a0, lL = 20.0, 0.5, 1e-6
+    g0 = gamma / math.sqrt(1 + a0 * a0 / 2)
+    b0 = math.sqrt(1 - 1 / g0 ** 2)
+    dzl = lL / (g0 * (1 + b0)) / 24 / g0          # 24 cells per rest-frame radiation wavelength
+    dxy = 1.5 * g0 * dzl
+    base = workloads.WORKLOADS["undulator_24x24x96"]
+    w = workloads.scaled(base, und_kind=2, K=a0, lambda_u=lL, n_periods=0, signal=1, pulse_fwhm=2 * lL,
+                         dist_head=3 * lL, dx=dxy, dy=dxy, dz=dzl, gamma=gamma, n_particles=64,
+                         sig_x=1e-9, sig_y=1e-9, sig_z=1e-12, rel_espread=0.0, space_charge=0, charge_e=1e3,
+                         plane_dist=0.35 * 96 * dzl)
+    om, inf = _spectrum_peak(w, 640, 200)
+    g0, b0 = inf["gamma0"], inf["beta0"]
+    assert abs(om / (g0 * (1 + b0) * C0 * 2 * math.pi / lL) - 1) < 0.02
+    lam_lab = 2 * math.pi * C0 / (om * g0 * (1 + b0))
+    assert abs(lam_lab / (lL * (1 + a0 * a0 / 2) / (4 * gamma * gamma)) - 1) < 0.02
 
 
 @pytest.mark.parametrize("b", [0.02, 0.1])

@@ -96,6 +96,8 @@ class Workload:
     seed_pulse_fwhm: float = 0.0 # c tau; <= 0: continuous
     seed_cep_deg: float = 0.0
     uniform: int = 0     # longitudinal profile: 0 Gaussian (rms sig_z), 1 uniform over [-sig_z, sig_z]
+    optimize: int = 0    # optimize-bunch-position (Sec. MESH): mesh and power plane follow the bunch's
+                         # drift before the undulator entrance, so it sits at its placed position inside
 
 
 def lab_bunch(w: Workload, n: Optional[int] = None, seed: Optional[int] = None) -> np.ndarray:
@@ -174,7 +176,7 @@ WORKLOADS = {
         sig_ux=0.02, sig_uy=0.02,
         charge_e=100e-12 / 1.602176634e-19, n_particles=2_000_000,
         lambda_r=1.782e-6, shot_noise=1, quiet=1,
-        plane_dist=0.3 * 512 * 9.900980e-8, steps=2000, seed=1236, precision=1),
+        plane_dist=0.45 * 512 * 9.900980e-8, optimize=1, steps=2000, seed=1236, precision=1),
     # The FEL run through an undulator line: four 12-period modules two periods apart, the
     # undulator parameter tapered by -0.005 per module (Sec. UNDULATOR, static-undulator-array).
     "fel_array_128x128x512": _w(
@@ -186,7 +188,7 @@ WORKLOADS = {
         sig_ux=0.02, sig_uy=0.02,
         charge_e=100e-12 / 1.602176634e-19, n_particles=2_000_000,
         lambda_r=1.782e-6, shot_noise=1, quiet=1,
-        plane_dist=0.3 * 512 * 9.900980e-8, steps=2000, seed=1240, precision=1),
+        plane_dist=0.45 * 512 * 9.900980e-8, optimize=1, steps=2000, seed=1240, precision=1),
     # Seeded UV FEL (Example 2 job file): 2500 x 2500 x 165 um at 30 x 30 x 0.02 um, 4 194 304
     # particles of a uniform 150 um bunch (55 pC, gamma 391.36, 1e-4 energy spread), planar
     # undulator K = 1.95, 2.8 cm; a 10 kW Gaussian seed at 0.265187 um (a0 = 9.857e-7, waist
@@ -210,7 +212,7 @@ WORKLOADS = {
         sig_ux=0.02, sig_uy=0.02,
         charge_e=100e-12 / 1.602176634e-19, n_particles=32_000_000,
         bunching=0.01, lambda_r=2.5e-7, quiet=1,
-        plane_dist=0.3 * 1024 * 1.562539e-8, steps=4000, seed=1237, precision=1),
+        plane_dist=0.45 * 1024 * 1.562539e-8, optimize=1, steps=4000, seed=1237, precision=1),
     # Optical undulator (inverse Compton): 192x192x768, 4M particles, Gaussian laser.
     "ics_192x192x768": _w(
         name="ics_192x192x768", nx=192, ny=192, nz=768,
@@ -232,19 +234,23 @@ SERVING_GRIDS = ((32, 32, 128), (64, 64, 256), (96, 96, 384), (128, 128, 512))
 
 
 def serving_requests(n_requests: int = 64, rate_hz: float = 4.0, seed: int = 1238,
-                     steps_range=(500, 2000), np_range=(1e4, 1e6)):
+                     steps_range=(500, 2000), np_range=(1e4, 1e6), grids=SERVING_GRIDS):
     """The serving stream: Poisson arrivals, random grid, particles, undulator, precision.
 
     Returns a list of (arrival_time_s, Workload).  Mesh resolution is sized from the
     textbook lab resonance lambda_u (1 + K^2/2) / (2 gamma^2): 12 cells per lab
-    resonant wavelength along z, and a transverse cell of 1.5 rest-frame cells.
+    resonant wavelength along z, and a transverse cell of 1.5 rest-frame cells.  The bunch
+    (rms length 0.08 of the mesh, head at 0.24) sits at the mesh centre once inside the
+    undulator (optimize-bunch-position), and the power plane lies 0.38 of the mesh ahead of
+    the centre: ahead of the head and 0.12 of the mesh inside the boundary.  `grids` replaces
+    the four grid sizes (the draw picks one of them uniformly).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     out = []
     for r in range(n_requests):
         t += rng.exponential(1.0 / rate_hz)
-        nx, ny, nz = SERVING_GRIDS[int(rng.integers(0, len(SERVING_GRIDS)))]
+        nx, ny, nz = grids[int(rng.integers(0, len(SERVING_GRIDS)))  % len(grids)]
         npart = int(round(math.exp(rng.uniform(math.log(np_range[0]), math.log(np_range[1])))))
         npart = max(4, npart - npart % 4)
         gamma = float(rng.uniform(20.0, 150.0))
@@ -259,9 +265,9 @@ def serving_requests(n_requests: int = 64, rate_hz: float = 4.0, seed: int = 123
         w = _w(name=f"serve_{r}", nx=nx, ny=ny, nz=nz, dx=dxy, dy=dxy, dz=dz,
                und_kind=0, K=K, lambda_u=lu, n_periods=12, dist_head=2 * lu,
                gamma=gamma, rel_espread=1e-4, sig_x=0.15 * nx * dxy / 6.0,
-               sig_y=0.15 * ny * dxy / 6.0, sig_z=0.1 * nz * dz / 1.0,
+               sig_y=0.15 * ny * dxy / 6.0, sig_z=0.08 * nz * dz,
                sig_ux=0.0, sig_uy=0.0, charge_e=50e-12 / 1.602176634e-19,
-               n_particles=npart, plane_dist=0.3 * nz * dz, steps=steps,
+               n_particles=npart, plane_dist=0.38 * nz * dz, optimize=1, steps=steps,
                seed=seed * 1000 + r, precision=prec)
         out.append((t, w))
     return out
