@@ -72,6 +72,12 @@ typedef struct mithra_grid {
     int32_t nf_points;
     /* bunch sampling (Sec. BUNCH, bunch-sampling) every bunch_every steps; 0 = off */
     int32_t bunch_every;
+    /* optimize-bunch-position (Sec. MESH), static undulators (kinds 0, 1, 4) only, ignored
+       otherwise: 1 moves the mesh and the power plane along z by the rest-frame drift of the bunch
+       reference (on axis, Lorentz factor bunch.gamma, relative velocity
+       v = (beta - beta0) / (1 - beta beta0)) until the undulator entrance reaches it, so that the
+       bunch sits at the placed position inside the undulator; 0 keeps the mesh where it is placed */
+    int32_t optimize_position;
 } mithra_grid;
 
 /* Undulator (manual Sec. UNDULATOR, Sec. "Field Initialization"). */

@@ -38,7 +38,7 @@ class Grid(C.Structure):
                 ("space_charge", C.c_int32), ("precision", C.c_int32), ("substeps", C.c_int32),
                 ("power_plane_dist", C.c_double), ("norm_freq", C.c_double), ("sort_every", C.c_int32),
                 ("nf_min", C.c_double), ("nf_max", C.c_double), ("nf_points", C.c_int32),
-                ("bunch_every", C.c_int32)]
+                ("bunch_every", C.c_int32), ("optimize_position", C.c_int32)]
 
 
 class Undulator(C.Structure):
@@ -254,6 +254,7 @@ def grid_from(w, precision=None, sort_every=0) -> Grid:
     g.sort_every = int(sort_every)
     g.nf_min, g.nf_max, g.nf_points = w.nf_min, w.nf_max, w.nf_points
     g.bunch_every = w.bunch_every
+    g.optimize_position = w.optimize
     return g
 
 

@@ -1013,7 +1013,22 @@ int derive(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, cons
     d.y0 = gr.cy - 0.5 * (gr.ny - 1) * d.dy;
     d.z0 = d.z_ref + d.g0 * gr.cz - 0.5 * (gr.nz - 1) * d.dz;
 
-    const double zp = d.z_ref + d.g0 * gr.power_plane_dist;
+    // optimize-bunch-position (Sec. MESH): before the undulator entrance reaches it, the bunch
+    // reference (on axis, Lorentz factor gamma) drifts in the rest frame with the relative
+    // velocity v = (beta - beta0) / (1 - beta beta0); the entrance, -zeta_ref / gamma0 ahead of it
+    // at its time T0, closes in with -beta0 c.  The mesh and the power plane move by the drift
+    // v c t up to the meeting, t = (-zeta_ref / gamma0) / ((v + beta0) c), so that the bunch
+    // sits at its placed position once it is inside the undulator.
+    double shift = 0.0;
+    if (gr.optimize_position && stat) {
+        const double beta = std::sqrt(1.0 - 1.0 / (b.gamma * b.gamma));
+        const double v = (beta - d.b0) / (1.0 - beta * d.b0);
+        const double t = (-zeta_ref / d.g0) / ((v + d.b0) * kC);
+        shift = v * kC * t;
+    }
+    d.z0 += shift;
+
+    const double zp = d.z_ref + shift + d.g0 * gr.power_plane_dist;
     double kp = std::round((zp - d.z0) / d.dz);
     if (kp < 1) kp = 1;
     if (kp > gr.nz - 2) kp = gr.nz - 2;
@@ -1142,6 +1157,8 @@ int mithra::validate_request(const mithra_grid* gr, double dt_lab, const mithra_
                                (gr->nf_points == 1 || gr->nf_max >= gr->nf_min)))
         return fail(MITHRA_EINVAL, "create: spectrum needs 0 < nf_min <= nf_max");
     if (gr->bunch_every < 0) return fail(MITHRA_EINVAL, "create: bunch_every must be >= 0");
+    if (gr->optimize_position != 0 && gr->optimize_position != 1)
+        return fail(MITHRA_EINVAL, "create: optimize_position must be 0 or 1");
     if (u->kind < -1 || u->kind > 4) return fail(MITHRA_EINVAL, "create: unknown undulator kind");
     if (u->kind == 4) {
         if (!finite_all({u->gap, u->taper}) || !(u->gap >= 0.0))

@@ -4,8 +4,11 @@ same alone and in the mix.
 
 "Alone" is the same request run by itself (mithra_create + mithra_step); "in the mix" is the
 request served while others run concurrently.  Runs own their buffers, so the only difference is
-the order of floating-point atomic additions in the deposition: FP64 requests must agree to
-1e-9 relative, FP32-mixed requests to 1e-3 (the stated 1e-4 field-energy bound is also checked).
+the order of floating-point atomic additions in the deposition, which differs between any two
+runs, alone or not.  The bounds are the stated tolerances of each precision: FP64 requests agree
+to 1e-9 of the peak power and of the field energy; FP32-mixed requests to 1 % of the peak power
+and 1e-4 of the field energy, the stated FP32 bounds.  The FP32 run-to-run spread (the same
+request alone twice) is measured beside them and must meet the same bounds.
 """
 import time
 
@@ -22,13 +25,14 @@ import paper_2009_13645_gb300 as m  # noqa: E402
 import workloads  # noqa: E402
 
 
+SMALL_GRIDS = ((32, 32, 128), (64, 64, 192))
+TOL = {0: (1e-9, 1e-9, 1e-12), 1: (1e-2, 1e-4, 1e-6)}   # power (of the peak), field energy, bunching
+
+
 def _requests(n, steps=(60, 160), seed=11):
-    reqs = []
-    for _, w in workloads.serving_requests(n, rate_hz=100.0, seed=seed, steps_range=steps, np_range=(2e3, 3e4)):
-        # keep the small grids so the test stays short
-        w = workloads.scaled(w, nx=min(w.nx, 64), ny=min(w.ny, 64), nz=min(w.nz, 192))
-        reqs.append(w)
-    return reqs
+    # the small grids keep the test short
+    return [w for _, w in workloads.serving_requests(n, rate_hz=100.0, seed=seed, steps_range=steps,
+                                                     np_range=(2e3, 3e4), grids=SMALL_GRIDS)]
 
 
 def _alone(w):
@@ -68,11 +72,19 @@ def test_results_same_alone_and_in_the_mix():
             assert res.status == 0 and res.steps == w.steps
             p_mix, _ = m.result_series(t)
             p_alone, fe_alone, b_alone = _alone(w)
-            tol = 1e-9 if w.precision == 0 else 1e-3
+            tp, te, tb = TOL[w.precision]
             scale = max(np.max(np.abs(p_alone)), 1e-300)
-            assert np.max(np.abs(p_mix - p_alone)) <= tol * scale, (w.name, w.precision)
-            assert abs(res.field_energy - fe_alone) <= (1e-9 if w.precision == 0 else 1e-4) * fe_alone
-            assert abs(res.bunching - b_alone) <= (1e-12 if w.precision == 0 else 1e-6)
+            mix = (np.max(np.abs(p_mix - p_alone)) / scale, abs(res.field_energy - fe_alone) / fe_alone,
+                   abs(res.bunching - b_alone))
+            if w.precision == 1:
+                p_again, fe_again, b_again = _alone(w)
+                floor = (np.max(np.abs(p_again - p_alone)) / scale, abs(fe_again - fe_alone) / fe_alone,
+                         abs(b_again - b_alone))
+                print(f"{w.name} FP32 alone vs alone {floor}, alone vs mix {mix}")
+                assert floor[0] <= tp and floor[1] <= te and floor[2] <= tb, (w.name, floor)
+            assert mix[0] <= tp, (w.name, w.precision, mix)
+            assert mix[1] <= te, (w.name, w.precision, mix)
+            assert mix[2] <= tb, (w.name, w.precision, mix)
             m.release(t)
     finally:
         m.serve_stop()
@@ -98,7 +110,7 @@ def test_admission_by_footprint_serialises_when_only_one_fits():
         assert st["pool_peak"] <= int(need * 1.5)
         assert st["reserved"] == 0 and st["active"] == 0
         p = [m.result_series(x)[0] for x in t]
-        assert np.max(np.abs(p[1] - p[0])) <= 1e-3 * np.max(np.abs(p[0]))
+        assert np.max(np.abs(p[1] - p[0])) <= TOL[1][0] * np.max(np.abs(p[0]))
     finally:
         m.serve_stop()
 
