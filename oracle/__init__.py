@@ -35,9 +35,16 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            "-o", tmp, src, "-lm"]
-    subprocess.check_call(cmd)
+    # OpenMP runs the independent loops on all cores (same results); without it, one thread
+    if subprocess.call(cmd[:-1] + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL) != 0:
+        subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def threads() -> int:
+    """Threads the oracle's independent loops run on (OMP_NUM_THREADS, else all cores)."""
+    return int(_load().orc_threads())
 
 
 class Params(C.Structure):
@@ -74,6 +81,7 @@ def _load():
         if _lib is None:
             lib = C.CDLL(build())
             dp = C.POINTER(C.c_double)
+            lib.orc_threads.restype = C.c_int
             lib.orc_create.restype = C.c_void_p
             lib.orc_create.argtypes = [C.POINTER(Params), dp, C.c_int64]
             lib.orc_destroy.argtypes = [C.c_void_p]

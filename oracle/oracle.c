@@ -35,6 +35,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* CODATA 2018 */
 #define C0 299792458.0
@@ -301,6 +304,7 @@ void orc_stencil(orc_run *r, int c)
     double *out = r->lev[2][c];
     const int lo[3] = {per[0] ? 0 : 1, per[1] ? 0 : 1, per[2] ? 0 : 1};
     const int hi[3] = {per[0] ? e[0] : e[0] - 1, per[1] ? e[1] : e[1] - 1, per[2] ? e[2] : e[2] - 1};
+#pragma omp parallel for schedule(static)
     for (int k = lo[2]; k < hi[2]; ++k) {
         const int km = wrap(k - 1, e[2]), kq = wrap(k + 1, e[2]);
         for (int j = lo[1]; j < hi[1]; ++j) {
@@ -577,6 +581,7 @@ static void emit_eb(orc_run *r)
     const double dt = r->dt, dx = r->dx, dy = r->dy, dz = r->dz;
     const int sc = r->p.space_charge;
     for (int c = 0; c < 6; ++c) memset(r->eb[c], 0, (size_t)r->ncell * sizeof(double));
+#pragma omp parallel for schedule(static)
     for (int k = lo[2]; k < hi[2]; ++k) {
         const int km = wrap(k - 1, n[2]), kq = wrap(k + 1, n[2]);
         for (int j = lo[1]; j < hi[1]; ++j) {
@@ -923,44 +928,75 @@ void orc_deposit_moves(orc_run *r, const double *old6, const double *new6, int64
     }
 }
 
+/* One particle's field step (external field, gather, Boris, move) for every sub-step, without
+   depositing: the sub-step's end points in cell units go to X (N + 1 points), whether the
+   sub-step's move is deposited to dep (both ends active) and whether the final charge is to
+   rest_ok.  The particle's position and momentum are updated in place. */
+static void push_particle(const orc_run *r, double *s, int N, double *X, char *dep, char *rho_ok)
+{
+    double pos[3] = {s[0], s[1], s[2]}, u[3] = {s[3], s[4], s[5]};
+    cellpos(r, pos, X);
+    for (int m = 0; m < N; ++m) {
+        const double t = r->T0 + ((double)r->step + 0.5) * r->dt + m * r->dtb;
+        double E[3], B[3], Es[3] = {0, 0, 0}, Bs[3] = {0, 0, 0};
+        const double *X1 = X + 3 * m;
+        double *X2 = X + 3 * (m + 1);
+        orc_external_field(r, r->x0 + pos[0], r->y0 + pos[1], r->z0 + pos[2], t, E, B);
+        const int a1 = active(r, X1);
+        if (a1) gather(r, X1, Es, Bs);
+        for (int l = 0; l < 3; ++l) {
+            E[l] += Es[l];
+            B[l] += Bs[l];
+        }
+        orc_boris(u, E, B, r->dtb);
+        const double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        double np_[3];
+        for (int l = 0; l < 3; ++l) np_[l] = pos[l] + C0 * r->dtb * u[l] / g;
+        cellpos(r, np_, X2);
+        dep[m] = (char)(a1 && active(r, X2));
+        for (int l = 0; l < 3; ++l) pos[l] = np_[l];
+    }
+    *rho_ok = (char)(r->p.space_charge && active(r, X + 3 * N));
+    s[0] = pos[0];
+    s[1] = pos[1];
+    s[2] = pos[2];
+    s[3] = u[0];
+    s[4] = u[1];
+    s[5] = u[2];
+}
+
+/* Push every particle (independent of one another: several threads may share the loop), then
+   deposit in particle order and, per particle, in sub-step order, as one serial loop would. */
 static void push_deposit(orc_run *r)
 {
     const int N = r->p.substeps > 0 ? r->p.substeps : 1;
     for (int c = 0; c < 4; ++c) memset(r->src[c], 0, (size_t)r->ncell * sizeof(double));
-    for (int64_t p = 0; p < r->np; ++p) {
-        double *s = r->pr + 6 * p;
-        double pos[3] = {s[0], s[1], s[2]}, u[3] = {s[3], s[4], s[5]};
-        for (int m = 0; m < N; ++m) {
-            const double t = r->T0 + ((double)r->step + 0.5) * r->dt + m * r->dtb;
-            double E[3], B[3], Es[3] = {0, 0, 0}, Bs[3] = {0, 0, 0}, X1[3], X2[3];
-            orc_external_field(r, r->x0 + pos[0], r->y0 + pos[1], r->z0 + pos[2], t, E, B);
-            cellpos(r, pos, X1);
-            const int a1 = active(r, X1);
-            if (a1) gather(r, X1, Es, Bs);
-            for (int l = 0; l < 3; ++l) {
-                E[l] += Es[l];
-                B[l] += Bs[l];
-            }
-            orc_boris(u, E, B, r->dtb);
-            const double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            double np_[3];
-            for (int l = 0; l < 3; ++l) np_[l] = pos[l] + C0 * r->dtb * u[l] / g;
-            cellpos(r, np_, X2);
-            if (a1 && active(r, X2)) deposit_move(r, X1, X2);
-            for (int l = 0; l < 3; ++l) pos[l] = np_[l];
+    const int64_t chunk = 65536;
+    double *X = (double *)malloc((size_t)chunk * 3 * (N + 1) * sizeof(double));
+    char *dep = (char *)malloc((size_t)chunk * (N + 1));
+    for (int64_t p0 = 0; p0 < r->np; p0 += chunk) {
+        const int64_t n = r->np - p0 < chunk ? r->np - p0 : chunk;
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < n; ++q)
+            push_particle(r, r->pr + 6 * (p0 + q), N, X + q * 3 * (N + 1), dep + q * (N + 1), dep + q * (N + 1) + N);
+        for (int64_t q = 0; q < n; ++q) {
+            const double *Xq = X + q * 3 * (N + 1);
+            for (int m = 0; m < N; ++m)
+                if (dep[q * (N + 1) + m]) deposit_move(r, Xq + 3 * m, Xq + 3 * (m + 1));
+            if (dep[q * (N + 1) + N]) deposit_rho(r, Xq + 3 * N);
         }
-        if (r->p.space_charge) {
-            double X[3];
-            cellpos(r, pos, X);
-            if (active(r, X)) deposit_rho(r, X);
-        }
-        s[0] = pos[0];
-        s[1] = pos[1];
-        s[2] = pos[2];
-        s[3] = u[0];
-        s[4] = u[1];
-        s[5] = u[2];
     }
+    free(X);
+    free(dep);
+}
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------- */

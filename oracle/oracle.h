@@ -8,8 +8,11 @@
  * CUDA library; both receive the same lab-frame particle arrays from the
  * seeded input generator and nothing else.
  *
- * The oracle is plain, serial and unblocked: every function follows one
- * equation of the manual in its own order and notation.
+ * The oracle is plain and unblocked: every function follows one equation of the
+ * manual in its own order and notation.  Loops whose iterations are independent of
+ * one another (the stencil, the E/B evaluation, the per-particle push) may run on
+ * several threads (OpenMP); every accumulation runs serially in a fixed order, so the
+ * results are the same for any thread count.
  *
  * Parity pins (tests/test_oracle_*.py) tie it to what the paper and the
  * mathematics fix: the discrete dispersion relations (Eqs. numericalDispersionCD,
@@ -88,6 +91,12 @@ typedef struct orc_params {
 } orc_params;
 
 typedef struct orc_run orc_run;
+
+/* Threads the oracle's independent loops use (OpenMP; 1 when built without it).  The stencil,
+   the E/B evaluation and the per-particle push run their iterations on several threads; every
+   sum whose order matters (the deposition, the diagnostics) stays serial, so results do not
+   depend on the thread count. */
+int orc_threads(void);
 
 /* Create a run from lab-frame particles lab6 (np x 6: x, y, z, ux, uy, uz; copied). */
 orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np);
