@@ -134,9 +134,10 @@ __device__ __forceinline__ float gap_window32(float kd, float pwin)
 // factors outside [0, L_u] (with an array's gap windows) and cosh/sinh of k_u y are evaluated in
 // FP32, the precision of the self-field they are added to.  Returns false for a particle of an
 // array whose step reaches past the gap that follows the plane's module (a few node planes in
-// front of each module entrance): it takes the general FP64 evaluation.
-__device__ __forceinline__ bool static_field_mixed(const ExtField& f, const PushConst& pc, int iz, float fz, int m,
-                                                   float x, float y, float E[3], float B[3])
+// front of each module entrance), and for a particle outside the mesh's z range in an array: it
+// takes the general FP64 evaluation.
+__device__ __forceinline__ bool static_field_mixed(const ExtField& f, const PushConst& pc, int iz, bool inside,
+                                                   double Z0, float fz, int m, float x, float y, float E[3], float B[3])
 {
     E[0] = E[1] = E[2] = 0.f;
     B[0] = B[1] = B[2] = 0.f;
@@ -144,8 +145,20 @@ __device__ __forceinline__ bool static_field_mixed(const ExtField& f, const Push
     const float th = fmaf(pc.kdz, fz, pc.kzs * (float)m);   // phase beyond the node plane
     for (int j = 0; j < nplanar; ++j) {
         const float c = j ? -pc.spolf : pc.cpolf, s = j ? pc.cpolf : pc.spolf;
-        const float4 t0 = __ldg(pc.ptab32[j] + 2 * iz);       // eB0 sin, eB0 cos, bB0 sin, bB0 cos
-        const float4 t1 = __ldg(pc.ptab32[j] + 2 * iz + 1);   // B0 sin, B0 cos, k_u u, k_u (u - L_u)
+        float4 t0, t1;   // eB0 sin, eB0 cos, bB0 sin, bB0 cos; B0 sin, B0 cos, k_u u, k_u (u - L_u)
+        if (inside) {
+            t0 = __ldg(pc.ptab32[j] + 2 * iz);
+            t1 = __ldg(pc.ptab32[j] + 2 * iz + 1);
+        } else {
+            // a plane outside the mesh (planar and helical fields): the table's entries formed
+            // here, the phase in FP64 and reduced to [-pi, pi] in FP64, its sine and cosine in FP32
+            const double ph = f.ku * (fma(pc.kz, (double)iz, Z0) - (j ? f.qlam : 0.0));
+            const double n = rint(ph * (0.5 / kPi));
+            float sn, cs;
+            sincosf((float)fma(-n, 2.0 * kPi, ph), &sn, &cs);
+            t0 = make_float4(pc.eB0f * sn, pc.eB0f * cs, pc.bB0f * sn, pc.bB0f * cs);
+            t1 = make_float4(pc.B0f * sn, pc.B0f * cs, (float)ph, (float)(ph - f.ku * f.Lu));
+        }
         const float ua = t1.z + th, ub = t1.w + th;
         float eS, bS, zC;   // eB0 sin, bB0 sin, B0 cos of the particle's phase
         if (ua >= 0.f && ub <= 0.f) {
@@ -460,10 +473,11 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
     float Ef[3], Bf[3];   // external field rounded to FP32 (FP32-mixed path)
     bool tab = false;
     if constexpr (std::is_same<real, float>::value) {
-        if (pc.ptab32[0] && ci[2] >= 0 && ci[2] < g.nz) {
+        const bool inside = ci[2] >= 0 && ci[2] < g.nz;
+        if (pc.ptab32[0] && (inside || ef.kind != 4)) {
             const float x = fmaf((float)ci[0] + f[0], pc.dxf, pc.x0f);
             const float y = fmaf((float)ci[1] + f[1], pc.dyf, pc.y0f);
-            tab = static_field_mixed(ef, pc, ci[2], f[2], m, x, y, Ef, Bf);
+            tab = static_field_mixed(ef, pc, ci[2], inside, Z0, f[2], m, x, y, Ef, Bf);
         }
     } else {
         if (pc.ptab[0] && ci[2] >= 0 && ci[2] < g.nz) {
