@@ -47,6 +47,11 @@ def threads() -> int:
     return int(_load().orc_threads())
 
 
+def set_threads(n: int) -> None:
+    """Run later steps on n threads (results do not depend on it)."""
+    _load().orc_set_threads(int(n))
+
+
 class Params(C.Structure):
     _fields_ = [
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
@@ -82,6 +87,7 @@ def _load():
             lib = C.CDLL(build())
             dp = C.POINTER(C.c_double)
             lib.orc_threads.restype = C.c_int
+            lib.orc_set_threads.argtypes = [C.c_int]
             lib.orc_create.restype = C.c_void_p
             lib.orc_create.argtypes = [C.POINTER(Params), dp, C.c_int64]
             lib.orc_destroy.argtypes = [C.c_void_p]

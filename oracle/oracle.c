@@ -840,8 +840,9 @@ static void gather(const orc_run *r, const double X[3], double E[3], double B[3]
     }
 }
 
-/* Straight piece a -> b (cell units) inside cell `cell`. */
-static void deposit_piece(orc_run *r, const double a[3], const double b[3], const int cell[3])
+/* Straight piece a -> b (cell units) inside cell `cell`.  Only nodes of the z planes
+   klo <= k < khi are written (a thread of the deposition owns those planes). */
+static void deposit_piece(orc_run *r, const double a[3], const double b[3], const int cell[3], int klo, int khi)
 {
     const double D[3] = {r->dx, r->dy, r->dz};
     double la[3], lb[3], mid[3], d[3];
@@ -865,12 +866,12 @@ static void deposit_piece(orc_run *r, const double a[3], const double b[3], cons
                 int idx[3] = {cell[0], cell[1], cell[2]};
                 idx[m] += Jm;
                 idx[n] += Jn;
-                r->src[l][IDX(r, idx[0], idx[1], idx[2])] += F * W;
+                if (idx[2] >= klo && idx[2] < khi) r->src[l][IDX(r, idx[0], idx[1], idx[2])] += F * W;
             }
     }
 }
 
-static void zigzag(orc_run *r, const double A[3], const double Bp[3])
+static void zigzag(orc_run *r, const double A[3], const double Bp[3], int klo, int khi)
 {
     int c1[3], c2[3];
     double R[3];
@@ -882,11 +883,11 @@ static void zigzag(orc_run *r, const double A[3], const double Bp[3])
         const double mid = 0.5 * (A[l] + Bp[l]);
         R[l] = fmin(lo + 1.0, fmax(hi, mid));
     }
-    deposit_piece(r, A, R, c1);
-    deposit_piece(r, R, Bp, c2);
+    deposit_piece(r, A, R, c1, klo, khi);
+    deposit_piece(r, R, Bp, c2, klo, khi);
 }
 
-static void deposit_move(orc_run *r, const double X1[3], const double X2[3])
+static void deposit_move(orc_run *r, const double X1[3], const double X2[3], int klo, int khi)
 {
     double m = 0.0;
     for (int l = 0; l < 3; ++l) m = fmax(m, fabs(X2[l] - X1[l]));
@@ -897,11 +898,11 @@ static void deposit_move(orc_run *r, const double X1[3], const double X2[3])
             A[l] = (s == 0) ? X1[l] : X1[l] + (X2[l] - X1[l]) * ((double)s / ns);
             B[l] = (s == ns - 1) ? X2[l] : X1[l] + (X2[l] - X1[l]) * ((double)(s + 1) / ns);
         }
-        zigzag(r, A, B);
+        zigzag(r, A, B, klo, khi);
     }
 }
 
-static void deposit_rho(orc_run *r, const double X[3])
+static void deposit_rho(orc_run *r, const double X[3], int klo, int khi)
 {
     const int i = (int)floor(X[0]), j = (int)floor(X[1]), k = (int)floor(X[2]);
     const double f[3] = {X[0] - i, X[1] - j, X[2] - k};
@@ -910,7 +911,7 @@ static void deposit_rho(orc_run *r, const double X[3])
         for (int J = 0; J < 2; ++J)
             for (int I = 0; I < 2; ++I) {
                 const double w = (I ? f[0] : 1.0 - f[0]) * (J ? f[1] : 1.0 - f[1]) * (K ? f[2] : 1.0 - f[2]);
-                r->src[3][IDX(r, i + I, j + J, k + K)] += rho * w;
+                if (k + K >= klo && k + K < khi) r->src[3][IDX(r, i + I, j + J, k + K)] += rho * w;
             }
 }
 
@@ -923,8 +924,8 @@ void orc_deposit_moves(orc_run *r, const double *old6, const double *new6, int64
         const double b[3] = {new6[6 * p] - r->x0, new6[6 * p + 1] - r->y0, new6[6 * p + 2] - r->z0};
         cellpos(r, a, X1);
         cellpos(r, b, X2);
-        if (active(r, X1) && active(r, X2)) deposit_move(r, X1, X2);
-        if (active(r, X2)) deposit_rho(r, X2);
+        if (active(r, X1) && active(r, X2)) deposit_move(r, X1, X2, 0, r->nz);
+        if (active(r, X2)) deposit_rho(r, X2, 0, r->nz);
     }
 }
 
@@ -979,11 +980,27 @@ static void push_deposit(orc_run *r)
 #pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; ++q)
             push_particle(r, r->pr + 6 * (p0 + q), N, X + q * 3 * (N + 1), dep + q * (N + 1), dep + q * (N + 1) + N);
-        for (int64_t q = 0; q < n; ++q) {
-            const double *Xq = X + q * 3 * (N + 1);
-            for (int m = 0; m < N; ++m)
-                if (dep[q * (N + 1) + m]) deposit_move(r, Xq + 3 * m, Xq + 3 * (m + 1));
-            if (dep[q * (N + 1) + N]) deposit_rho(r, Xq + 3 * N);
+        /* each thread adds to its own z planes only, visiting the particles in order: every
+           node receives its terms in the order of one serial loop */
+#pragma omp parallel
+        {
+            int klo = 0, khi = r->nz;
+#ifdef _OPENMP
+            const int nt = omp_get_num_threads(), t = omp_get_thread_num();
+            klo = (int)((int64_t)r->nz * t / nt);
+            khi = (int)((int64_t)r->nz * (t + 1) / nt);
+#endif
+            for (int64_t q = 0; q < n; ++q) {
+                const double *Xq = X + q * 3 * (N + 1);
+                for (int m = 0; m < N; ++m) {
+                    if (!dep[q * (N + 1) + m]) continue;
+                    /* a move from z1 to z2 writes the node planes floor(min) .. floor(max) + 1 */
+                    const double z1 = Xq[3 * m + 2], z2 = Xq[3 * (m + 1) + 2];
+                    if (floor(fmax(z1, z2)) + 1.0 < (double)klo || floor(fmin(z1, z2)) >= (double)khi) continue;
+                    deposit_move(r, Xq + 3 * m, Xq + 3 * (m + 1), klo, khi);
+                }
+                if (dep[q * (N + 1) + N]) deposit_rho(r, Xq + 3 * N, klo, khi);
+            }
         }
     }
     free(X);
@@ -996,6 +1013,15 @@ int orc_threads(void)
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }
 

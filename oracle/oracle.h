@@ -97,6 +97,8 @@ typedef struct orc_run orc_run;
    sum whose order matters (the deposition, the diagnostics) stays serial, so results do not
    depend on the thread count. */
 int orc_threads(void);
+/* Use n threads for the later steps (n >= 1; no effect without OpenMP). */
+void orc_set_threads(int n);
 
 /* Create a run from lab-frame particles lab6 (np x 6: x, y, z, ux, uy, uz; copied). */
 orc_run *orc_create(const orc_params *p, const double *lab6, int64_t np);
