@@ -103,14 +103,33 @@ typedef struct mithra_undulator {
     double taper;
 } mithra_undulator;
 
-/* Bunch given as macro-particles (bunch type "file", Sec. BUNCH). */
+/* The bunch (Sec. BUNCH): either macro-particles the caller gives (bunch type "file"), or, when
+   lab_particles is NULL, an ellipsoid bunch generated on the device from the parameters below
+   (bunch-initialization of type ellipsoid; Sec. "Electron Bunch Generation"), loaded
+   quasi-randomly as mithra_ellipsoid_bunch does with
+   sig = {sig_x, sig_y, sig_z}, sig_u = {eps_n_x / sig_x, eps_n_y / sig_y, gamma rel_espread}
+   (a beam at its waist: the rms normalised momentum is the normalised emittance over the rms size;
+   the rms energy spread sets the rms of gamma*beta_z) and the Halton index of particle p shifted by
+   `seed` (index p + 1 + seed). */
 typedef struct mithra_bunch {
     int64_t n;                 /* number of macro-particles (>= 0) */
     double charge_e;           /* bunch charge in electrons (> 0 when n > 0) */
     double gamma;              /* mean Lorentz factor; with the undulator it fixes the rest frame */
-    double sig_z;              /* lab rms length; the bunch head is taken 3 sig_z ahead of the reference point */
+    double sig_z;              /* lab rms length (uniform profile: half length); the bunch head is taken
+                                  3 sig_z ahead of the reference point */
     const double *lab_particles; /* host, n x 6 row-major: x, y, z (m, relative to the bunch reference point),
-                                    gamma*beta_x, gamma*beta_y, gamma*beta_z; lab frame at t' = 0 */
+                                    gamma*beta_x, gamma*beta_y, gamma*beta_z; lab frame at t' = 0.
+                                    NULL: generate the bunch from the fields below */
+    int32_t uniform;           /* generated: 0 Gaussian current profile, 1 uniform over [-sig_z, sig_z] */
+    double rel_espread;        /* generated: rms relative energy spread (>= 0) */
+    double sig_x, sig_y;       /* generated: rms transverse size (>= 0) */
+    double eps_n_x, eps_n_y;   /* generated: normalised emittance (>= 0; 0 when the size is 0) */
+    double cse_sigma;          /* generated, uniform profile: rms of the Gaussian edges (<= 0: none) */
+    double lambda_r;           /* generated: lab wavelength of the bunching and of the shot-noise slices;
+                                  <= 0: the run's resonance seen in the lab, 2 pi / (k* gamma0 (1 + beta0)) */
+    double bunching, bunching_phase; /* generated: bunching factor at lambda_r and its phase (rad) */
+    int32_t shot_noise;        /* generated: 1 adds the shot noise of charge_e electrons per slice lambda_r */
+    uint64_t seed;             /* generated: Halton index offset (n + seed < 2^32) */
 } mithra_bunch;
 
 /* Seed injected through total-field / scattered-field planes (Sec. "Seed Field"; Sec. FIELD,
@@ -340,8 +359,10 @@ int mithra_serve_stop(void);
    Scratch: one FP64 partial per 4096 nodes in a fixed 256 KiB array inside the library's device
    memory, present on every GPU that loads the library until the process exits; hence n may not
    exceed MITHRA_NOALLOC_MAX_NODES (EINVAL otherwise).  The first call on a device looks up that
-   array's device address with the device current (cudaGetSymbolAddress); make that first call
-   before any stream capture.  All calls share the array: calls whose work overlaps on the GPU
+   array's device address with the device current (cudaGetSymbolAddress) and keeps it for the
+   process; make that first call before any stream capture.  A cudaDeviceReset destroys the array
+   with the context: do not call this entry point on that device after a reset (every run handle
+   and device buffer of the device is gone as well).  All calls share the array: calls whose work overlaps on the GPU
    race, so order them on one stream.  Each call writes every partial it reads; nothing needs
    clearing between calls.  Errors: EINVAL, ECUDA. */
 #define MITHRA_NOALLOC_MAX_NODES (134217728LL)

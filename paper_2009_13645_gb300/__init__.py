@@ -63,7 +63,11 @@ class Seed(C.Structure):
 
 class Bunch(C.Structure):
     _fields_ = [("n", C.c_int64), ("charge_e", C.c_double), ("gamma", C.c_double),
-                ("sig_z", C.c_double), ("lab_particles", C.POINTER(C.c_double))]
+                ("sig_z", C.c_double), ("lab_particles", C.POINTER(C.c_double)),
+                ("uniform", C.c_int32), ("rel_espread", C.c_double), ("sig_x", C.c_double),
+                ("sig_y", C.c_double), ("eps_n_x", C.c_double), ("eps_n_y", C.c_double),
+                ("cse_sigma", C.c_double), ("lambda_r", C.c_double), ("bunching", C.c_double),
+                ("bunching_phase", C.c_double), ("shot_noise", C.c_int32), ("seed", C.c_uint64)]
 
 
 _lib = None

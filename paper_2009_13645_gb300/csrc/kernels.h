@@ -3,12 +3,19 @@
 
 #include <cuda.h>
 
+#include "../../include/mithra.h"
 #include "common.cuh"
 
 namespace mithra {
 
 // Number of kernels launched by this library since it was loaded (all runs, all threads).
 void count_launches(int64_t n);
+
+// Quasi-random ellipsoid bunch (lab frame, n x 6) written to device memory d_out on stream st;
+// particle p takes the Halton numbers of index p + 1 + j0.  Scratch for the shot noise comes from
+// alloc / free_fn (ctx).  Returns a MITHRA status.
+int ellipsoid_device(const mithra_ellipsoid& e, int64_t n, uint64_t j0, double* d_out, void* (*alloc)(void*, size_t),
+                     void (*free_fn)(void*, void*), void* ctx, cudaStream_t st);
 // Record `msg` as the calling thread's last error (read by mithra_last_error) and return `code`.
 int set_last_error(int code, const char* msg);
 

@@ -38,17 +38,18 @@ struct EllArgs {
     mithra_ellipsoid e;
     int64_t n, nu;     // particles, of which nu fill the flat part of a uniform profile
     double uz0;        // sqrt(gamma^2 - 1)
+    unsigned j0;       // Halton index offset
 };
 
 // Bases (the manual leaves the assignment open): 2,3 transverse positions (Eq. gaussian2D), 5,7
 // transverse momenta, 11 (13) the longitudinal position (Eq. uniform1D / gaussian1D), 17,19 the
-// longitudinal momentum spread; particle p at index p + 1.
+// longitudinal momentum spread; particle p at index p + 1 + j0.
 __global__ void k_ellipsoid(EllArgs a, double* __restrict__ out)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n) return;
     const mithra_ellipsoid& e = a.e;
-    const unsigned j = (unsigned)(p + 1);
+    const unsigned j = (unsigned)(p + 1) + a.j0;
     double* q = out + 6 * p;
     const double r1 = sqrt(-2.0 * log(halton(0, j))), a1 = 2.0 * kPi * halton(1, j);
     q[0] = e.sig[0] * r1 * cos(a1);
@@ -64,7 +65,7 @@ __global__ void k_ellipsoid(EllArgs a, double* __restrict__ out)
     } else {
         // Gaussian edges of the same peak line density: lower half to the tail, upper half to
         // the head of the flat part
-        const unsigned je = (unsigned)(p - a.nu + 1);
+        const unsigned je = (unsigned)(p - a.nu + 1) + a.j0;
         const double ze = e.cse_sigma * sqrt(-2.0 * log(halton(4, je))) * cos(2.0 * kPi * halton(5, je));
         z = ze < 0.0 ? -e.sig[2] + ze : e.sig[2] + ze;
     }
@@ -115,58 +116,40 @@ __global__ void k_shot_noise(double* __restrict__ out, int64_t n, double lam, lo
 
 using mithra::set_last_error;
 
-extern "C" int mithra_ellipsoid_bunch(const mithra_ellipsoid* e, int64_t n, double* out6, void* stream)
+int mithra::ellipsoid_device(const mithra_ellipsoid& ell, int64_t n, uint64_t j0, double* d, void* (*alloc)(void*, size_t),
+                             void (*free_fn)(void*, void*), void* ctx, cudaStream_t st)
 {
     using namespace mithra;
-    if (!e || (n > 0 && !out6)) return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: null argument");
-    if (n < 0 || n >= ((int64_t)1 << 32) - 1) return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: n out of range");
+    const mithra_ellipsoid* e = &ell;
     for (double v : {e->gamma, e->sig[0], e->sig[1], e->sig[2], e->sig_u[0], e->sig_u[1], e->sig_u[2], e->cse_sigma,
                      e->lambda_r, e->bunching, e->bunching_phase, e->charge_e})
         if (!std::isfinite(v)) return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: non-finite value");
     if (!(e->gamma >= 1.0)) return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: gamma must be >= 1");
     if (e->shot_noise && !(e->lambda_r > 0.0 && e->charge_e > 0.0))
         return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: shot noise needs lambda_r > 0 and charge_e > 0");
+    if (n < 0 || (uint64_t)n + j0 >= ((uint64_t)1 << 32) - 1)
+        return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: n + seed out of range");
     if (n == 0) return MITHRA_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    mithra_alloc_fn af;
-    mithra_free_fn ff;
-    void* ctx;
-    get_allocator(&af, &ff, &ctx);
-    auto dalloc = [&](size_t b) -> void* {
-        void* p = nullptr;
-        if (af) return af(ctx, b);
-        if (cudaMalloc(&p, b) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        return p;
-    };
-    auto dfree = [&](void* p) {
-        if (!p) return;
-        if (ff) ff(ctx, p);
-        else cudaFree(p);
-    };
     EllArgs a;
     a.e = *e;
     a.n = n;
     a.nu = n;
+    a.j0 = (unsigned)j0;
     const double L = 2.0 * e->sig[2];
     if (e->uniform && e->cse_sigma > 0.0) a.nu = (int64_t)std::llround((double)n * L / (L + std::sqrt(2.0 * kPi) * e->cse_sigma));
     a.uz0 = std::sqrt(e->gamma * e->gamma - 1.0);
-    double* d = (double*)dalloc((size_t)n * 6 * sizeof(double));
-    long long* mm = (long long*)dalloc(2 * sizeof(long long));
-    if (!d || !mm) {
-        dfree(d);
-        dfree(mm);
-        return set_last_error(MITHRA_ENOMEM, "ellipsoid_bunch: device allocation failed");
-    }
     int rc = MITHRA_OK;
+    long long* mm = nullptr;
     unsigned* cnt = nullptr;
     const unsigned nb = (unsigned)((n + 255) / 256);
     do {
         k_ellipsoid<<<nb, 256, 0, st>>>(a, d);
         count_launches(1);
         if (e->shot_noise) {
+            if (!(mm = (long long*)alloc(ctx, 2 * sizeof(long long)))) {
+                rc = set_last_error(MITHRA_ENOMEM, "ellipsoid_bunch: device allocation failed");
+                break;
+            }
             const long long init[2] = {LLONG_MAX, LLONG_MIN};
             if (cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, st) != cudaSuccess) break;
             k_slice_range<<<nb, 256, 0, st>>>(d, n, e->lambda_r, mm);
@@ -179,7 +162,7 @@ extern "C" int mithra_ellipsoid_bunch(const mithra_ellipsoid* e, int64_t n, doub
                 rc = set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: too many shot-noise slices");
                 break;
             }
-            if (!(cnt = (unsigned*)dalloc((size_t)ns * sizeof(unsigned)))) {
+            if (!(cnt = (unsigned*)alloc(ctx, (size_t)ns * sizeof(unsigned)))) {
                 rc = set_last_error(MITHRA_ENOMEM, "ellipsoid_bunch: device allocation failed");
                 break;
             }
@@ -188,14 +171,61 @@ extern "C" int mithra_ellipsoid_bunch(const mithra_ellipsoid* e, int64_t n, doub
             k_shot_noise<<<nb, 256, 0, st>>>(d, n, e->lambda_r, h[0], e->charge_e, cnt);
             count_launches(3);
         }
-        if (cudaMemcpyAsync(out6, d, (size_t)n * 6 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) break;
         if (cudaStreamSynchronize(st) != cudaSuccess) break;
     } while (false);
     const cudaError_t err = cudaGetLastError();
     if (rc == MITHRA_OK && err != cudaSuccess) rc = set_last_error(MITHRA_ECUDA, cudaGetErrorString(err));
     if (cudaStreamSynchronize(st) != cudaSuccess) cudaGetLastError();
-    dfree(cnt);
-    dfree(mm);
-    dfree(d);
+    if (cnt) free_fn(ctx, cnt);
+    if (mm) free_fn(ctx, mm);
+    return rc;
+}
+
+namespace {
+struct HostAlloc {
+    mithra_alloc_fn af;
+    mithra_free_fn ff;
+    void* ctx;
+};
+void* host_alloc(void* c, size_t b)
+{
+    auto* h = (HostAlloc*)c;
+    if (h->af) return h->af(h->ctx, b);
+    void* p = nullptr;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void host_free(void* c, void* p)
+{
+    auto* h = (HostAlloc*)c;
+    if (!p) return;
+    if (h->ff) h->ff(h->ctx, p);
+    else cudaFree(p);
+}
+}  // namespace
+
+extern "C" int mithra_ellipsoid_bunch(const mithra_ellipsoid* e, int64_t n, double* out6, void* stream)
+{
+    using namespace mithra;
+    if (!e || (n > 0 && !out6)) return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: null argument");
+    if (n < 0 || n >= ((int64_t)1 << 32) - 1) return set_last_error(MITHRA_EINVAL, "ellipsoid_bunch: n out of range");
+    if (n == 0) return ellipsoid_device(*e, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+    cudaStream_t st = (cudaStream_t)stream;
+    HostAlloc ha;
+    get_allocator(&ha.af, &ha.ff, &ha.ctx);
+    double* d = (double*)host_alloc(&ha, (size_t)n * 6 * sizeof(double));
+    if (!d) return set_last_error(MITHRA_ENOMEM, "ellipsoid_bunch: device allocation failed");
+    int rc = ellipsoid_device(*e, n, 0, d, host_alloc, host_free, &ha, st);
+    if (rc == MITHRA_OK) {
+        if (cudaMemcpyAsync(out6, d, (size_t)n * 6 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            const cudaError_t err = cudaGetLastError();
+            rc = set_last_error(MITHRA_ECUDA, cudaGetErrorString(err));
+        }
+    }
+    host_free(&ha, d);
     return rc;
 }

@@ -1108,7 +1108,39 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
             delete r;
             return fail(MITHRA_ENOMEM, "device allocation failed (lab particles)");
         }
-        cudaError_t e = cudaMemcpyAsync(lab, b.lab_particles, (size_t)b.n * 6 * 8, cudaMemcpyHostToDevice, r->stream);
+        cudaError_t e = cudaSuccess;
+        if (b.lab_particles) {
+            e = cudaMemcpyAsync(lab, b.lab_particles, (size_t)b.n * 6 * 8, cudaMemcpyHostToDevice, r->stream);
+        } else {
+            // generated ellipsoid bunch (Sec. BUNCH, bunch-initialization): the quasi-random loader
+            // with the bunch's parameters, written straight to device memory
+            mithra_ellipsoid el{};
+            el.uniform = b.uniform;
+            el.gamma = b.gamma;
+            el.sig[0] = b.sig_x;
+            el.sig[1] = b.sig_y;
+            el.sig[2] = b.sig_z;
+            el.sig_u[0] = b.sig_x > 0.0 ? b.eps_n_x / b.sig_x : 0.0;
+            el.sig_u[1] = b.sig_y > 0.0 ? b.eps_n_y / b.sig_y : 0.0;
+            el.sig_u[2] = b.gamma * b.rel_espread;
+            el.cse_sigma = b.cse_sigma;
+            el.lambda_r = b.lambda_r > 0.0 ? b.lambda_r : 2.0 * kPi / (d.kstar * d.g0 * (1.0 + d.b0));
+            el.bunching = b.bunching;
+            el.bunching_phase = b.bunching_phase;
+            el.shot_noise = b.shot_noise;
+            el.charge_e = b.charge_e;
+            struct Adapter {
+                static void* get(void* c, size_t n) { return ((DevMem*)c)->get(n); }
+                static void put(void* c, void* q) { ((DevMem*)c)->release(q); }
+            };
+            rc = ellipsoid_device(el, b.n, b.seed, lab, Adapter::get, Adapter::put, &r->mem, r->stream);
+            if (rc) {
+                r->mem.release(lab);
+                r->destroy_all();
+                delete r;
+                return rc;
+            }
+        }
         if (e == cudaSuccess) e = launch_boost<real>(lab, b.n, r->P, g, r->ef, d.z_ref, r->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
         r->mem.release(lab);
@@ -1171,10 +1203,22 @@ int mithra::validate_request(const mithra_grid* gr, double dt_lab, const mithra_
     if (!(b->gamma >= 1.0)) return fail(MITHRA_EINVAL, "create: gamma must be >= 1");
     if (b->n < 0 || b->n >= (int64_t(1) << 31)) return fail(MITHRA_EINVAL, "create: particle count out of range");
     if (b->n > 0) {
-        if (!b->lab_particles) return fail(MITHRA_EINVAL, "create: lab_particles is null");
         if (!(b->charge_e > 0)) return fail(MITHRA_EINVAL, "create: charge_e must be > 0");
-        for (int64_t i = 0; i < 6 * b->n; ++i)
-            if (!std::isfinite(b->lab_particles[i])) return fail(MITHRA_EINVAL, "create: non-finite particle value");
+        if (b->lab_particles) {
+            for (int64_t i = 0; i < 6 * b->n; ++i)
+                if (!std::isfinite(b->lab_particles[i])) return fail(MITHRA_EINVAL, "create: non-finite particle value");
+        } else {
+            if (!finite_all({b->rel_espread, b->sig_x, b->sig_y, b->eps_n_x, b->eps_n_y, b->cse_sigma, b->lambda_r,
+                             b->bunching, b->bunching_phase}))
+                return fail(MITHRA_EINVAL, "create: non-finite bunch parameter");
+            if (!(b->rel_espread >= 0 && b->sig_x >= 0 && b->sig_y >= 0 && b->sig_z >= 0 && b->eps_n_x >= 0 &&
+                  b->eps_n_y >= 0 && b->bunching >= 0))
+                return fail(MITHRA_EINVAL, "create: bunch sizes, emittances, spread and bunching must be >= 0");
+            if ((b->uniform != 0 && b->uniform != 1) || (b->shot_noise != 0 && b->shot_noise != 1))
+                return fail(MITHRA_EINVAL, "create: uniform and shot_noise must be 0 or 1");
+            if ((uint64_t)b->n + b->seed >= ((uint64_t)1 << 32) - 1)
+                return fail(MITHRA_EINVAL, "create: n + seed must be below 2^32 - 1");
+        }
     }
     return MITHRA_OK;
 }

@@ -341,7 +341,7 @@ extern "C" int mithra_submit(const mithra_grid* g, const mithra_undulator* u, co
     r->g = *g;
     r->u = *u;
     r->b = *b;
-    if (b->n > 0) r->lab.assign(b->lab_particles, b->lab_particles + 6 * b->n);
+    if (b->n > 0 && b->lab_particles) r->lab.assign(b->lab_particles, b->lab_particles + 6 * b->n);
     r->b.lab_particles = nullptr;
     r->nsteps = nsteps;
     r->reserve = mithra::footprint(g, u, b, nsteps);

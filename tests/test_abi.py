@@ -39,14 +39,15 @@ def test_struct_layouts_match_c(tmp_path):
                  ' offsetof(mithra_undulator, dist_to_bunch_head), offsetof(mithra_bunch, lab_particles),'
                  ' offsetof(mithra_grid, nf_points), offsetof(mithra_grid, bunch_every),'
                  ' offsetof(mithra_undulator, n_modules), offsetof(mithra_undulator, taper));'
-                 'printf("%zu\\n", offsetof(mithra_grid, optimize_position));return 0;}\n')
+                 'printf("%zu %zu\\n", offsetof(mithra_grid, optimize_position), offsetof(mithra_bunch, seed));'
+                 'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     py = [ctypes.sizeof(m.Grid), ctypes.sizeof(m.Undulator), ctypes.sizeof(m.Bunch),
           m.Grid.sort_every.offset, m.Undulator.dist_to_bunch_head.offset, m.Bunch.lab_particles.offset,
           m.Grid.nf_points.offset, m.Grid.bunch_every.offset, m.Undulator.n_modules.offset,
-          m.Undulator.taper.offset, m.Grid.optimize_position.offset]
+          m.Undulator.taper.offset, m.Grid.optimize_position.offset, m.Bunch.seed.offset]
     assert vals == py
 
 
