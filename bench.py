@@ -87,10 +87,21 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
+    def snapshot(self):
+        """One reading, taken right before and right after the timed region (a short region may
+        see no sample of the periodic query)."""
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            self.lines.extend(l.strip() for l in out.stdout.splitlines() if l.strip())
+        except Exception:
+            pass
+
     def start(self):
+        self.snapshot()
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "5"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -102,14 +113,16 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self) -> dict:
-        if self.proc is None:
+        if self.proc is None and not self.lines:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.t.join(timeout=2)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        self.snapshot()
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for ln in self.lines:
@@ -161,21 +174,69 @@ def _ncu_traffic(kernel: str):
         return None
 
 
-def cpu_oracle_rate(w, lab, budget_s: float, max_steps: int):
-    """Oracle throughput on the workload: steps until the budget is spent (at least one)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_leg(w, lab, steps: int, skip: int = 4):
+    """The oracle on all host cores (OpenMP; its independent loops only, so the results are those
+    of one thread): `steps` steps, the rate taken over the steps after the first `skip`.  Returns
+    the run (at `steps`), the rate in steps/s and the threads used."""
     import oracle
-    t0 = time.perf_counter()
     o = oracle.Run(oracle.params_from(w), lab)
-    t_create = time.perf_counter() - t0
-    steps = 0
+    o.step(skip)
     t1 = time.perf_counter()
-    while steps < max_steps:
-        o.step(1)
-        steps += 1
-        if time.perf_counter() - t1 > budget_s:
-            break
+    o.step(steps - skip)
     dt = time.perf_counter() - t1
-    return o, steps, dt, t_create
+    return o, (steps - skip) / dt, oracle.threads()
+
+
+def oracle_serial_rate(w, lab, steps: int = 2):
+    """The same oracle on one thread (the serial reference), over a couple of steps."""
+    import oracle
+    n = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        o = oracle.Run(oracle.params_from(w), lab)
+        o.step(1)
+        t1 = time.perf_counter()
+        o.step(steps)
+        dt = time.perf_counter() - t1
+        o.close()
+    finally:
+        oracle.set_threads(n)
+    return steps / dt
+
+
+def precision_errors(a: dict, b: dict, M: int) -> dict:
+    """Errors of run a against run b: relative L2 and maximum norm of the potentials (A as a
+    vector, phi), the radiated power over complete DFT windows (max |dp| / max |p|), the field
+    energy and the bunching factor."""
+    import numpy as np
+    A_a, A_b = np.stack(a["pot"][:3]), np.stack(b["pot"][:3])
+    nphi = max(float(np.linalg.norm(b["pot"][3])), 1e-300)
+    pa, pb = a["p"][M - 1:], b["p"][M - 1:]
+    return {"field_l2_rel_A": float(np.linalg.norm(A_a - A_b) / np.linalg.norm(A_b)),
+            "field_l2_rel_phi": float(np.linalg.norm(a["pot"][3] - b["pot"][3]) / nphi),
+            "field_max_rel_A": float(np.max(np.abs(A_a - A_b)) / np.max(np.abs(A_b))),
+            "power_rel": float(np.max(np.abs(pa - pb)) / max(float(np.max(np.abs(pb))), 1e-300)),
+            "field_energy_rel": abs(a["diag"][0] - b["diag"][0]) / b["diag"][0],
+            "bunching_abs": abs(a["diag"][1] - b["diag"][1])}
 
 
 def run_reference(args):
@@ -189,6 +250,7 @@ def run_reference(args):
     o = oracle.Run(oracle.params_from(w), lab)
     o.step(min(args.warmup, 1))   # the oracle has no cache to warm; one step settles page faults
     budget = float(os.environ.get("MITHRA_REF_BUDGET_S", "150"))
+    cores = oracle.threads()
     t1 = time.perf_counter()
     steps = 0
     while steps < args.steps:
@@ -203,11 +265,12 @@ def run_reference(args):
             "steps": args.steps, "steps_timed": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [w.nx, w.ny, w.nz], "particles": w.n_particles,
-                       "precision": "fp64 (CPU oracle, serial)"},
+                       "precision": f"fp64 (CPU oracle, {cores} threads)"},
             "particle_pushes_per_s": w.n_particles * steps / dt,
-            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "cpu": cpu_model(), "nproc": os.cpu_count(),
                              "sample": f"{steps} full field steps of {WORKLOAD} ({cells} cells, "
-                                       f"{w.n_particles} particles), serial FP64 C"},
+                                       f"{w.n_particles} particles), FP64 C on {cores} threads (OpenMP)"},
             "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -241,12 +304,20 @@ def serving_run(m, workloads, all_fp64: bool, n_requests: int, rate_hz: float):
         m.serve_stop()
     ok = [r for r in res if r.status == 0]
     lat = sorted(r.t_done - r.t_submit for r in ok)
+    wait = sorted(r.t_admit - r.t_submit for r in ok)
+    service = sorted(r.t_done - r.t_admit for r in ok)
     span = max(r.t_done for r in ok) - min(r.t_submit for r in ok)
     cells = sum(w.nx * w.ny * w.nz * w.steps for (_, w), r in zip(reqs, res) if r.status == 0)
     pushes = sum(w.n_particles * w.steps for (_, w), r in zip(reqs, res) if r.status == 0)
-    q = lambda f: lat[min(len(lat) - 1, int(math.ceil(f * len(lat))) - 1)]
+
+    def q(v, f):
+        return v[min(len(v) - 1, int(math.ceil(f * len(v))) - 1)]
+
     return {"requests": n_requests, "completed": len(ok), "arrival_rate_hz": rate_hz,
-            "p50_s": q(0.50), "p99_s": q(0.99), "max_s": lat[-1], "makespan_s": span,
+            "p50_s": q(lat, 0.50), "p99_s": q(lat, 0.99), "max_s": lat[-1], "makespan_s": span,
+            "queue_wait_p50_s": q(wait, 0.50), "queue_wait_p99_s": q(wait, 0.99),
+            "service_p50_s": q(service, 0.50), "service_p99_s": q(service, 0.99),
+            "latency": "time to result = queue wait (submit to admission) + service (admission to done)",
             "cell_updates_per_s": cells / span, "particle_pushes_per_s": pushes / span,
             "pool_peak_bytes": peak, "precision": "fp64 for every request" if all_fp64 else "50/50 FP32-mixed/FP64"}
 
@@ -267,6 +338,9 @@ def main():
     ap.add_argument("--no-diag", action="store_true", help="skip the spectrum / bunch-sampling run")
     ap.add_argument("--no-seeded", action="store_true", help="skip the seeded UV FEL workload")
     ap.add_argument("--no-loading", action="store_true", help="skip the quasi-random bunch loading")
+    ap.add_argument("--no-big", action="store_true", help="skip the 256x256x1024 and 192x192x768 workloads")
+    ap.add_argument("--error-windows", type=int, default=3,
+                    help="radiated-power DFT windows of the error-against-oracle leg (0: skip it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -408,6 +482,30 @@ def main():
                   "kernel_ms_per_step": {k: v[0] / Ks for k, v in statss.items() if v[1]}}
         del labs
 
+    # ---- the large helical run (256 x 256 x 1024, 32 M particles) and the inverse-Compton run ----
+    big = {}
+    if not args.no_big:
+        for wn in ("helical_256x256x1024", "ics_192x192x768"):
+            wb = workloads.WORKLOADS[wn]
+            labb = workloads.lab_bunch(wb)
+            Kb = max(10, K // 2)
+            msb, statsb, _, _, infob, _ = timed_run(1, Kb, False, wb, labb)
+            msb = reduce_max(msb)
+            cb = wb.nx * wb.ny * wb.nz
+            plb = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in statsb.items()}
+            ent = {"value": whole_job_rate(ws, cb, Kb, msb), "unit": "cell-updates/s",
+                   "particle_pushes_per_s": whole_job_rate(ws, wb.n_particles, Kb, msb), "ms_per_step": msb / Kb,
+                   "steps": Kb, "grid": [wb.nx, wb.ny, wb.nz], "particles": wb.n_particles,
+                   "precision": "fp32-mixed", "kernel_ms_per_step": {k: v[0] / Kb for k, v in statsb.items() if v[1]}}
+            if plb.get("stencil"):
+                a = 64 * cb / (plb["stencil"] * 1e-3) / 1e9
+                ent["stencil_roofline"] = {"achieved": a, "frac": a / _peaks()[0], "ms_per_launch": plb["stencil"]}
+            if plb.get("push_deposit"):
+                a = 80 * wb.n_particles / (plb["push_deposit"] * 1e-3) / 1e9
+                ent["push_roofline"] = {"achieved": a, "frac": a / _peaks()[0], "ms_per_launch": plb["push_deposit"]}
+            big[wn] = ent
+            del labb
+
     # ---- quasi-random loading of a 32 M-particle ellipsoid bunch (Halton, uniform + CSE edges) --
     loading = None
     if not args.no_loading:
@@ -462,7 +560,9 @@ def main():
     alg = {
         "stencil": 4 * 4 * 4 * ncell,                       # 4 potentials x (psi^n, psi^{n-1}, source, psi^{n+1})
         "emit_eb": 68 * info["emitted_nodes"],              # see emit_roof below
-        "push_deposit": 2 * 48 * w.n_particles,             # particle state in and out (cell, offset, momentum)
+        # particle state in and out counted as one int32 cell index, three FP32 offsets and three
+        # 8-byte momenta: 40 B each way (the layout keeps three int32 cells: 48 B moved each way)
+        "push_deposit": 2 * 40 * w.n_particles,
         "clear_sources": 4 * 4 * ncell,
         "mur": 0,
         "power": 0,
@@ -474,6 +574,7 @@ def main():
             achieved = alg[kern] / (per_launch[kern] * 1e-3) / 1e9
             roof = {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "traffic": _ncu_traffic(kern),
+                    "state_bytes_per_launch": 2 * 48 * w.n_particles if kern == "push_deposit" else None,
                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_kind == "measured" else "fallback 6.8 TB/s",
                     "alg_bytes_per_launch": alg[kern], "ms_per_launch": per_launch[kern]}
@@ -493,27 +594,46 @@ def main():
                      "alg_bytes_per_launch": eb_bytes, "emitted_nodes": info["emitted_nodes"],
                      "traffic": _ncu_traffic("emit_eb")}
 
-    # ---- CPU baseline (oracle) and the error of the GPU path against it ----------------------
+    # ---- CPU baseline (oracle) and the errors of both GPU paths against it ---------------------
     cpu = None
     err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        o, s_cpu, dt_cpu, _ = cpu_oracle_rate(w, lab, args.cpu_budget, 6)
-        cpu = {"value": cells * s_cpu / dt_cpu, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{s_cpu} full field steps of {wname} after creation, serial FP64 C",
-               "particle_pushes_per_s": w.n_particles * s_cpu / dt_cpu}
-        err = {"steps": s_cpu}
-        fo, bo = o.diag()
-        for prec, tag in ((1, "fp32_mixed"), (0, "fp64")):
-            g = m.Run.from_workload(w, lab, precision=prec)
-            g.step(s_cpu)
-            fg, bg = g.diag()
-            l2 = []
-            for c in range(3):
-                a, bb = g.field(c, 1), o.field(c, 1)
-                l2.append(float(np.linalg.norm(a - bb) / max(np.linalg.norm(bb), 1e-300)))
-            err[tag] = {"field_l2_rel_A": max(l2), "field_energy_rel": abs(fg - fo) / fo,
-                        "bunching_abs": abs(bg - bo)}
-            g.close()
+        M = int(round(info["M"]))
+        n_err = max(args.error_windows, 1) * M
+        o, rate, cores = oracle_leg(w, lab, n_err)
+        serial = oracle_serial_rate(w, lab)
+        cpu = {"value": cells * rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "cpu": cpu_model(), "nproc": os.cpu_count(),
+               "sample": f"steps 5-{n_err} of {wname} ({cells} cells, {w.n_particles} particles), FP64 C, "
+                         f"independent loops on {cores} threads (OpenMP), deposition serial",
+               "particle_pushes_per_s": w.n_particles * rate,
+               "serial": {"value": cells * serial, "unit": "cell-updates/s", "cores": 1,
+                          "sample": f"2 steps of {wname} on one thread"}}
+        if args.error_windows > 0:
+            ref = {"pot": [o.field(c, 1) for c in range(4)], "p": o.series()[0], "diag": o.diag()}
+
+            def gpu(prec, labx, sort_every=0):
+                g = m.Run.from_workload(w, labx, precision=prec, sort_every=sort_every)
+                g.step(n_err)
+                out = {"pot": [g.field(c, 1) for c in range(4)], "p": g.series()[0], "diag": g.diag()}
+                g.close()
+                return out
+
+            err = {"steps": n_err, "power_windows": args.error_windows, "M": M,
+                   "what": "relative L2 / max of the potentials at the last step, radiated power over complete "
+                           "DFT windows (max |dp| / max |p|), field energy, bunching"}
+            g32 = gpu(1, lab)
+            err["fp32_mixed"] = precision_errors(g32, ref, M)
+            err["fp32_mixed"]["run_to_run"] = precision_errors(gpu(1, lab), g32, M)
+            g64 = gpu(0, lab)
+            err["fp64"] = precision_errors(g64, ref, M)
+            pert = lab[::-1].copy()
+            sgn = np.where(np.random.default_rng(3).random(pert[:, 3:].shape) < 0.5, -1.0, 1.0)
+            pert[:, 3:] *= 1.0 + 4.4e-16 * sgn
+            err["fp64"]["atomic_reordering_floor"] = precision_errors(gpu(0, pert, -1), g64, M)
+            err["bounds"] = {"fp32_mixed": "field energy 1e-4, radiated power 1 %",
+                             "fp64": "1e-11 on fields + 4 x the atomic-reordering floor"}
+        o.close()
 
     served = None
     if not args.no_serving:
@@ -546,6 +666,7 @@ def main():
         "emit_roofline": emit_roof,
         "cpu_baseline": cpu,
         "error_vs_oracle": err,
+        "large_runs": big or None,
         "e2e": {"value": whole_job_rate(ws, cells, K, t_e2e * 1e3), "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K, "what": "mithra_create from pinned host particles (H2D), "
                 f"{K} steps, power series + diagnostics to host (D2H)"},
