@@ -17,13 +17,16 @@
  * Parity pins (tests/test_oracle_*.py) tie it to what the paper and the
  * mathematics fix: the discrete dispersion relations (Eqs. numericalDispersionCD,
  * NSFDDispersionCD), the exact one-cell shift of NSFD at c dt = dz, the Mur
- * coefficient formulas and the Engquist-Majda reflection curves, discrete
- * charge continuity, the Lorentz gauge residual, Boris rotation invariants,
- * Lorentz invariants of the transformed undulator field, the single-electron
- * undulator trajectory, and the on-axis resonance.
- * The absolute radiated power of undulator radiation through a finite plane
- * is parity unpinned (the manual prints only figure curves for it); its
- * plane-wave flux and its coherent scaling are pinned.
+ * coefficient formulas and the Engquist-Majda reflection curves, the Mur edge and
+ * corner values (a field satisfying every meeting face's outgoing condition is
+ * reproduced exactly), E and B at nodes (exact for potentials linear in space) and
+ * the field energy of uniform fields, discrete charge continuity, the Lorentz gauge
+ * residual, Boris rotation invariants, Lorentz invariants of the transformed
+ * undulator field, the single-electron undulator trajectory and the
+ * optimize-bunch-position drift, the on-axis resonance of planar, helical and
+ * optical undulators, the plane-wave flux and coherent scaling of the radiated
+ * power, and the absolute power of a weak-undulator electron against the flux of
+ * the equivalent rest-frame dipole through the plane (within 8 %).
  */
 #ifndef MITHRA_ORACLE_H
 #define MITHRA_ORACLE_H
