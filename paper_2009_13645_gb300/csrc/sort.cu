@@ -14,21 +14,40 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Lanes of a warp that share a bin add to its counter once: the leader (lowest lane) adds their
+// number, and every lane learns the value the counter had before (*base) and its own rank among
+// them.  Particles that share a cell (and the many outside the node range, all in one bin) are
+// neighbours in a warp, so most of their atomics on one address collapse into one.
+__device__ __forceinline__ int32_t warp_aggregated_add(int32_t* ctr, int32_t bin, bool active)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (!active) return 0;
+    const unsigned peers = __match_any_sync(act, bin);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(ctr + bin, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 template <typename real>
 __global__ void k_keys(Particles<real> P, int64_t np, Geom g, int32_t* __restrict__ key, int32_t* __restrict__ count,
                        int64_t nbins)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    const int i = P.ix[p], j = P.iy[p], k = P.iz[p];
-    int32_t kk;
-    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) {
-        const int64_t row = (int64_t)k * g.ny + ((k & 1) ? g.ny - 1 - j : j);
-        kk = (int32_t)(row * g.nx + ((row & 1) ? g.nx - 1 - i : i));
-    } else
-        kk = (int32_t)(nbins - 1);
-    key[p] = kk;
-    atomicAdd(count + kk, 1);
+    const bool in = p < np;
+    int32_t kk = 0;
+    if (in) {
+        const int i = P.ix[p], j = P.iy[p], k = P.iz[p];
+        if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) {
+            const int64_t row = (int64_t)k * g.ny + ((k & 1) ? g.ny - 1 - j : j);
+            kk = (int32_t)(row * g.nx + ((row & 1) ? g.nx - 1 - i : i));
+        } else
+            kk = (int32_t)(nbins - 1);
+        key[p] = kk;
+    }
+    warp_aggregated_add(count, kk, in);
 }
 
 // Exclusive scan of one tile per block; the tile total goes to partial[blockIdx.x].
@@ -115,8 +134,9 @@ __global__ void k_slot(const int32_t* __restrict__ key, int64_t np, int32_t* __r
                        int32_t* __restrict__ perm)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    perm[p] = atomicAdd(cursor + key[p], 1);
+    const bool in = p < np;
+    const int32_t slot = warp_aggregated_add(cursor, in ? key[p] : 0, in);
+    if (in) perm[p] = slot;
 }
 
 template <typename real>
