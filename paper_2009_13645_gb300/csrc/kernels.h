@@ -180,6 +180,10 @@ struct PushConst {
     // FP32-mixed deposit tile: fixed-point scale per source grid (2^30 / (128 |qJ_l|), 2^30 /
     // (128 |q|)) and its inverse
     float tscale[4], tunit[4];
+    // optical undulator, FP32-mixed path: the transverse rest-frame amplitudes gamma0 (1 + beta0) E0
+    // and gamma0 (1 + beta0) E0 / c (the Lorentz transform of a wave travelling along -z, evaluated in
+    // FP64), E0, E0 / c, the waist, 1 / z_R, z_R and k_L, rounded to FP32
+    float ltE, ltB, E0f, E0cf, w0f, izrf, zrf, kLf;
 };
 
 cudaError_t launch_phase_table(const ExtField& ef, const StepDev* sd, double kz, int nz, double2* t0, double2* t1,

@@ -563,6 +563,14 @@ struct RunT final : mithra_run {
         pc.eB0f = (float)(ef.g0 * ef.b0 * kC * ef.B0);
         pc.bB0f = (float)(ef.g0 * ef.B0);
         pc.B0f = (float)ef.B0;
+        pc.ltE = (float)(ef.g0 * (1.0 + ef.b0) * ef.E0);
+        pc.ltB = (float)(ef.g0 * (1.0 + ef.b0) * ef.E0 / kC);
+        pc.E0f = (float)ef.E0;
+        pc.E0cf = (float)(ef.E0 / kC);
+        pc.w0f = (float)ef.w0;
+        pc.izrf = (float)(1.0 / ef.zr);
+        pc.zrf = (float)ef.zr;
+        pc.kLf = (float)ef.kL;
         pbeg(MITHRA_K_PUSH, &e0);
         if (ptab[0]) CU(launch_phase_table(ef, sd, pc.kz, g.nz, ptab[0], ptab[1], stream));
         if (ptab32[0]) CU(launch_phase_table32(ef, sd, pc.kz, g.nz, ptab32[0], ptab32[1], ptab32a, stream));

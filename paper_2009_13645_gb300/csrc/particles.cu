@@ -214,6 +214,53 @@ __device__ __forceinline__ bool static_field_mixed(const ExtField& f, const Push
     return true;
 }
 
+// Optical undulator (Sec. "Optical Undulator", Eqs. opticalUndulatorPW / opticalUndulatorGB,
+// signalTypes) for the FP32-mixed path at the rest-frame event (x, y, z, t).  The lab coordinates
+// and the retarded time tau of the counter-propagating wave are formed in FP64 and the carrier
+// phase w_L tau is reduced to [-pi, pi] in FP64; the envelope, the beam profile, the Gouy and
+// curvature phases and the cosines are evaluated in FP32.  A wave along -z has B_perp = z x E_perp / c
+// (paraxial), so the Lorentz transform to the frame moving with +beta0 multiplies both transverse
+// fields by gamma0 (1 + beta0) and leaves E_z, B_z unchanged: that factor sits in the FP64-evaluated
+// amplitudes ltE, ltB, rounded once.
+__device__ __forceinline__ void optical_field_mixed(const ExtField& f, const PushConst& pc, double x, double y,
+                                                    double z, double t, float E[3], float B[3])
+{
+    const double zeta = f.g0 * fma(f.b0 * kC, t, z);
+    const double tl = f.g0 * fma(f.b0 / kC, z, t);
+    const double tau = (tl - f.t_f) + (zeta - f.zeta_f) / kC;
+    const double ph = f.wL * tau;
+    const float phr = (float)fma(-rint(ph * (0.5 / kPi)), 2.0 * kPi, ph);
+    float env = 1.f;
+    if (f.tp > 0.0 && !(f.signal == 1 && tau > 0.0)) {
+        const float u = (float)(tau / f.tp);
+        env = expf(-1.3862944f * u * u);   // 2 ln 2
+    }
+    float S, El = 0.f, Bl = 0.f;
+    if (f.kind == 2 || f.w0 <= 0.0) {
+        S = env * cosf(phr);
+    } else {
+        const float l = (float)(f.zeta_f - zeta);     // distance travelled past the focus
+        const float lz = l * pc.izrf;
+        const float q = 1.f + lz * lz;                // (w(l) / w0)^2
+        const float rpar = (float)(x * f.cpol + y * f.spol), rper = (float)(y * f.cpol - x * f.spol);
+        const float r2 = rpar * rpar + rper * rper;
+        const float curv = pc.kLf * r2 * l / (2.f * (l * l + pc.zrf * pc.zrf));
+        const float gouy = atanf(lz);
+        const float iw = rsqrtf(q);                   // w0 / w(l)
+        const float amp = iw * expf(-r2 / (pc.w0f * pc.w0f * q)) * env;
+        S = amp * cosf(phr + gouy - curv);
+        const float sl = amp * cosf(phr + 2.f * gouy - curv + 1.5707964f) * pc.izrf * iw;
+        El = pc.E0f * rpar * sl;                      // E0 r_par w0 / (z_R w) amp f
+        Bl = pc.E0cf * rper * sl;
+    }
+    E[0] = pc.ltE * S * pc.cpolf;
+    E[1] = pc.ltE * S * pc.spolf;
+    E[2] = -El;
+    B[0] = pc.ltB * S * pc.spolf;
+    B[1] = -pc.ltB * S * pc.cpolf;
+    B[2] = -Bl;
+}
+
 // FP32 table for the mixed path, two float4 per node plane and planar field: the sin and cos of
 // the plane's phase k_u u times the FP64 rest-frame amplitudes (gamma0 beta0 c B, gamma0 B, B),
 // and the distances k_u u, k_u (u - L_u) to both ends of the undulator; FP64 throughout, rounded
@@ -478,6 +525,12 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
             const float x = fmaf((float)ci[0] + f[0], pc.dxf, pc.x0f);
             const float y = fmaf((float)ci[1] + f[1], pc.dyf, pc.y0f);
             tab = static_field_mixed(ef, pc, ci[2], inside, Z0, f[2], m, x, y, Ef, Bf);
+        } else if (ef.kind == 2 || ef.kind == 3) {
+            const double x = g.x0 + ((double)ci[0] + (double)f[0]) * g.dx;
+            const double y = g.y0 + ((double)ci[1] + (double)f[1]) * g.dy;
+            const double z = g.z0 + ((double)ci[2] + (double)f[2]) * g.dz;
+            optical_field_mixed(ef, pc, x, y, z, t_half + (double)m * g.dtb, Ef, Bf);
+            tab = true;
         }
     } else {
         if (pc.ptab[0] && ci[2] >= 0 && ci[2] < g.nz) {

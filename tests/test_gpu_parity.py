@@ -188,6 +188,29 @@ def test_full_step_fp64_kinds(kind, substeps, solver, order):
     _compare_run(o, g, 60, 1e-11, 1e-10, w, lab)
 
 
+@pytest.mark.parametrize("kind", [2, 3])
+def test_full_step_fp32_mixed_optical(kind):
+    """FP32-mixed path in an optical undulator (plane wave and Gaussian beam): the carrier phase
+    reduced in FP64, profile and envelope in FP32, the transverse Lorentz factor gamma0 (1 + beta0)
+    in FP64-evaluated amplitudes.  Field energy within the stated 1e-4, momenta within 1e-5 of
+    their scale after 60 steps (FP32 offsets and fields)."""
+    base = workloads.WORKLOADS["ics_192x192x768"]
+    w = workloads.scaled(base, nx=22, ny=20, nz=40, n_particles=1200, sig_x=2e-9, sig_y=2e-9,
+                         sig_z=2e-9, und_kind=kind, substeps=2, solver=0, mur_order=2, charge_e=2e3)
+    lab = workloads.lab_bunch(w)
+    o, g = pair(w, 1, lab=lab)
+    o.step(60)
+    g.step(60)
+    fo, _ = o.diag()
+    fg, _ = g.diag()
+    assert abs(fg - fo) / fo < 1e-4, (fg, fo)
+    po, pg = o.particles(), g.particles()
+    assert np.max(np.abs(pg[:, 3:] - po[:, 3:])) < 1e-5 * np.max(np.abs(po[:, 3:]))
+    inf = o.info()
+    D = np.array([inf["dx"], inf["dy"], inf["dz"]])
+    assert np.max(np.abs(pg[:, :3] - po[:, :3]) / D) < 1e-4
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_step_undulator_array(precision):
     """Static undulator array (one-period modules half a period apart, K tapered by 0.1 per
