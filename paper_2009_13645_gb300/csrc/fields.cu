@@ -383,6 +383,8 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
             if (p <= plast) {
                 real(*st)[EmitSmem<real>::RS] = sm.raw[stage(p)];
                 uint64_t* bar = &sm.bar[stage(p)];
+                // the stage held plane p - ENS, which the block read before its last barrier
+                if (p >= pfirst + ENS) mithra::fence_proxy_async_smem();
                 const int nc = use_phi ? 7 : 6;
                 mithra::mbar_expect_tx(bar, (uint32_t)(nc * RN * sizeof(real)));
                 for (int c = 0; c < nc; ++c) mithra::tma_load_3d(st[c], &em.m[c], i0 - 1, j0 - 1, p, bar);

@@ -61,6 +61,14 @@ struct TmaMaps {
     CUtensorMap emit[3][4];   // E/B emission region box (kEmitBoxW x kEmitBoxH), per level and component
 };
 
+// The maps one stencil launch reads: psi^n with halo, psi^{n-1} and the source of each component
+// (1.5 KB of kernel parameters; the whole ring's maps would pass 4 KB).
+struct StencilMaps {
+    CUtensorMap halo[4];
+    CUtensorMap body[4];
+    CUtensorMap src[4];
+};
+
 template <typename real>
 struct TmaArgs {
     real* out[4];
@@ -73,6 +81,10 @@ struct TmaArgs {
     real a1, ax, ay, a6, w, w0, s[4];
     real axw, axw0, ayw, ayw0;   // ax w, ax w0, ay w, ay w0 (products taken in FP64)
     int* err;
+    // failure test: the plane pfirst + skip_plane of every block is never copied (-1: none), and
+    // every wait gives up after `spin` polls
+    int skip_plane;
+    uint32_t spin;
 };
 
 template <typename real>
@@ -87,7 +99,7 @@ struct Vec2T<double> {
 };
 
 template <typename real>
-__global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_constant__ TmaMaps maps, TmaArgs<real> a,
+__global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_constant__ StencilMaps maps, TmaArgs<real> a,
                                                               int64_t sy, int64_t sz)
 {
     using T = Tile<real>;
@@ -106,8 +118,8 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     const int x = xt + cx, y = yt + ty;
     const bool yin = y >= 1 && y <= ey - 2;
     const bool mineA = yin && x >= 1 && x <= ex - 2, mineB = yin && x + 1 >= 1 && x + 1 <= ex - 2;
-    const CUtensorMap* mh = &maps.halo[a.lev_n][comp];
-    const CUtensorMap* mb = &maps.body[a.lev_m][comp];
+    const CUtensorMap* mh = &maps.halo[comp];
+    const CUtensorMap* mb = &maps.body[comp];
     const CUtensorMap* ms = &maps.src[comp];
     const int pfirst = k0 - 1, plast = k1 + 1;
 
@@ -118,7 +130,10 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     __syncthreads();
     auto issue = [&](int p) {
         const int s = (p - pfirst) % NST;
+        if (p - pfirst == a.skip_plane) return;   // failure test: this plane's copy never comes
         unsigned char* st = smem + s * T::STAGE;
+        // the stage held plane p - NST, which the block read before its last barrier
+        if (p >= pfirst + NST) fence_proxy_async_smem();
         mbar_expect_tx(bars + s, (uint32_t)T::TX_BYTES);
         tma_load_3d(st, mh, xt - T::HX, yt - 1, p, bars + s);
         tma_load_3d(st + T::OFF_PREV, mb, xt, yt, p, bars + s);
@@ -134,7 +149,7 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     auto wait_plane = [&](int p) {
         const int s = (p - pfirst) % NST;
         const uint32_t parity = (uint32_t)(((p - pfirst) / NST) & 1);
-        if (!mbar_wait(bars + s, parity)) ok = false;
+        if (!mbar_wait(bars + s, parity, a.spin)) ok = false;
     };
     // row dy of plane p's halo tile, at the pair's first cell
     auto hrow = [&](int p, int dy) -> const real* {
@@ -226,7 +241,7 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
             if (a.err) atomicExch(a.err, 1);
             for (int p = max(pfirst, k - 1); p <= last_issued; ++p) {
                 const int st = (p - pfirst) % NST;
-                mbar_wait(bars + st, (uint32_t)(((p - pfirst) / NST) & 1));
+                mbar_wait(bars + st, (uint32_t)(((p - pfirst) / NST) & 1), a.spin);
             }
         }
         __syncthreads();
@@ -311,7 +326,7 @@ bool emit_maps(const TmaMaps* maps, int lev_n, int lev_n1, EmitMaps* out)
 template <typename real>
 cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* const prev[4], const MurFaceCoef* mur,
                                int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp, int* err,
-                               cudaStream_t st)
+                               cudaStream_t st, int test_skip_plane)
 {
     using T = Tile<real>;
     static bool attr_set = false;
@@ -343,6 +358,8 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* co
     a.ayw = (real)(cf.ay * cf.w);
     a.ayw0 = (real)(cf.ay * cf.w0);
     a.err = err;
+    a.skip_plane = test_skip_plane;
+    a.spin = test_skip_plane >= 0 ? 1024u : kSpinLimit;
     a.mur = (mur && tma_x_faces<real>()) ? ((mur->ft[0][0] != 0.0 || mur->ft[0][1] != 0.0) ? 2 : 1) : 0;
     a.mf0 = mur ? (real)mur->f0[0] : (real)0;
     a.mf1 = mur ? (real)mur->f1[0] : (real)0;
@@ -350,7 +367,13 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* co
     a.mfz = mur ? (real)mur->ft[0][1] : (real)0;
     const int nchunk = (g.nz - 2 + KZ - 1) / KZ;
     const dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, nchunk * ncomp);
-    k_stencil_tma<real><<<grd, TX / 2 * TY, T::SMEM, st>>>(*maps, a, g.sy, g.sz);
+    StencilMaps sm;
+    for (int c = 0; c < 4; ++c) {
+        sm.halo[c] = maps->halo[lev_n][c];
+        sm.body[c] = maps->body[lev_m][c];
+        sm.src[c] = maps->src[c];
+    }
+    k_stencil_tma<real><<<grd, TX / 2 * TY, T::SMEM, st>>>(sm, a, g.sy, g.sz);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -360,9 +383,9 @@ template bool tma_supported<double>(const Geom&);
 template TmaMaps* make_tma_maps<float>(float* const[3][4], float* const[4], const Geom&);
 template TmaMaps* make_tma_maps<double>(double* const[3][4], double* const[4], const Geom&);
 template cudaError_t launch_stencil_tma<float>(const TmaMaps*, float* const[4], float* const[4], const MurFaceCoef*,
-                                               int, int, const Geom&, const StencilCoef&, int, int*, cudaStream_t);
+                                               int, int, const Geom&, const StencilCoef&, int, int*, cudaStream_t, int);
 template cudaError_t launch_stencil_tma<double>(const TmaMaps*, double* const[4], double* const[4],
                                                 const MurFaceCoef*, int, int, const Geom&, const StencilCoef&, int,
-                                                int*, cudaStream_t);
+                                                int*, cudaStream_t, int);
 
 }  // namespace mithra

@@ -44,10 +44,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// Orders this thread's (and, after a block barrier, the block's) earlier generic-proxy accesses of
+// shared memory before its later async-proxy operations: a tensor copy that refills a stage the
+// block has just read must not overwrite it before those reads are performed.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Bounded wait; false when the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit)
 {
-    for (uint32_t s = 0; s < kSpinLimit; ++s)
+    for (uint32_t s = 0; s < limit; ++s)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
