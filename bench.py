@@ -276,13 +276,14 @@ def run_reference(args):
     return 0
 
 
-def serving_run(m, workloads, all_fp64: bool, n_requests: int, rate_hz: float):
-    """The serving stream: Poisson arrivals, mixed grids, bunches and precision flags."""
+def serving_run(m, workloads, all_fp64: bool, n_requests: int, rate_hz: float, grouped: bool = False):
+    """The serving stream: Poisson arrivals, mixed grids, bunches and precision flags.  grouped: the
+    requests at a replay of their captured period advance together, one graph launch for all."""
     reqs = workloads.serving_requests(n_requests, rate_hz)
     if all_fp64:
         reqs = [(t, workloads.scaled(w, precision=0)) for t, w in reqs]
     labs = [workloads.lab_bunch(w) for _, w in reqs]
-    m.serve_start(64 << 30, max_active=16, queue_capacity=4 * n_requests, steps_per_chunk=16)
+    m.serve_start(64 << 30, max_active=16, queue_capacity=4 * n_requests, steps_per_chunk=16, grouped=grouped)
     try:
         t0 = time.perf_counter()
         tickets = []
@@ -298,6 +299,7 @@ def serving_run(m, workloads, all_fp64: bool, n_requests: int, rate_hz: float):
             time.sleep(0.005)
         res = [r for _, r in res]
         peak = m.serve_stats()["pool_peak"]
+        gstats = m.serve_group_stats()
         for t in tickets:
             m.release(t)
     finally:
@@ -319,7 +321,10 @@ def serving_run(m, workloads, all_fp64: bool, n_requests: int, rate_hz: float):
             "service_p50_s": q(service, 0.50), "service_p99_s": q(service, 0.99),
             "latency": "time to result = queue wait (submit to admission) + service (admission to done)",
             "cell_updates_per_s": cells / span, "particle_pushes_per_s": pushes / span,
-            "pool_peak_bytes": peak, "precision": "fp64 for every request" if all_fp64 else "50/50 FP32-mixed/FP64"}
+            "pool_peak_bytes": peak, "precision": "fp64 for every request" if all_fp64 else "50/50 FP32-mixed/FP64",
+            "design": ("grouped: ready requests' captured periods as child graphs of one graph launch"
+                       if grouped else "per-request streams, each replaying its own captured period"),
+            "group_launches": gstats["group_launches"], "group_periods": gstats["group_periods"]}
 
 
 def main():
@@ -638,6 +643,7 @@ def main():
     served = None
     if not args.no_serving:
         served = serving_run(m, workloads, False, args.serving_requests, 4.0)
+        served["grouped"] = serving_run(m, workloads, False, args.serving_requests, 4.0, grouped=True)
         served["fp64_path"] = serving_run(m, workloads, True, args.serving_requests, 4.0)
 
     value = whole_job_rate(ws, cells, K, ms32)

@@ -333,6 +333,16 @@ typedef struct mithra_result {
    the installed allocator), at most max_active requests on the device, a queue of at most
    queue_capacity waiting requests, and steps_per_chunk steps enqueued per request at a time. */
 int mithra_serve_start(size_t hbm_budget_bytes, int max_active, int queue_capacity, int steps_per_chunk);
+/* As mithra_serve_start; grouped = 1 also advances the admitted requests together: whenever two or
+   more of them are at a step from which their next steps are one replay of their captured period
+   (see mithra_step), one graph whose child graphs are those periods advances all of them with one
+   launch, rebuilt when its members change; a request's own steps keep their order (the group
+   waits for each member's stream and each member's stream waits for the group).  Requests outside
+   a group step on their own streams as with grouped = 0.  Results do not depend on the grouping. */
+int mithra_serve_start_grouped(size_t hbm_budget_bytes, int max_active, int queue_capacity, int steps_per_chunk,
+                               int grouped);
+/* out = {group launches, request periods advanced by them} since mithra_serve_start*. */
+int mithra_serve_group_stats(int64_t out[2]);
 /* Queue one request (inputs copied; never blocks).  EAGAIN when the queue is full, EINVAL as
    mithra_create, and when no server is running. */
 int mithra_submit(const mithra_grid *grid, const mithra_undulator *und, const mithra_bunch *bunch, int64_t nsteps,

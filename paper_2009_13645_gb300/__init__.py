@@ -115,6 +115,8 @@ def load(rebuild: bool = False):
     L.mithra_version.restype = C.c_int
     L.mithra_kernel_launches.restype = C.c_int64
     L.mithra_serve_start.argtypes = [C.c_size_t, C.c_int, C.c_int, C.c_int]
+    L.mithra_serve_start_grouped.argtypes = [C.c_size_t, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.mithra_serve_group_stats.argtypes = [C.POINTER(C.c_int64)]
     L.mithra_submit.argtypes = [C.POINTER(Grid), C.POINTER(Undulator), C.POINTER(Bunch), C.c_int64,
                                 C.POINTER(C.c_uint64)]
     L.mithra_poll.argtypes = [C.c_uint64, C.POINTER(C.c_int), C.c_void_p]
@@ -152,10 +154,19 @@ class Result(C.Structure):
                 ("power_peak", C.c_double), ("hbm_bytes", C.c_int64), ("reserved_bytes", C.c_int64)]
 
 
-def serve_start(hbm_budget_bytes: int, max_active: int = 8, queue_capacity: int = 256, steps_per_chunk: int = 16):
-    """Start the serving loop on the current device (see include/mithra.h)."""
-    _check(load().mithra_serve_start(C.c_size_t(int(hbm_budget_bytes)), int(max_active), int(queue_capacity),
-                                     int(steps_per_chunk)))
+def serve_start(hbm_budget_bytes: int, max_active: int = 8, queue_capacity: int = 256, steps_per_chunk: int = 16,
+                grouped: bool = False):
+    """Start the serving loop on the current device (see include/mithra.h); grouped: ready requests
+    advance together, one graph launch for all of them."""
+    _check(load().mithra_serve_start_grouped(C.c_size_t(int(hbm_budget_bytes)), int(max_active), int(queue_capacity),
+                                             int(steps_per_chunk), 1 if grouped else 0))
+
+
+def serve_group_stats() -> dict:
+    """Group launches of the running server and the request periods they advanced."""
+    out = (C.c_int64 * 2)()
+    _check(load().mithra_serve_group_stats(out))
+    return {"group_launches": int(out[0]), "group_periods": int(out[1])}
 
 
 def submit(w, lab6=None, nsteps=None, precision=None) -> int:

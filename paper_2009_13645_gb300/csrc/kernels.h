@@ -54,11 +54,13 @@ MurFaceCoef mur_face_coef(const Geom& g, int order);
 
 // With `mur` (not null: the run's Mur coefficients) and FP32 storage the stencil also writes the
 // Mur values of the interior nodes of the x faces (x = 0 and x = ex - 1) of every lattice it
-// updates; tma_x_faces<real>() tells whether it does.
+// updates; tma_x_faces<real>() tells whether it does.  test_skip_plane >= 0 (failure tests only):
+// every block leaves the copy of its plane pfirst + test_skip_plane out and its waits give up
+// after 1024 polls, so the bounded-wait path runs and sets *err.
 template <typename real>
 cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* const prev[4], const MurFaceCoef* mur,
                                int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp, int* err,
-                               cudaStream_t st);
+                               cudaStream_t st, int test_skip_plane = -1);
 
 template <typename real>
 constexpr bool tma_x_faces()

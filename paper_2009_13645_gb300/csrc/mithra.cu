@@ -161,6 +161,8 @@ struct mithra_run {
     virtual int bunch_samples(double* out, size_t cap_rows, size_t* n_rows) = 0;
     virtual int sync() = 0;
     virtual int64_t graph_steps() const = 0;
+    virtual cudaGraph_t period_graph(int64_t steps_left) = 0;
+    virtual void period_replayed() = 0;
     virtual void destroy_all() = 0;
 
     // common state
@@ -256,6 +258,7 @@ struct RunT final : mithra_run {
     TmaMaps* tma = nullptr;    // tensor maps of the TMA stencil (null: plain stencil)
     MurFaceCoef murc{};        // Mur face coefficients (the FP32 TMA stencil writes the x faces)
     int* err_word = nullptr;   // set by a kernel whose bounded wait expired
+    int test_tma_skip = -1;    // failure tests: TMA stencil plane left uncopied (-1: none)
     unsigned* counters = nullptr;   // last-block counters (Mur edges, power), zero between launches
     StepDev* sd = nullptr;     // per-step values derived on the device from the step counter
     StepConst scst{};
@@ -263,6 +266,7 @@ struct RunT final : mithra_run {
     static constexpr int64_t kGraphMaxSteps = 480;
     bool use_graphs = true;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t gtmpl = nullptr;   // the captured steps as a graph (a serving group embeds it)
     int64_t glen = 0;
     int64_t gnodes = 0;
 
@@ -412,6 +416,10 @@ struct RunT final : mithra_run {
         use_graphs = !(no_graph && no_graph[0] == '1');
         const char* no_tma = std::getenv("MITHRA_NO_TMA");
         if (!(no_tma && no_tma[0] == '1')) tma = make_tma_maps<real>(pot, src, g);
+        // failure tests: MITHRA_TEST_TMA_SKIP_PLANE=p makes every TMA stencil block leave its p-th
+        // plane uncopied, so that its bounded wait expires and mithra_sync reports ETIMEDOUT
+        const char* skip = std::getenv("MITHRA_TEST_TMA_SKIP_PLANE");
+        test_tma_skip = (skip && skip[0] >= '0' && skip[0] <= '9') ? std::atoi(skip) : -1;
         murc = mur_face_coef(g, mur_order);
         int rc = full_box(nstep % 2);
         if (rc) return rc;
@@ -597,7 +605,8 @@ struct RunT final : mithra_run {
         if (tma) {
             real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
             real* prevp[4] = {pot[lev(0)][0], pot[lev(0)][1], pot[lev(0)][2], pot[lev(0)][3]};
-            CU(launch_stencil_tma<real>(tma, outp, prevp, &murc, lev(1), lev(0), g, cf, ncomp, err_word, stream));
+            CU(launch_stencil_tma<real>(tma, outp, prevp, &murc, lev(1), lev(0), g, cf, ncomp, err_word, stream,
+                                        test_tma_skip));
         } else {
             CU(launch_stencil<real>(L, g, cf, ncomp, stream));
         }
@@ -674,9 +683,28 @@ struct RunT final : mithra_run {
     void graph_reset()
     {
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (gtmpl) cudaGraphDestroy(gtmpl);
         gexec = nullptr;
+        gtmpl = nullptr;
         glen = 0;
         gnodes = 0;
+    }
+
+    // The captured period as a graph, when the next steps are exactly one replay of it: at an
+    // aligned step with at least a period left, and with room in the series for it (growing the
+    // series re-captures).  The caller launches it (inside a graph of its own) and then calls
+    // period_replayed().
+    cudaGraph_t period_graph(int64_t steps_left) override
+    {
+        const int64_t L = graph_steps();
+        if (L <= 0 || !gexec || !gtmpl || glen != L || nstep < L || nstep % L != 0 || steps_left < L) return nullptr;
+        if (grow_series(nstep + L) != MITHRA_OK) return nullptr;
+        return gexec ? gtmpl : nullptr;
+    }
+    void period_replayed() override
+    {
+        nstep += glen;
+        count_launches(gnodes);
     }
 
     // Capture the L steps from an aligned step (a multiple of L, after the first period) into a
@@ -703,11 +731,12 @@ struct RunT final : mithra_run {
             return fail(MITHRA_ECUDA, "graph capture: the step state is not periodic");
         }
         e = cudaGraphInstantiate(&gexec, gr, 0);
-        cudaGraphDestroy(gr);
         if (e != cudaSuccess) {
+            cudaGraphDestroy(gr);
             gexec = nullptr;
             return fail(MITHRA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
         }
+        gtmpl = gr;
         glen = L;
         gnodes = launch_count() - l0;
         CU(cudaGraphLaunch(gexec, stream));
@@ -1261,6 +1290,13 @@ int64_t mithra::graph_steps(mithra_t r, int64_t* nstep)
 {
     if (nstep) *nstep = r ? r->nstep : 0;
     return r ? r->graph_steps() : 0;
+}
+
+cudaGraph_t mithra::period_graph(mithra_t r, int64_t steps_left) { return r ? r->period_graph(steps_left) : nullptr; }
+
+void mithra::period_replayed(mithra_t r)
+{
+    if (r) r->period_replayed();
 }
 
 int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, const mithra_bunch* b, int64_t nsteps)

@@ -3,6 +3,8 @@
 
 #include <stdint.h>
 
+#include <cuda_runtime.h>
+
 #include "../../include/mithra.h"
 
 namespace mithra {
@@ -19,5 +21,10 @@ int64_t footprint(const mithra_grid* gr, const mithra_undulator* u, const mithra
 // Steps of the run's captured graph (0: steps are launched one by one) and the steps enqueued so
 // far; a call of exactly that many steps from a multiple of it (after the first) is one replay.
 int64_t graph_steps(mithra_t r, int64_t* nstep);
+// The run's captured period when its next steps are exactly one replay of it (null otherwise); the
+// caller launches it - a serving group embeds it in one graph with other runs' periods - and then
+// reports the replay with period_replayed (the host side advances by the period).
+cudaGraph_t period_graph(mithra_t r, int64_t steps_left);
+void period_replayed(mithra_t r);
 
 }  // namespace mithra

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -124,6 +125,11 @@ struct Server {
     mithra_free_fn block_free = nullptr;
     void* block_ctx = nullptr;
     int max_active = 8, queue_cap = 256, chunk = 16;
+    bool grouped = false;                 // one graph launch advances every ready request by its period
+    cudaStream_t gstream = nullptr;       // the group launches
+    cudaGraphExec_t gexec = nullptr;      // the group of the last launch (rebuilt when it changes)
+    std::vector<uintptr_t> gkey;          // its members: ticket and period graph of each
+    std::atomic<int64_t> group_launches{0}, group_periods{0};
     int64_t reserved = 0;
     std::mutex mu;
     std::condition_variable cv;
@@ -142,7 +148,83 @@ struct Server {
     }
     void loop();
     void finish(const std::shared_ptr<Request>& r, int status, const char* msg);
+    bool launch_group(const std::vector<std::shared_ptr<Request>>& ready, const std::vector<cudaGraph_t>& graphs);
 };
+
+// One launch of the ready requests' periods: a graph whose child graphs are the periods (each
+// request's own captured steps, on its own buffers), rebuilt only when the members or their
+// periods change.  The group stream first waits for every member's stream, and every member's
+// stream then waits for the group, so the order of each request's steps is kept.
+bool Server::launch_group(const std::vector<std::shared_ptr<Request>>& ready, const std::vector<cudaGraph_t>& graphs)
+{
+    if (!gstream && cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking) != cudaSuccess) {
+        gstream = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    std::vector<uintptr_t> key;
+    for (size_t i = 0; i < ready.size(); ++i) {
+        key.push_back((uintptr_t)ready[i]->ticket);
+        key.push_back((uintptr_t)graphs[i]);
+    }
+    if (key != gkey || !gexec) {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gkey.clear();
+        cudaGraph_t G = nullptr;
+        if (cudaGraphCreate(&G, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        bool ok = true;
+        for (cudaGraph_t c : graphs) {
+            cudaGraphNode_t node;
+            if (cudaGraphAddChildGraphNode(&node, G, nullptr, 0, c) != cudaSuccess) {
+                ok = false;
+                break;
+            }
+        }
+        if (ok && cudaGraphInstantiate(&gexec, G, 0) != cudaSuccess) {
+            gexec = nullptr;
+            ok = false;
+        }
+        cudaGraphDestroy(G);
+        if (!ok) {
+            cudaGetLastError();
+            return false;
+        }
+        gkey = key;
+    }
+    for (auto& r : ready) {
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        cudaEventRecord(e, r->stream);
+        cudaStreamWaitEvent(gstream, e, 0);
+        cudaEventDestroy(e);
+    }
+    if (cudaGraphLaunch(gexec, gstream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaEvent_t g_done;
+    cudaEventCreateWithFlags(&g_done, cudaEventDisableTiming);
+    cudaEventRecord(g_done, gstream);
+    for (auto& r : ready) {
+        cudaStreamWaitEvent(r->stream, g_done, 0);
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        cudaEventRecord(e, r->stream);
+        r->inflight.push_back(e);
+        int64_t at = 0;
+        const int64_t L = mithra::graph_steps(r->run, &at);
+        mithra::period_replayed(r->run);
+        r->enqueued += L;
+    }
+    cudaEventDestroy(g_done);
+    ++group_launches;
+    group_periods += (int64_t)ready.size();
+    return true;
+}
 
 std::mutex g_srv_mu;
 Server* g_srv = nullptr;
@@ -243,6 +325,34 @@ void Server::loop()
                 r->inflight.pop_front();
                 progress = true;
             }
+        }
+        // grouped: the requests whose next steps are one replay of their captured period advance
+        // together, their periods being the child graphs of one graph and one launch.  A ready
+        // request that still has a period in flight waits for partners; one with nothing in
+        // flight goes at once (with whoever is ready, or alone on its own stream).
+        std::vector<Request*> in_group;
+        if (grouped) {
+            std::vector<std::shared_ptr<Request>> ready;
+            std::vector<cudaGraph_t> graphs;
+            bool must_go = false;
+            for (auto& r : active) {
+                if (r->status != MITHRA_OK || r->enqueued >= r->nsteps || r->inflight.size() >= 2) continue;
+                cudaGraph_t gr = mithra::period_graph(r->run, r->nsteps - r->enqueued);
+                if (gr) {
+                    ready.push_back(r);
+                    graphs.push_back(gr);
+                    must_go = must_go || r->inflight.empty();
+                }
+            }
+            if (ready.size() >= 2 && launch_group(ready, graphs)) {
+                for (auto& r : ready) in_group.push_back(r.get());
+                progress = true;
+            } else if (ready.size() == 1 && !must_go) {
+                in_group.push_back(ready[0].get());   // waits this round
+            }
+        }
+        for (auto& r : active) {
+            if (std::find(in_group.begin(), in_group.end(), r.get()) != in_group.end()) continue;
             if (r->enqueued < r->nsteps && r->inflight.size() < 2) {
                 // chunks end on the run's graph boundaries, and a whole graph period from a
                 // boundary goes as one replay
@@ -277,8 +387,13 @@ void Server::loop()
         if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(100));
     }
     // stopping: drop what is still on the device
+    if (gstream) cudaStreamSynchronize(gstream);
     for (auto& r : active) finish(r, MITHRA_ETIMEDOUT, "server stopped before the request finished");
     active.clear();
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    if (gstream) cudaStreamDestroy(gstream);
+    gstream = nullptr;
     std::lock_guard<std::mutex> lk(mu);
     for (auto& r : queue) {
         r->state = DONE;
@@ -292,6 +407,12 @@ void Server::loop()
 
 extern "C" int mithra_serve_start(size_t hbm_budget_bytes, int max_active, int queue_capacity, int steps_per_chunk)
 {
+    return mithra_serve_start_grouped(hbm_budget_bytes, max_active, queue_capacity, steps_per_chunk, 0);
+}
+
+extern "C" int mithra_serve_start_grouped(size_t hbm_budget_bytes, int max_active, int queue_capacity,
+                                          int steps_per_chunk, int grouped)
+{
     std::lock_guard<std::mutex> lk(g_srv_mu);
     if (g_srv) return set_last_error(MITHRA_EINVAL, "serve_start: already running");
     if (hbm_budget_bytes < (1u << 20)) return set_last_error(MITHRA_EINVAL, "serve_start: budget below 1 MiB");
@@ -302,6 +423,7 @@ extern "C" int mithra_serve_start(size_t hbm_budget_bytes, int max_active, int q
     s->max_active = max_active;
     s->queue_cap = queue_capacity;
     s->chunk = steps_per_chunk;
+    s->grouped = grouped != 0;
     // the pool comes from the installed allocator (cudaMalloc when none), on the caller's thread
     mithra_alloc_fn a = nullptr;
     mithra_free_fn f = nullptr;
@@ -440,6 +562,15 @@ extern "C" int mithra_serve_stats(int64_t stats[6])
         stats[4] = (int64_t)g_srv->pool.in_use;
         stats[5] = (int64_t)g_srv->pool.peak;
     }
+    return MITHRA_OK;
+}
+
+extern "C" int mithra_serve_group_stats(int64_t out[2])
+{
+    std::lock_guard<std::mutex> lk(g_srv_mu);
+    if (!g_srv) return set_last_error(MITHRA_EINVAL, "serve_group_stats: the server is not running");
+    out[0] = g_srv->group_launches.load();
+    out[1] = g_srv->group_periods.load();
     return MITHRA_OK;
 }
 
