@@ -388,8 +388,19 @@ struct Fields4 {
     real* c[4];
 };
 
+// E and B at the nodes, interleaved per node: E_x, E_y, E_z, B_x, B_y, B_z and two unused entries,
+// eight values per node (32 B in FP32, 64 B in FP64), so that the six components of a node are
+// read with two (FP32) or four (FP64) 16-byte loads.
+constexpr int kEBStride = 8;
 template <typename real>
 struct Fields6 {
+    real* p;
+    __host__ __device__ real& at(int c, int64_t id) const { return p[id * kEBStride + c]; }
+};
+
+// Six separate arrays of E_x .. B_z (the allocation-free energy's caller arrays).
+template <typename real>
+struct Fields6Soa {
     real* c[6];
 };
 

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(kRedThreads) k_power_step(Fields6<real> eb, Ge
     double contrib = 0.0;
     if (pl < plane) {
         const int64_t id = (int64_t)ps.kp * g.sz + pl;
-        if (id == ps.onaxis_id) ps.onaxis_series[sd.n] = (double)eb.c[0][id];
-        const double x[4] = {(double)eb.c[0][id], (double)eb.c[1][id], (double)eb.c[3][id], (double)eb.c[4][id]};
+        if (id == ps.onaxis_id) ps.onaxis_series[sd.n] = (double)eb.at(0, id);
+        const double x[4] = {(double)eb.at(0, id), (double)eb.at(1, id), (double)eb.at(3, id), (double)eb.at(4, id)};
         double* r = ps.ring + (int64_t)sd.slot * 4 * plane + pl;
         double re[4], im[4];
 #pragma unroll
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(Fields6<real> eb, int64_
         double e2 = 0.0, b2 = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double e = (double)eb.c[c][t], b = (double)eb.c[3 + c][t];
+            const double e = (double)eb.at(c, t), b = (double)eb.at(3 + c, t);
             e2 += e * e;
             b2 += b * b;
         }
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kRedThreads) k_spec_step(Fields6<real> eb, Geo
     double contrib = 0.0;
     if (pl < plane) {
         const int64_t id = (int64_t)s.kp * g.sz + pl;
-        const double x[4] = {(double)eb.c[0][id], (double)eb.c[1][id], (double)eb.c[3][id], (double)eb.c[4][id]};
+        const double x[4] = {(double)eb.at(0, id), (double)eb.at(1, id), (double)eb.at(3, id), (double)eb.at(4, id)};
         const double cn = ph[0], sn = ph[1], co = ph[2], so = ph[3];
         const double* ro = s.ring + (full ? (int64_t)((n - Mk) % s.Mh) : 0) * 4 * plane + pl;
         double* ac = s.acc + (int64_t)k * 8 * plane + pl;
@@ -262,10 +262,10 @@ __global__ void k_spec_ring(Fields6<real> eb, Geom g, SpecStep s)
     if (pl >= plane) return;
     const int64_t id = (int64_t)s.kp * g.sz + pl;
     double* r = s.ring + (int64_t)(s.sd->n % s.Mh) * 4 * plane + pl;
-    r[0] = (double)eb.c[0][id];
-    r[plane] = (double)eb.c[1][id];
-    r[2 * plane] = (double)eb.c[3][id];
-    r[3 * plane] = (double)eb.c[4][id];
+    r[0] = (double)eb.at(0, id);
+    r[plane] = (double)eb.at(1, id);
+    r[2 * plane] = (double)eb.at(3, id);
+    r[3 * plane] = (double)eb.at(4, id);
 }
 
 // One block per frequency: compensated sum of its partials.

@@ -244,7 +244,7 @@ struct EmitArgs {
     const real* a0[3];   // A^n
     const real* a1[3];   // A^{n+1}
     const real* phi;     // phi^n (node), may be null when space charge is off
-    real* eb[6];
+    real* eb;            // E, B interleaved (kEBStride values per node)
     real* src[4];        // sources to clear inside the box (entries may be null)
     // E from pair sums of the staggered values (0.5 / dt: the node average's 1/2 folded in), the
     // gradient of phi (0.5 / d), B from sums of two pair sums (0.125 / d: the averages' 1/2 and
@@ -482,12 +482,17 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
             const real by = (sxp - sx0) * a.b2dz - byp1;
             real ezk = ez1;
             if (use_phi) ezk -= (php - ph0) * a.i2dz;
-            a.eb[0][id] = ex1;
-            a.eb[1][id] = ey1;
-            a.eb[2][id] = ezk;
-            a.eb[3][id] = bx;
-            a.eb[4][id] = by;
-            a.eb[5][id] = bz1;
+            // the node's whole slot (unused entries zero): full 32-byte sectors, no partial writes
+            real* o = a.eb + id * kEBStride;
+            if constexpr (sizeof(real) == 4) {
+                *reinterpret_cast<float4*>(o) = make_float4(ex1, ey1, ezk, bx);
+                *reinterpret_cast<float4*>(o + 4) = make_float4(by, bz1, 0.f, 0.f);
+            } else {
+                *reinterpret_cast<double2*>(o) = make_double2(ex1, ey1);
+                *reinterpret_cast<double2*>(o + 2) = make_double2(ezk, bx);
+                *reinterpret_cast<double2*>(o + 4) = make_double2(by, bz1);
+                *reinterpret_cast<double2*>(o + 6) = make_double2(0.0, 0.0);
+            }
             if (clear) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
@@ -702,7 +707,7 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
         a.a1[c] = L.n1[c];
     }
     a.phi = g.space_charge ? L.n0[3] : nullptr;
-    for (int c = 0; c < 6; ++c) a.eb[c] = eb.c[c];
+    a.eb = eb.p;
     for (int c = 0; c < 4; ++c) a.src[c] = (bx.box && bx.clear) ? (real*)L.src[c] : nullptr;
     if (!g.space_charge) a.src[3] = nullptr;
     a.hdt = (real)(1.0 / g.dt) * (real)0.5;

@@ -220,7 +220,7 @@ struct RunT final : mithra_run {
     real* pot[3][4] = {};      // ring of three time levels of A_x, A_y, A_z, phi
     int base = 0;              // pot[(base + 0) % 3] = level n, (base + 1) % 3 = level n+1
     real* src[4] = {};
-    real* eb[6] = {};
+    real* eb = nullptr;   // E, B at the nodes, interleaved (Fields6)
     Particles<real> P{}, T{};
     SortScratch ss{};
     double* ring = nullptr;
@@ -294,7 +294,7 @@ struct RunT final : mithra_run {
             L.src[c] = src[c];
         }
         Fields6<real> E6;
-        for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
+        E6.p = eb;
         EmitBox bx{nullptr, nullptr, -1, false};
         EmitMaps em;
         if (emit_maps(tma, lev(2), lev(0), &em)) bx.maps = &em;
@@ -311,12 +311,11 @@ struct RunT final : mithra_run {
                 if (!(pot[l][c] = (real*)mem.get(cell))) return fail(MITHRA_ENOMEM, "device allocation failed (fields)");
         for (int c = 0; c < 4; ++c)
             if (!(src[c] = (real*)mem.get(cell))) return fail(MITHRA_ENOMEM, "device allocation failed (sources)");
-        for (int c = 0; c < 6; ++c)
-            if (!(eb[c] = (real*)mem.get(cell))) return fail(MITHRA_ENOMEM, "device allocation failed (E/B)");
+        if (!(eb = (real*)mem.get(cell * kEBStride))) return fail(MITHRA_ENOMEM, "device allocation failed (E/B)");
         for (int l = 0; l < 3; ++l)
             for (int c = 0; c < 4; ++c) CU(cudaMemsetAsync(pot[l][c], 0, cell, stream));
         for (int c = 0; c < 4; ++c) CU(cudaMemsetAsync(src[c], 0, cell, stream));
-        for (int c = 0; c < 6; ++c) CU(cudaMemsetAsync(eb[c], 0, cell, stream));
+        CU(cudaMemsetAsync(eb, 0, cell * kEBStride, stream));
         const int64_t n = np > 0 ? np : 1;
         for (Particles<real>* Q : {&P, &T}) {
             Q->ix = (int32_t*)mem.get(n * 4);
@@ -507,7 +506,7 @@ struct RunT final : mithra_run {
     {
         const int ncomp = g.space_charge ? 4 : 3;
         Fields6<real> E6;
-        for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
+        E6.p = eb;
         Fields4<real> S4;
         for (int c = 0; c < 4; ++c) S4.c[c] = src[c];
         int rc = MITHRA_OK;
@@ -775,7 +774,7 @@ struct RunT final : mithra_run {
     {
         if (which < 4) return pot[lev(level)][which];
         if (which < 8) return src[which - 4];
-        return eb[which - 8];
+        return eb;   // interleaved: component which - 8 of every kEBStride values
     }
 
     int fields(int which, int level, double* out, size_t cap) override
@@ -785,6 +784,15 @@ struct RunT final : mithra_run {
         if (which >= 8) {
             const int rc = emit_full();
             if (rc) return rc;
+        }
+        if (which >= 8) {
+            // E, B: a strided device-to-host copy of one component of the interleaved array
+            std::vector<real> h((size_t)g.ncell);
+            CU(cudaMemcpy2DAsync(h.data(), sizeof(real), eb + (which - 8), kEBStride * sizeof(real), sizeof(real),
+                                 (size_t)g.ncell, cudaMemcpyDeviceToHost, stream));
+            CU(cudaStreamSynchronize(stream));
+            for (int64_t i = 0; i < g.ncell; ++i) out[i] = (double)h[(size_t)i];
+            return MITHRA_OK;
         }
         std::vector<real> h((size_t)g.ncell);
         CU(cudaMemcpyAsync(h.data(), field_ptr(which, level), (size_t)g.ncell * sizeof(real), cudaMemcpyDeviceToHost,
@@ -839,7 +847,7 @@ struct RunT final : mithra_run {
     int diag(double* fe, double* b3) override
     {
         Fields6<real> E6;
-        for (int c = 0; c < 6; ++c) E6.c[c] = eb[c];
+        E6.p = eb;
         double h[4] = {0, 0, 0, 0};
         if (fe) {
             const int rc = emit_full();

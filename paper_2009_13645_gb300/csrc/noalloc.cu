@@ -53,7 +53,7 @@ __device__ __forceinline__ double block_total(double v)
 
 // One block per tile: electric plus magnetic energy density summed over kTileNodes nodes.
 template <typename real>
-__global__ void __launch_bounds__(kThreads) k_energy_tiles(mithra::Fields6<real> eb, int64_t n, double* partial)
+__global__ void __launch_bounds__(kThreads) k_energy_tiles(mithra::Fields6Soa<real> eb, int64_t n, double* partial)
 {
     constexpr double eps0 = 1.0 / (mithra::kMu0 * mithra::kC * mithra::kC);
     const int64_t base = (int64_t)blockIdx.x * kTileNodes;
@@ -126,11 +126,11 @@ extern "C" int mithra_field_energy_noalloc(const void* const eb[6], int precisio
     const int64_t ntiles = (n + kTileNodes - 1) / kTileNodes;
     if (ntiles > 0) {
         if (precision == 0) {
-            mithra::Fields6<double> f;
+            mithra::Fields6Soa<double> f;
             for (int c = 0; c < 6; ++c) f.c[c] = (double*)eb[c];
             k_energy_tiles<double><<<(unsigned)ntiles, kThreads, 0, st>>>(f, n, partial);
         } else {
-            mithra::Fields6<float> f;
+            mithra::Fields6Soa<float> f;
             for (int c = 0; c < 6; ++c) f.c[c] = (float*)eb[c];
             k_energy_tiles<float><<<(unsigned)ntiles, kThreads, 0, st>>>(f, n, partial);
         }

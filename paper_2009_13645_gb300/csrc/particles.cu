@@ -568,9 +568,20 @@ __device__ __forceinline__ bool push_one(int m, const int ci[3], const real f[3]
 #pragma unroll
                 for (int I = 0; I < 2; ++I) {
                     const real w = wx[I] * wy[J] * wz[K];
-                    const int64_t id = o + K * g.sz + J * g.sy + I;
+                    const real* q = eb.p + (o + K * g.sz + J * g.sy + I) * kEBStride;
+                    real v[6];
+                    if constexpr (sizeof(real) == 4) {
+                        const float4 a = __ldg(reinterpret_cast<const float4*>(q));
+                        const float2 b = __ldg(reinterpret_cast<const float2*>(q + 4));
+                        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y;
+                    } else {
+                        const double2 a = __ldg(reinterpret_cast<const double2*>(q));
+                        const double2 b = __ldg(reinterpret_cast<const double2*>(q + 2));
+                        const double2 c = __ldg(reinterpret_cast<const double2*>(q + 4));
+                        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y, v[4] = c.x, v[5] = c.y;
+                    }
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) s[c] += w * __ldg(eb.c[c] + id);
+                    for (int c = 0; c < 6; ++c) s[c] += w * v[c];
                 }
     }
     real ig;
