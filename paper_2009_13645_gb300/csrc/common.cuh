@@ -336,7 +336,55 @@ __device__ __forceinline__ bool last_block(unsigned* counter)
     if (last) __threadfence();
     return last;
 }
+
+// Programmatic dependent launch.  The kernels of a step are launched with programmatic stream
+// serialisation (launch_dep): a kernel's blocks may become resident while the previous kernel
+// of the stream is still finishing its last blocks, which hides the launch and ramp-up of every
+// kernel boundary.  Each such kernel calls dep_begin() first, in every block, before it reads
+// or writes device memory: it lets its own successor launch, then waits until its predecessor
+// has completed and that kernel's writes are visible.  Launched the ordinary way, the wait is
+// a no-op.
+__device__ __forceinline__ void dep_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 #endif
+
+#ifndef MITHRA_DEP_LAUNCH
+#define MITHRA_DEP_LAUNCH 1
+#endif
+
+// Whether a step kernel of precision `real` is launched as a programmatic dependent on stream
+// st: on the FP32-mixed path when launched directly.  Steps captured into a graph already start
+// back to back, and there waiting blocks of the small kernels (phase table, Mur, power) made a
+// replayed period slower; the FP64 path was slower with it in both modes.
+template <typename real>
+inline bool dep_launch_on(cudaStream_t st)
+{
+    if (!MITHRA_DEP_LAUNCH || sizeof(real) != 4) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
+// Launch kernel k, with programmatic stream serialisation when dep is set (k calls dep_begin()
+// first in every block).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(bool dep, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = dep ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // Stored momentum gamma*beta.  FP64 path: a double.  FP32-mixed path: an unevaluated sum of two
 // floats (hi, lo) with hi the float nearest to hi + lo, about 48 significant bits: the momentum

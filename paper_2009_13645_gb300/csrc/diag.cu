@@ -52,6 +52,7 @@ template <typename real>
 __global__ void __launch_bounds__(kRedThreads) k_power_step(Fields6<real> eb, Geom g, PowerStep ps,
                                                             double* __restrict__ partial)
 {
+    dep_begin();
     __shared__ double sh[32];
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,7 +114,11 @@ cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const Powe
     PowerStep p = ps;
     p.scale = scale;
     p.series = series;
-    k_power_step<real><<<nb, kRedThreads, 0, st>>>(eb, g, p, partial);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_power_step<real>, dim3(nb), dim3(kRedThreads), 0,
+                                          st, eb, g, p, partial);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -210,6 +215,7 @@ template <typename real>
 __global__ void __launch_bounds__(kRedThreads) k_spec_step(Fields6<real> eb, Geom g, SpecStep s,
                                                            double* __restrict__ partial)
 {
+    dep_begin();
     __shared__ double sh[32];
     __shared__ double ph[4];
     const int k = blockIdx.y;
@@ -257,6 +263,7 @@ __global__ void __launch_bounds__(kRedThreads) k_spec_step(Fields6<real> eb, Geo
 template <typename real>
 __global__ void k_spec_ring(Fields6<real> eb, Geom g, SpecStep s)
 {
+    dep_begin();
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pl >= plane) return;
@@ -271,6 +278,7 @@ __global__ void k_spec_ring(Fields6<real> eb, Geom g, SpecStep s)
 // One block per frequency: compensated sum of its partials.
 __global__ void k_spec_final(const double* __restrict__ partial, int npartial, SpecStep s, double* __restrict__ series)
 {
+    dep_begin();
     __shared__ double sh[32];
     const int k = blockIdx.x;
     const int64_t n = s.sd->n;
@@ -292,9 +300,21 @@ cudaError_t launch_spectrum_step(const Fields6<real>& eb, const Geom& g, const S
     const int64_t plane = (int64_t)g.nx * g.ny;
     const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
     if ((int)nb > npartial || s.nf < 1) return cudaErrorInvalidValue;
-    k_spec_step<real><<<dim3(nb, s.nf), kRedThreads, 0, st>>>(eb, g, s, partial);
-    k_spec_ring<real><<<nb, kRedThreads, 0, st>>>(eb, g, s);
-    k_spec_final<<<s.nf, kRedThreads, 0, st>>>(partial, (int)nb, s, series);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_spec_step<real>, dim3(nb, s.nf),
+                                          dim3(kRedThreads), 0, st, eb, g, s, partial);
+        if (le != cudaSuccess) return le;
+    }
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_spec_ring<real>, dim3(nb), dim3(kRedThreads), 0,
+                                          st, eb, g, s);
+        if (le != cudaSuccess) return le;
+    }
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_spec_final, dim3(s.nf), dim3(kRedThreads), 0, st,
+                                          partial, (int)nb, s, series);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(3);
     return cudaGetLastError();
 }
@@ -308,6 +328,7 @@ template <typename real>
 __global__ void __launch_bounds__(kRedThreads) k_bunch_moments(Particles<real> P, int64_t np, Geom g, BunchSample b,
                                                                double* __restrict__ partial)
 {
+    dep_begin();
     __shared__ double sh[32];
     if (b.sd->n % b.every != 0) return;
     real s1[7], s2[7];
@@ -348,6 +369,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bunch_moments(Particles<real> P
 __global__ void k_bunch_row(const double* __restrict__ partial, int npartial, int64_t np, BunchSample b,
                             double* __restrict__ series)
 {
+    dep_begin();
     __shared__ double sh[32];
     __shared__ double tot[14];
     const int64_t n = b.sd->n;
@@ -389,8 +411,16 @@ cudaError_t launch_bunch_sample(const Particles<real>& P, int64_t np, const Geom
     if (b.every < 1) return cudaErrorInvalidValue;
     int nb = (int)std::min<int64_t>((np + kRedThreads - 1) / kRedThreads, (int64_t)npartial);
     if (nb < 1) nb = 1;
-    k_bunch_moments<real><<<nb, kRedThreads, 0, st>>>(P, np, g, b, partial);
-    k_bunch_row<<<1, kRedThreads, 0, st>>>(partial, nb, np, b, series);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_bunch_moments<real>, dim3(nb), dim3(kRedThreads),
+                                          0, st, P, np, g, b, partial);
+        if (le != cudaSuccess) return le;
+    }
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_bunch_row, dim3(1), dim3(kRedThreads), 0, st,
+                                          partial, nb, np, b, series);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(2);
     return cudaGetLastError();
 }

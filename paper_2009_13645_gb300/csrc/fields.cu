@@ -33,6 +33,7 @@ struct StencilArgs {
 template <typename real>
 __global__ void __launch_bounds__(256) k_stencil(StencilArgs<real> a, int64_t sy, int64_t sz)
 {
+    dep_begin();
     const int comp = blockIdx.z % a.ncomp;
     const int chunk = blockIdx.z / a.ncomp;
     const int ex = a.ex[comp], ey = a.ey[comp], ez = a.ez[comp];
@@ -109,6 +110,7 @@ __device__ inline int64_t lin(int i, int j, int k, int64_t sy, int64_t sz) { ret
 template <typename real>
 __global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
 {
+    dep_begin();
     const int comp = blockIdx.y;
     if (comp >= a.ncomp) return;
     const int f = a.face0 + (int)blockIdx.z;
@@ -213,6 +215,7 @@ template <typename real>
 __global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy, int64_t sz,
                                                   int64_t maxpts, unsigned* counter)
 {
+    dep_begin();
     const int comp = blockIdx.y;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (comp < a.ncomp && t < maxpts) mur_point(a, cf, sy, sz, comp, false, t);
@@ -315,6 +318,7 @@ template <typename real, bool TM>
 __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
     k_emit(EmitArgs<real> a, Geom g, const __grid_constant__ EmitMaps em)
 {
+    dep_begin();
     extern __shared__ unsigned char emit_smem_raw[];
     EmitSmem<real>& sm = *reinterpret_cast<EmitSmem<real>*>(
         emit_smem_raw + ((128 - (mithra::su32(emit_smem_raw) & 127)) & 127));
@@ -550,7 +554,11 @@ cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const Sten
     const dim3 blk(32, 8);
     const int nchunk = (g.nz - 2 + a.kchunk - 1) / a.kchunk;
     const dim3 grd((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, nchunk * ncomp);
-    k_stencil<real><<<grd, blk, 0, st>>>(a, g.sy, g.sz);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_stencil<real>, dim3(grd), dim3(blk), 0, st, a,
+                                          g.sy, g.sz);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -653,13 +661,22 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
             }
         }
         const int thr = 256;
-        k_mur_faces<real>
-            <<<dim3((unsigned)((maxface + thr - 1) / thr), ncomp, 6 - a.face0), thr, 0, st>>>(a, g.sy, g.sz);
+        {
+            const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_mur_faces<real>,
+                                              dim3((unsigned)((maxface + thr - 1) / thr), ncomp, 6 - a.face0),
+                                              dim3(thr), 0, st, a, g.sy, g.sz);
+            if (le != cudaSuccess) return le;
+        }
         ++nl;
     }
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
     const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
-    k_mur_edges<real><<<dim3((unsigned)((edges + 63) / 64), ncomp), 64, 0, st>>>(a, ec, g.sy, g.sz, edges, counter);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_mur_edges<real>,
+                                          dim3((unsigned)((edges + 63) / 64), ncomp), dim3(64), 0, st, a, ec, g.sy,
+                                          g.sz, edges, counter);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(nl + 1);
     return cudaGetLastError();
 }
@@ -689,7 +706,11 @@ cudaError_t launch_mur_tfsf_xfaces(const FieldLevels<real>& L, const Geom& g, in
         a.ft[ax][1] = (real)m.ft[ax][1];
     }
     const int64_t pts = 2 * (int64_t)g.ny;
-    k_mur_faces<real><<<dim3((unsigned)((pts + 127) / 128), 2, 2), 128, 0, st>>>(a, g.sy, g.sz);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_mur_faces<real>,
+                                          dim3((unsigned)((pts + 127) / 128), 2, 2), dim3(128), 0, st, a, g.sy, g.sz);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -732,7 +753,11 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
         static const cudaError_t attr =
             cudaFuncSetAttribute(k_emit<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (attr != cudaSuccess) return attr;
-        k_emit<real, true><<<grd, ENT, smem, st>>>(a, g, *bx.maps);
+        {
+            const cudaError_t le = launch_dep(dep_launch_on<real>(st), (k_emit<real, true>), dim3(grd), dim3(ENT),
+                                              smem, st, a, g, *bx.maps);
+            if (le != cudaSuccess) return le;
+        }
     } else {
         const dim3 grd((g.nx - 2 + EX - 1) / EX, (g.ny - 2 + EY - 1) / EY, a.nchunk + (a.kp >= 1 ? 1 : 0));
         static const cudaError_t attr =
@@ -740,7 +765,11 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
         if (attr != cudaSuccess) return attr;
         EmitMaps none;
         memset(&none, 0, sizeof none);
-        k_emit<real, false><<<grd, ENT, smem, st>>>(a, g, none);
+        {
+            const cudaError_t le = launch_dep(dep_launch_on<real>(st), (k_emit<real, false>), dim3(grd), dim3(ENT),
+                                              smem, st, a, g, none);
+            if (le != cudaSuccess) return le;
+        }
     }
     count_launches(1);
     return cudaGetLastError();
@@ -753,6 +782,7 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
 // (i, j) of z planes 1 and 2: fbuf[((c * 2 + plane - 1) * ny + j) * nx + i].
 __global__ void k_seed_eval(SeedField s, Geom g, const StepDev* sd, double T0, double* __restrict__ fbuf)
 {
+    dep_begin();
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= 2 * plane) return;
@@ -778,6 +808,7 @@ struct TfsfArgs {
 template <typename real>
 __global__ void k_tfsf(TfsfArgs<real> a, Geom g, const double* __restrict__ fbuf)
 {
+    dep_begin();
     const int c = blockIdx.y;
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -800,7 +831,12 @@ cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf
                         const StepDev* sd, double T0, double* fbuf, cudaStream_t st)
 {
     const int64_t plane = (int64_t)g.nx * g.ny;
-    k_seed_eval<<<(unsigned)((2 * plane + 127) / 128), 128, 0, st>>>(s, g, sd, T0, fbuf);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_seed_eval,
+                                          dim3((unsigned)((2 * plane + 127) / 128)), dim3(128), 0, st, s, g, sd, T0,
+                                          fbuf);
+        if (le != cudaSuccess) return le;
+    }
     TfsfArgs<real> a;
     for (int c = 0; c < 2; ++c) {
         a.out[c] = out[c];
@@ -811,7 +847,11 @@ cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf
     a.a2 = cf.ax;
     a.a4 = cf.ay;
     a.a6 = cf.a6;
-    k_tfsf<real><<<dim3((unsigned)((plane + 127) / 128), 2), 128, 0, st>>>(a, g, fbuf);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_tfsf<real>,
+                                          dim3((unsigned)((plane + 127) / 128), 2), dim3(128), 0, st, a, g, fbuf);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(2);
     return cudaGetLastError();
 }

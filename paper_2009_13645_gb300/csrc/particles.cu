@@ -270,6 +270,7 @@ __device__ __forceinline__ void optical_field_mixed(const ExtField& f, const Pus
 // {B_i, B_{i+1} (0 after the last module), 1 for the last module, 0}.
 __global__ void k_phase_table32(ExtField f, const StepDev* sd, double kz, int nz, float4* t0, float4* t1, float4* ta)
 {
+    dep_begin();
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
     if (iz >= nz) return;
     const double zn = fma(kz, (double)iz, sd->Z0);
@@ -300,13 +301,18 @@ __global__ void k_phase_table32(ExtField f, const StepDev* sd, double kz, int nz
 cudaError_t launch_phase_table32(const ExtField& ef, const StepDev* sd, double kz, int nz, float4* t0, float4* t1,
                                  float4* ta, cudaStream_t st)
 {
-    k_phase_table32<<<(nz + 127) / 128, 128, 0, st>>>(ef, sd, kz, nz, t0, t1, ta);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<float>(st), k_phase_table32, dim3((nz + 127) / 128),
+                                          dim3(128), 0, st, ef, sd, kz, nz, t0, t1, ta);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
 
 __global__ void k_phase_table(ExtField f, const StepDev* sd, double kz, int nz, double2* t0, double2* t1)
 {
+    dep_begin();
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
     if (iz >= nz) return;
     const double zn = fma(kz, (double)iz, sd->Z0);
@@ -322,7 +328,11 @@ __global__ void k_phase_table(ExtField f, const StepDev* sd, double kz, int nz, 
 cudaError_t launch_phase_table(const ExtField& ef, const StepDev* sd, double kz, int nz, double2* t0, double2* t1,
                                cudaStream_t st)
 {
-    k_phase_table<<<(nz + 127) / 128, 128, 0, st>>>(ef, sd, kz, nz, t0, t1);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<double>(st), k_phase_table, dim3((nz + 127) / 128), dim3(128),
+                                          0, st, ef, sd, kz, nz, t0, t1);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -657,6 +667,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
     k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb, Fields4<real> src, PushConst pc,
            int* box_out)
 {
+    dep_begin();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff};
     int hi[3] = {(int)0x80000000, (int)0x80000000, (int)0x80000000};
@@ -918,7 +929,11 @@ cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, con
                         cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    k_push<real><<<nblocks(np, 128), 128, 0, st>>>(P, np, g, ef, eb, src, pc, box_out);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_push<real>, dim3(nblocks(np, 128)), dim3(128), 0,
+                                          st, P, np, g, ef, eb, src, pc, box_out);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(1);
     return cudaGetLastError();
 }

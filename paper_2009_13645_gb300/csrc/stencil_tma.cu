@@ -102,6 +102,7 @@ template <typename real>
 __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_constant__ StencilMaps maps, TmaArgs<real> a,
                                                               int64_t sy, int64_t sz)
 {
+    dep_begin();
     using T = Tile<real>;
     using V2 = typename Vec2T<real>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -373,7 +374,11 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* co
         sm.body[c] = maps->body[lev_m][c];
         sm.src[c] = maps->src[c];
     }
-    k_stencil_tma<real><<<grd, TX / 2 * TY, T::SMEM, st>>>(sm, a, g.sy, g.sz);
+    {
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_stencil_tma<real>, dim3(grd), dim3(TX / 2 * TY),
+                                          T::SMEM, st, sm, a, g.sy, g.sz);
+        if (le != cudaSuccess) return le;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
