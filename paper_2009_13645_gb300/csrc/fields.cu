@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<r
 // factors 1/2 live in the difference constants);
 // the z neighbours (S_x, S_y and phi at k -+ 1) stay in registers, so plane k is finished while
 // plane k+1 is being read.  The next plane's loads are issued before the current plane is
-// computed.
+// computed, and one barrier per plane orders both the stage ring and the sums: the in-plane
+// differences of a plane's sums are taken after the next plane's barrier.
 // ---------------------------------------------------------------------------------------
 template <typename real>
 struct EmitArgs {
@@ -426,10 +427,10 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
         for (int d = 0; d < ENS - 1; ++d) issue(pfirst + d);
     }
     // per-column state: A_z at plane p-1 (own and halo position); S_x, S_y, phi at planes p-2 (0)
-    // and p-1 (1); the partial E, B of plane p-1
+    // and p-1 (1); E of plane p-1 before the z derivative of phi
     real az0m = 0, az1m = 0, haz0m = 0, haz1m = 0;
     real sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0, ph0 = 0, ph1 = 0;
-    real ex1 = 0, ey1 = 0, ez1 = 0, bz1 = 0, bxp1 = 0, byp1 = 0;
+    real ex1 = 0, ey1 = 0, ez1 = 0;
     bool ok = true;
     int p = pfirst;
     for (; p <= plast; ++p) {
@@ -445,6 +446,16 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
         }
         const real(*r)[EmitSmem<real>::RS] = sm.raw[stage(p)];
         const int b = p & 1;
+        // the in-plane differences of plane p-1's sums (B_z, and the y / x derivatives of S_z in
+        // B_x, B_y): its sums were written before this plane's barrier
+        real bz1 = 0, bxp1 = 0, byp1 = 0;
+        if (p > pfirst) {
+            const real(*S)[RN] = sm.sum[b ^ 1];
+            const int q = qo;
+            bz1 = (S[1][q + 1] - S[1][q - 1]) * a.b2dx - (S[0][q + RW] - S[0][q - RW]) * a.b2dy;
+            bxp1 = (S[2][q + RW] - S[2][q - RW]) * a.b2dy;
+            byp1 = (S[2][q + 1] - S[2][q - 1]) * a.b2dx;
+        }
         // node averages and sums of plane p at this thread's positions (A_z of the first plane
         // has no previous plane: its S_z and E_z are never read)
         const real az0 = r[4][qo], az1 = r[5][qo], php = use_phi ? r[6][qo] : (real)0;
@@ -465,8 +476,6 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
             haz0m = h0;
             haz1m = h1;
         }
-        __syncthreads();
-        const real(*S)[RN] = sm.sum[b];
         const int q = qo;
         real ex = (nx0 - nx1) * a.hdt;
         real ey = (ny0 - ny1) * a.hdt;
@@ -475,9 +484,6 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
             ex -= (r[6][q + 1] - r[6][q - 1]) * a.i2dx;
             ey -= (r[6][q + RW] - r[6][q - RW]) * a.i2dy;
         }
-        const real bz = (S[1][q + 1] - S[1][q - 1]) * a.b2dx - (S[0][q + RW] - S[0][q - RW]) * a.b2dy;
-        const real bxp = (S[2][q + RW] - S[2][q - RW]) * a.b2dy;
-        const real byp = (S[2][q + 1] - S[2][q - 1]) * a.b2dx;
         // plane k = p - 1 has its z neighbours now
         const int k = p - 1;
         if (k >= ka && emit && !(skip_xy && k >= bl[2] && k <= bh[2])) {
@@ -506,9 +512,10 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
         sx0 = sx1, sx1 = sxp;
         sy0 = sy1, sy1 = syp;
         ph0 = ph1, ph1 = php;
-        ex1 = ex, ey1 = ey, ez1 = ez, bz1 = bz, bxp1 = bxp, byp1 = byp;
-        // sum[b] is next written two planes later, after the first barrier of the next plane,
-        // which every thread reaches only once it is done with it
+        ex1 = ex, ey1 = ey, ez1 = ez;
+        // sum[b] is read in the next plane (after its barrier) and written again two planes
+        // later, after the barrier of that plane, which every thread reaches only once it is
+        // done reading it
     }
     if constexpr (TM) {
         if (!ok && t == 0) {

@@ -180,8 +180,9 @@ struct PushConst {
     // gamma0 beta0 c and gamma0
     float kugf, pwinf, egbf, gbf;
     // FP32-mixed deposit tile: fixed-point scale per source grid (2^30 / (128 |qJ_l|), 2^30 /
-    // (128 |q|)) and its inverse
+    // (128 |q|)), its inverse, and the charges in tile units (qJ_l and q times the scale)
     float tscale[4], tunit[4];
+    float qJt[3], qrhot;
     // optical undulator, FP32-mixed path: the transverse rest-frame amplitudes gamma0 (1 + beta0) E0
     // and gamma0 (1 + beta0) E0 / c (the Lorentz transform of a wave travelling along -z, evaluated in
     // FP64), E0, E0 / c, the waist, 1 / z_R, z_R and k_L, rounded to FP32

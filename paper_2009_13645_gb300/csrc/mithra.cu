@@ -566,6 +566,7 @@ struct RunT final : mithra_run {
             const double sc = qa > 0.0 ? 1073741824.0 / (128.0 * qa) : 1.0;
             pc.tscale[l] = (float)sc;
             pc.tunit[l] = (float)(1.0 / (double)pc.tscale[l]);
+            (l < 3 ? pc.qJt[l] : pc.qrhot) = (float)((l < 3 ? pc.qJ[l] : pc.qrho) * (double)pc.tscale[l]);
         }
         pc.eB0f = (float)(ef.g0 * ef.b0 * kC * ef.B0);
         pc.bB0f = (float)(ef.g0 * ef.B0);

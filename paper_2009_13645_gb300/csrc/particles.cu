@@ -461,6 +461,88 @@ __device__ __forceinline__ void deposit_rho(const int c[3], const real fo[3], re
             for (int I = 0; I < 2; ++I) T.add(3, o + K * T.sz + J * T.sy + I, q * wx[I] * wy[J] * wz[K]);
 }
 
+// The FP32-mixed deposit tile as the tile path of the push addresses it: the shared-window byte
+// address of entry 0 of each source grid in this lane's copy, and the tile's pitches.
+struct TileQ {
+    unsigned cb[4];
+    int sy, sz;
+};
+
+__device__ __forceinline__ void tile_red(unsigned a, float v)
+{
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(__float2int_rn(v)) : "memory");
+}
+
+// deposit_piece on the tile: one straight piece starting at la (relative to its cell, whose tile
+// entry is o) with extent d; qs = the charges qJ_l in tile units.
+__device__ __forceinline__ void tile_piece(const float la[3], const float d[3], int o, const TileQ& T,
+                                           const float qs[3])
+{
+    const int st[3] = {1, T.sy, T.sz};
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        if (d[l] == 0.f) continue;
+        const int m = (l + 1) % 3, n = (l + 2) % 3;
+        const float F = qs[l] * d[l];
+        const float cross = d[m] * d[n] * (1.f / 12.f);
+        const float wm1 = la[m] + 0.5f * d[m], wm0 = 1.f - wm1;
+        const float wn1 = la[n] + 0.5f * d[n], wn0 = 1.f - wn1;
+        const unsigned a0 = T.cb[l] + 4u * (unsigned)o;
+        const unsigned am = 4u * (unsigned)st[m], an = 4u * (unsigned)st[n];
+        tile_red(a0, F * (wm0 * wn0 + cross));
+        tile_red(a0 + am, F * (wm1 * wn0 - cross));
+        tile_red(a0 + an, F * (wm0 * wn1 - cross));
+        tile_red(a0 + am + an, F * (wm1 * wn1 + cross));
+    }
+}
+
+// The zigzag of a move from offset f of its cell (f in [0, 1), tile entry o) to b (cell units
+// relative to that cell, b in [-1, 2)) on the tile, and with rho the charge at the end point
+// (offset nf of the end cell): the currents of zigzag() and deposit_rho().  The start cell is
+// the piece's base cell, so the cell indices need no floor: the end cell is -1, 0 or +1 per axis.
+__device__ __forceinline__ void tile_move(const float f[3], const float b[3], const float nf[3], bool rho, int o,
+                                          const TileQ& T, const float qs[3], float qr)
+{
+    float c2[3], R[3], E1[3], d1[3];
+    bool cr = false;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        c2[l] = b[l] >= 1.f ? 1.f : (b[l] < 0.f ? -1.f : 0.f);
+        const float mid = 0.5f * (f[l] + b[l]);
+        R[l] = fminf(fminf(0.f, c2[l]) + 1.f, fmaxf(fmaxf(0.f, c2[l]), mid));
+        cr = cr || c2[l] != 0.f;
+    }
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        E1[l] = cr ? R[l] : b[l];
+        d1[l] = E1[l] - f[l];
+    }
+    tile_piece(f, d1, o, T, qs);
+    const int o2 = o + (int)c2[0] + (int)c2[1] * T.sy + (int)c2[2] * T.sz;
+    if (cr) {
+        float la[3], d2[3];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            la[l] = R[l] - c2[l];
+            d2[l] = b[l] - R[l];
+        }
+        tile_piece(la, d2, o2, T, qs);
+    }
+    if (rho) {
+        const float wx0 = 1.f - nf[0], wy[2] = {1.f - nf[1], nf[1]}, wz[2] = {1.f - nf[2], nf[2]};
+        const unsigned a0 = T.cb[3] + 4u * (unsigned)o2;
+#pragma unroll
+        for (int K = 0; K < 2; ++K)
+#pragma unroll
+            for (int J = 0; J < 2; ++J) {
+                const float w = qr * wz[K] * wy[J];
+                const unsigned a = a0 + 4u * (unsigned)(K * T.sz + J * T.sy);
+                tile_red(a, w * wx0);
+                tile_red(a + 4u, w * nf[0]);
+            }
+    }
+}
+
 // Block-wide bounding box of [lo, hi] (inclusive node ranges; empty when lo > hi), returned to
 // every thread.  Two barriers.
 __device__ __forceinline__ void block_box(const int lo[3], const int hi[3], int out[6])
@@ -772,23 +854,16 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 // most one cell) and at most |q| to a node of rho, so a block of 128 sums to at most
                 // 128 |qJ_l| (128 |q|): that maps to 2^30, and the rounding of each term adds at
                 // most 1/2.
-                TileTarget T;
-                T.t = tile;
-                T.base = (unsigned)__cvta_generic_to_shared(tile) + 4u * (unsigned)cs * (threadIdx.x & ((1u << lc) - 1u));
-                T.sh = 2;
-                T.vol = vol;
+                TileQ T;
+                const unsigned tb = (unsigned)__cvta_generic_to_shared(tile) + 4u * (unsigned)cs * (threadIdx.x & ((1u << lc) - 1u));
+#pragma unroll
+                for (int c = 0; c < 4; ++c) T.cb[c] = tb + 4u * (unsigned)(c * vol);
                 T.sy = tx;
                 T.sz = tx * ty;
-                T.ox = bx0;
-                T.oy = box[1];
-                T.oz = box[2];
-                T.scale[0] = pc.tscale[0];
-                T.scale[1] = pc.tscale[1];
-                T.scale[2] = pc.tscale[2];
-                T.scale[3] = pc.tscale[3];
                 if (simple) {
-                    zigzag(f, b, ci, T, qJ);
-                    if (rho_t) deposit_rho(nc, nf, q, T);
+                    const float qs[3] = {pc.qJt[0], pc.qJt[1], pc.qJt[2]};
+                    const int o = (ci[2] - box[2]) * T.sz + (ci[1] - box[1]) * T.sy + (ci[0] - bx0);
+                    tile_move(f, b, nf, rho_t, o, T, qs, pc.qrhot);
                 }
                 __syncthreads();
                 // quad index -> (grid, k, j, quad of the row) with FP32 reciprocals: the quotients
@@ -796,8 +871,11 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 // an integer.  With rows of the grids that are whole quads (nx a multiple of 4) a
                 // quad with a nonzero node is one float4 atomic (16-byte aligned), else one atomic
                 // per nonzero node.
+                // approximate reciprocals: relative error below 2^-21 in the products, which moves a
+                // quotient below 2^10 by less than 2^-11, inside the 1/(2 divisor) >= 2^-11 margin
                 const int qx = tx >> 2, vq = vol >> 2, nq = nent >> 2;
-                const float ivq = 1.f / (float)vq, iqxy = 1.f / (float)(qx * ty), iqx = 1.f / (float)qx;
+                const float ivq = __fdividef(1.f, (float)vq), iqxy = __fdividef(1.f, (float)(qx * ty));
+                const float iqx = __fdividef(1.f, (float)qx);
                 const bool vec = (g.sy & 3) == 0 && (g.sz & 3) == 0;
                 for (int i = threadIdx.x; i < nq; i += blockDim.x) {
                     int4 v = tile4[i];
