@@ -35,7 +35,10 @@ namespace mithra {
 
 namespace {
 
-constexpr int TX = 64, TY = 8, NST = 4, KZ = 32;
+#ifndef MITHRA_STENCIL_KZ
+#define MITHRA_STENCIL_KZ 32
+#endif
+constexpr int TX = 64, TY = 8, NST = 4, KZ = MITHRA_STENCIL_KZ;   // tile, stages, planes per block
 
 template <typename real>
 struct Tile {
@@ -156,30 +159,33 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     auto hrow = [&](int p, int dy) -> const real* {
         return (const real*)(smem + ((p - pfirst) % NST) * T::STAGE) + (ty + 1 + dy) * T::W + cx + T::HX;
     };
-    // registers of planes k-1 (0), k (1), k+1 (2): the pair (ca, cb), and the sums of each cell's
-    // two x neighbours (XA = x-1 + x+1 of the first cell, XB of the second) and of its two y
-    // neighbours (YA, YB), formed once per plane and used in three updates; x+2 alone (xq) for the
-    // Mur x face
-    real ca0, ca1, ca2, cb0, cb1, cb2, xq0, xq1, xq2;
-    real XA0, XA1, XA2, XB0, XB1, XB2, YA0, YA1, YA2, YB0, YB1, YB2;
-    auto load = [&](int p, real& ca, real& cb, real& xq, real& XA, real& XB, real& YA, real& YB) {
+    // registers of one plane: the pair (ca, cb), and the sums of each cell's two x neighbours (XA =
+    // x-1 + x+1 of the first cell, XB of the second) and of its two y neighbours (YA, YB), formed
+    // once per plane and used in three updates; x+2 alone (xq) for the Mur x face.  Planes k-1,
+    // k and k+1 are live; the loop below is unrolled three times so that moving on a plane renames
+    // them instead of copying.
+    struct Plane {
+        real ca, cb, xq, XA, XB, YA, YB;
+    };
+    Plane P0, P1, P2;
+    auto load = [&](int p, Plane& P) {
         const real* r = hrow(p, 0);
         const V2 c = *(const V2*)r;
-        ca = c.x;
-        cb = c.y;
+        P.ca = c.x;
+        P.cb = c.y;
         const real xm = r[-1];
-        xq = r[2];
+        P.xq = r[2];
         const V2 m = *(const V2*)hrow(p, -1);
         const V2 q = *(const V2*)hrow(p, 1);
-        XA = cb + xm;
-        XB = xq + ca;
-        YA = q.x + m.x;
-        YB = q.y + m.y;
+        P.XA = P.cb + xm;
+        P.XB = P.xq + P.ca;
+        P.YA = q.x + m.x;
+        P.YB = q.y + m.y;
     };
     wait_plane(pfirst);
     wait_plane(pfirst + 1);
-    load(pfirst, ca0, cb0, xq0, XA0, XB0, YA0, YB0);
-    load(pfirst + 1, ca1, cb1, xq1, XA1, XB1, YA1, YB1);
+    load(pfirst, P0);
+    load(pfirst + 1, P1);
     ok = __syncthreads_and(ok) != 0;
     if (ok && threadIdx.x == 0 && pfirst + NST <= plast) {
         issue(pfirst + NST);
@@ -187,19 +193,19 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     }
     real* __restrict__ o = a.out[comp];
     const real s = a.s[comp];
-    int k = k0;
-    for (; k <= k1 && ok; ++k) {
+    // plane k from planes k-1 (L), k (C) and k+1 (N, loaded here)
+    auto step = [&](int k, const Plane& L, const Plane& C, Plane& N) {
         wait_plane(k + 1);
-        load(k + 1, ca2, cb2, xq2, XA2, XB2, YA2, YB2);
+        load(k + 1, N);
         const unsigned char* stk = smem + ((k - pfirst) % NST) * T::STAGE;
         const V2 pm = *(const V2*)((const real*)(stk + T::OFF_PREV) + ty * TX + cx);
         const V2 sr = *(const V2*)((const real*)(stk + T::OFF_SRC) + ty * TX + cx);
         if ((mineA || mineB) && ok) {
             // ax (w (N^{k-1} + N^{k+1}) + w0 N^k) over the two x neighbours, likewise along y
-            const real vA = a.a1 * ca1 - pm.x + a.axw * (XA0 + XA2) + a.axw0 * XA1 + a.ayw * (YA0 + YA2) +
-                            a.ayw0 * YA1 + a.a6 * (ca0 + ca2) + s * sr.x;
-            const real vB = a.a1 * cb1 - pm.y + a.axw * (XB0 + XB2) + a.axw0 * XB1 + a.ayw * (YB0 + YB2) +
-                            a.ayw0 * YB1 + a.a6 * (cb0 + cb2) + s * sr.y;
+            const real vA = a.a1 * C.ca - pm.x + a.axw * (L.XA + N.XA) + a.axw0 * C.XA + a.ayw * (L.YA + N.YA) +
+                            a.ayw0 * C.YA + a.a6 * (L.ca + N.ca) + s * sr.x;
+            const real vB = a.a1 * C.cb - pm.y + a.axw * (L.XB + N.XB) + a.axw0 * C.XB + a.ayw * (L.YB + N.YB) +
+                            a.ayw0 * C.YB + a.a6 * (L.cb + N.cb) + s * sr.y;
             const int64_t row = (int64_t)k * sz + (int64_t)y * sy;
             if (mineA && mineB) {
                 V2 v;
@@ -215,27 +221,34 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
                 // Mur x faces (the formula and the summation order of k_mur_faces)
                 const bool o2 = a.mur != 1;
                 if (x == 0 && mineB)   // b = x (this pair's first cell), q = x + 1
-                    o[row] = a.mf0 * (pm.x + vB) + a.mf1 * (ca1 + cb1) - pm.y + a.mfy * (o2 ? YA1 + YB1 : (real)0) +
-                             a.mfz * (o2 ? ca2 + ca0 + cb2 + cb0 : (real)0);
+                    o[row] = a.mf0 * (pm.x + vB) + a.mf1 * (C.ca + C.cb) - pm.y +
+                             a.mfy * (o2 ? C.YA + C.YB : (real)0) + a.mfz * (o2 ? N.ca + L.ca + N.cb + L.cb : (real)0);
                 if (mineA && x == ex - 2)   // q = x, b = x + 1 (this pair's second cell)
-                    o[row + x + 1] = a.mf0 * (pm.y + vA) + a.mf1 * (cb1 + ca1) - pm.x +
-                                     a.mfy * (o2 ? YB1 + YA1 : (real)0) + a.mfz * (o2 ? cb2 + cb0 + ca2 + ca0 : (real)0);
+                    o[row + x + 1] = a.mf0 * (pm.y + vA) + a.mf1 * (C.cb + C.ca) - pm.x +
+                                     a.mfy * (o2 ? C.YB + C.YA : (real)0) +
+                                     a.mfz * (o2 ? N.cb + L.cb + N.ca + L.ca : (real)0);
                 if (mineB && x + 1 == ex - 2) {   // q = x + 1, b = x + 2 (the next pair's first cell)
                     const real nmb = cx + 2 < TX ? ((const real*)(stk + T::OFF_PREV))[ty * TX + cx + 2]
                                                  : a.prev[comp][row + x + 2];
-                    o[row + x + 2] = a.mf0 * (nmb + vB) + a.mf1 * (xq1 + cb1) - pm.y +
-                                     a.mfy * (o2 ? hrow(k, 1)[2] + hrow(k, -1)[2] + YB1 : (real)0) +
-                                     a.mfz * (o2 ? xq2 + xq0 + cb2 + cb0 : (real)0);
+                    o[row + x + 2] = a.mf0 * (nmb + vB) + a.mf1 * (C.xq + C.cb) - pm.y +
+                                     a.mfy * (o2 ? hrow(k, 1)[2] + hrow(k, -1)[2] + C.YB : (real)0) +
+                                     a.mfz * (o2 ? N.xq + L.xq + N.cb + L.cb : (real)0);
                 }
             }
         }
-        ca0 = ca1, ca1 = ca2, cb0 = cb1, cb1 = cb2, xq0 = xq1, xq1 = xq2;
-        XA0 = XA1, XA1 = XA2, XB0 = XB1, XB1 = XB2, YA0 = YA1, YA1 = YA2, YB0 = YB1, YB1 = YB2;
         ok = __syncthreads_and(ok) != 0;
         if (ok && threadIdx.x == 0 && k + NST <= plast) {
             issue(k + NST);
             last_issued = k + NST;
         }
+    };
+    int k = k0;
+    while (k <= k1 && ok) {
+        step(k++, P0, P1, P2);
+        if (k > k1 || !ok) break;
+        step(k++, P1, P2, P0);
+        if (k > k1 || !ok) break;
+        step(k++, P2, P0, P1);
     }
     if (!ok) {
         if (threadIdx.x == 0) {
