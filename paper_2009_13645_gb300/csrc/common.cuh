@@ -337,17 +337,40 @@ __device__ __forceinline__ bool last_block(unsigned* counter)
     return last;
 }
 
+// Sum of v over the block (the result in thread 0; sh: 32 doubles of shared memory), a fixed
+// tree: warp shuffles, then the warp sums.
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
 // Programmatic dependent launch.  The kernels of a step are launched with programmatic stream
 // serialisation (launch_dep): a kernel's blocks may become resident while the previous kernel
 // of the stream is still finishing its last blocks, which hides the launch and ramp-up of every
 // kernel boundary.  Each such kernel calls dep_begin() first, in every block, before it reads
-// or writes device memory: it lets its own successor launch, then waits until its predecessor
-// has completed and that kernel's writes are visible.  Launched the ordinary way, the wait is
-// a no-op.
+// or writes device memory: it waits until its predecessor has completed and that kernel's
+// writes are visible, and only then lets its own successor launch.  So at most two kernels of
+// the stream overlap, and everything before the predecessor completed before this kernel was
+// launched: no block of an older kernel can still be writing, or caching in an SM's L1 a line
+// this kernel later reads.  (Letting the successor launch first allowed chains of small kernels
+// to be resident at once, and a kernel two launches on read a stale L1 copy of the step state
+// that the older kernel was about to overwrite.)  Launched the ordinary way, the wait is a
+// no-op.
 __device__ __forceinline__ void dep_begin()
 {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 #endif
 

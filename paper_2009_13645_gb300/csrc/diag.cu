@@ -8,22 +8,6 @@ namespace mithra {
 
 constexpr int kRedThreads = 256;
 
-__device__ __forceinline__ double block_sum(double v, double* sh)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
-    if (w == 0) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    }
-    __syncthreads();
-    return v;
-}
-
 // Final pass: one block adds the block partials (columns `ncol` interleaved) with
 // Neumaier-compensated sums per thread, then a tree.
 __global__ void k_final(const double* __restrict__ partial, int npartial, int ncol, double scale, double* __restrict__ out)
@@ -43,90 +27,7 @@ __global__ void k_final(const double* __restrict__ partial, int npartial, int nc
 }
 
 // ---- radiated power -------------------------------------------------------------------
-// One step of the running DFT on the power plane: every plane point adds its new sample of
-// E_x, E_y, B_x, B_y times exp(-j w t_n) to its accumulators and, once the window is full,
-// subtracts the sample of step n - M kept in the ring (the DFT over the last M steps, updated
-// instead of recomputed); the interior points then add Re(Ex By* - Ey Bx*) of their
-// accumulators to a per-block partial.  The on-axis E_x of the step is recorded by one thread.
-template <typename real>
-__global__ void __launch_bounds__(kRedThreads) k_power_step(Fields6<real> eb, Geom g, PowerStep ps,
-                                                            double* __restrict__ partial)
-{
-    dep_begin();
-    __shared__ double sh[32];
-    const int64_t plane = (int64_t)g.nx * g.ny;
-    const int64_t pl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const StepDev sd = *ps.sd;
-    double contrib = 0.0;
-    if (pl < plane) {
-        const int64_t id = (int64_t)ps.kp * g.sz + pl;
-        if (id == ps.onaxis_id) ps.onaxis_series[sd.n] = (double)eb.at(0, id);
-        const double x[4] = {(double)eb.at(0, id), (double)eb.at(1, id), (double)eb.at(3, id), (double)eb.at(4, id)};
-        double* r = ps.ring + (int64_t)sd.slot * 4 * plane + pl;
-        double re[4], im[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double a = ps.acc[(2 * q) * plane + pl], b = ps.acc[(2 * q + 1) * plane + pl];
-            a += x[q] * sd.cn;
-            b -= x[q] * sd.sn;
-            if (sd.full) {
-                const double o = r[q * plane];
-                a -= o * sd.co;
-                b += o * sd.so;
-            }
-            ps.acc[(2 * q) * plane + pl] = a;
-            ps.acc[(2 * q + 1) * plane + pl] = b;
-            r[q * plane] = x[q];
-            re[q] = a;
-            im[q] = b;
-        }
-        const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
-        if (sd.emit && i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2)
-            contrib = (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
-    }
-    const double tot = block_sum(contrib, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-    // the last block to finish adds the partials (compensated, in a fixed order) to series[n]
-    // once the window is complete, and leaves the counter at zero for the next step
-    if (last_block(ps.counter)) {
-        if (sd.emit) {
-            double s = 0.0, comp = 0.0;
-            for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-                const double v = __ldcg(partial + i);
-                const double t = s + v;
-                comp += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
-                s = t;
-            }
-            const double all = block_sum(s + comp, sh);
-            if (threadIdx.x == 0) ps.series[sd.n] = all * ps.scale;
-        }
-        if (threadIdx.x == 0) *ps.counter = 0;
-    }
-}
-
-template <typename real>
-cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const PowerStep& ps, double scale,
-                              double* partial, int npartial, double* series, cudaStream_t st)
-{
-    const int64_t plane = (int64_t)g.nx * g.ny;
-    const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
-    if ((int)nb > npartial) return cudaErrorInvalidValue;
-    PowerStep p = ps;
-    p.scale = scale;
-    p.series = series;
-    {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_power_step<real>, dim3(nb), dim3(kRedThreads), 0,
-                                          st, eb, g, p, partial);
-        if (le != cudaSuccess) return le;
-    }
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-template cudaError_t launch_power_step<float>(const Fields6<float>&, const Geom&, const PowerStep&, double, double*,
-                                              int, double*, cudaStream_t);
-template cudaError_t launch_power_step<double>(const Fields6<double>&, const Geom&, const PowerStep&, double, double*,
-                                               int, double*, cudaStream_t);
+// The power step runs in the step tail (power_point in kernels.h, the launch in fields.cu).
 
 // ---- field energy ----------------------------------------------------------------------
 template <typename real>

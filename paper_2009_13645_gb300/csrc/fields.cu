@@ -209,21 +209,81 @@ __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeC
     n1[lin(p[0], p[1], p[2], sy, sz)] = num;
 }
 
-// The edges of every component (blockIdx.y), then, in the last block to finish, the 8 corners of
-// every component.
+// The step tail, one launch of 1-D blocks of kTailThreads: blocks [0, ncomp nbe) the Mur edges of
+// component b / nbe; then npw blocks of the power step (plane points); then the blocks of the
+// next step's phase tables (node planes).  The last block to finish writes the 8 corners of every
+// component (the edges are in), adds the power partials (compensated, in a fixed order) into the
+// step's series entry once the window is complete, and advances the step state: nothing after
+// this launch in the step reads it.
+constexpr int kTailThreads = 256;
 template <typename real>
-__global__ void __launch_bounds__(64) k_mur_edges(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy, int64_t sz,
-                                                  int64_t maxpts, unsigned* counter)
+__global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy,
+                                                            int64_t sz, int64_t maxpts, int nbe, int npw,
+                                                            Fields6<real> eb, Geom g, StepTail tl, unsigned* counter)
 {
     dep_begin();
-    const int comp = blockIdx.y;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (comp < a.ncomp && t < maxpts) mur_point(a, cf, sy, sz, comp, false, t);
+    __shared__ double sh[32];
+    const int b = (int)blockIdx.x;
+    const int ne = a.ncomp * nbe;
+    if (b < ne) {
+        const int64_t t = (int64_t)(b % nbe) * blockDim.x + threadIdx.x;
+        if (t < maxpts) mur_point(a, cf, sy, sz, b / nbe, false, t);
+    } else if (b < ne + npw) {
+        const StepDev sd = *tl.sd;
+        const int64_t pl = (int64_t)(b - ne) * blockDim.x + threadIdx.x;
+        const double c = pl < (int64_t)g.nx * g.ny ? power_point(eb, g, tl.power, sd, pl) : 0.0;
+        const double tot = block_sum(c, sh);
+        if (threadIdx.x == 0) tl.partial[b - ne] = tot;
+    } else {
+        const int iz = (b - ne - npw) * (int)blockDim.x + (int)threadIdx.x;
+        if (iz < tl.phase.nz) {
+            // the next step's lab offset, from the same function that advances the state below
+            const StepDev nx = step_state(tl.sd->next, tl.sc);
+            phase_tables_entry(tl.phase, nx.Z0, iz);
+        }
+    }
     if (last_block(counter)) {
         const int c = (int)threadIdx.x >> 3;
         if (c < a.ncomp) mur_point(a, cf, sy, sz, c, true, (int64_t)(threadIdx.x & 7));
-        if (threadIdx.x == 0) *counter = 0;
+        const StepDev sd = *tl.sd;
+        if (npw > 0 && sd.emit) {
+            double s = 0.0, comp = 0.0;
+            for (int i = threadIdx.x; i < npw; i += blockDim.x) {
+                const double v = __ldcg(tl.partial + i);
+                const double t = s + v;
+                comp += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+                s = t;
+            }
+            const double all = block_sum(s + comp, sh);
+            if (threadIdx.x == 0) tl.power.series[sd.n] = all * tl.power.scale;
+        }
+        __syncthreads();   // every thread of this block has read the state
+        if (threadIdx.x == 0) {
+            *tl.sd = step_state(sd.next, tl.sc);
+            *counter = 0;
+        }
     }
+}
+
+// At a run's creation: block 0 sets the state of step 0, every block fills node planes of the
+// phase tables of step 0.
+__global__ void k_step_init(StepDev* sd, StepConst sc, PhaseTables pt)
+{
+    const StepDev s0 = step_state(0, sc);
+    const int iz = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (iz < pt.nz) phase_tables_entry(pt, s0.Z0, iz);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sd = s0;
+}
+
+cudaError_t launch_step_init(StepDev* sd, const StepConst& sc, const PhaseTables& pt, cudaStream_t st)
+{
+    const bool tables = pt.t32[0] || pt.t64[0];
+    const int nb = tables ? (pt.nz + kTailThreads - 1) / kTailThreads : 1;
+    PhaseTables p = pt;
+    if (!tables) p.nz = 0;
+    k_step_init<<<nb, kTailThreads, 0, st>>>(sd, sc, p);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -259,8 +319,6 @@ struct EmitArgs {
     const int* box;      // cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit; null: whole grid
     int* box_reset;      // box the next push reduces into: reset to empty here (may be null)
     int* err;            // set when a bounded wait on the tensor copies expired (may be null)
-    StepDev* step;       // non-null: block 0 also starts the step (step_advance)
-    StepConst step_c;
 };
 
 #ifndef MITHRA_EMIT_KZ
@@ -326,8 +384,6 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
     const int t = threadIdx.x, tx = t % EX, ty = t / EX;
     if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t < 6)
         a.box_reset[t] = t < 3 ? 0x7fffffff : (int)0x80000000;
-    // the step's state (no other block of the emission reads it; later kernels do)
-    if (a.step && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) step_advance(a.step, a.step_c);
     // nodes [lo - 1, hi + 2] around the cells of the last deposit: the particles gather at their
     // cells' nodes next step, and with sub-steps they move up to one cell during that step
     int bl[3] = {1, 1, 1}, bh[3] = {g.nx - 2, g.ny - 2, g.nz - 2};
@@ -634,7 +690,7 @@ static MurEdgeCoef<real> mur_edge_coef(const Geom& g)
 
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
-                       unsigned* counter, cudaStream_t st)
+                       unsigned* counter, const StepTail& tail, cudaStream_t st)
 {
     MurArgs<real> a;
     a.face0 = x_faces_done ? 2 : 0;
@@ -678,10 +734,18 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     }
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
     const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
+    const int nbe = (int)((edges + kTailThreads - 1) / kTailThreads);
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int npw = (int)((plane + kTailThreads - 1) / kTailThreads);
+    if (npw > tail.npartial) return cudaErrorInvalidValue;
+    const bool tables = tail.phase.t32[0] || tail.phase.t64[0];
+    const int npt = tables ? (tail.phase.nz + kTailThreads - 1) / kTailThreads : 0;
+    Fields6<real> E6;
+    E6.p = (real*)tail.eb;
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_mur_edges<real>,
-                                          dim3((unsigned)((edges + 63) / 64), ncomp), dim3(64), 0, st, a, ec, g.sy,
-                                          g.sz, edges, counter);
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_step_tail<real>,
+                                          dim3((unsigned)(ncomp * nbe + npw + npt)), dim3(kTailThreads), 0, st, a, ec,
+                                          g.sy, g.sz, edges, nbe, npw, E6, g, tail, counter);
         if (le != cudaSuccess) return le;
     }
     count_launches(nl + 1);
@@ -749,8 +813,6 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
     a.box = bx.box;
     a.box_reset = bx.box_reset;
     a.err = bx.err;
-    a.step = bx.step;
-    a.step_c = bx.step_c;
     a.nchunk = (g.nz - 2 + EKZ - 1) / EKZ;
     constexpr int smem = (int)sizeof(EmitSmem<real>) + 128;
     if (bx.maps) {
@@ -871,9 +933,9 @@ template cudaError_t launch_tfsf<double>(double* const[2], const Geom&, const St
 template cudaError_t launch_stencil<float>(const FieldLevels<float>&, const Geom&, const StencilCoef&, int, cudaStream_t);
 template cudaError_t launch_stencil<double>(const FieldLevels<double>&, const Geom&, const StencilCoef&, int, cudaStream_t);
 template cudaError_t launch_mur<float>(const FieldLevels<float>&, const Geom&, int, int, bool, unsigned*,
-                                      cudaStream_t);
+                                      const StepTail&, cudaStream_t);
 template cudaError_t launch_mur<double>(const FieldLevels<double>&, const Geom&, int, int, bool, unsigned*,
-                                       cudaStream_t);
+                                       const StepTail&, cudaStream_t);
 template cudaError_t launch_emit<float>(const FieldLevels<float>&, const Fields6<float>&, const Geom&, const EmitBox&,
                                         cudaStream_t);
 template cudaError_t launch_emit<double>(const FieldLevels<double>&, const Fields6<double>&, const Geom&,

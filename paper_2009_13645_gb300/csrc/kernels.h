@@ -83,8 +83,9 @@ template <typename real>
 cudaError_t launch_mur_tfsf_xfaces(const FieldLevels<real>& L, const Geom& g, int order, cudaStream_t st);
 
 // Per-step values derived on the device from the step counter, so that a captured sequence of
-// steps replays without host-side parameters.  The step's first kernel (the E/B emission) fills
-// it at the start of every step.
+// steps replays without host-side parameters.  Every kernel of step n reads it; the last block of
+// the step's last kernel (the step tail) advances it to step n + 1, and the run's creation sets
+// it to step 0.
 struct StepDev {
     int64_t n;        // the step being computed
     int64_t next;     // the counter: the step after it
@@ -100,10 +101,9 @@ struct StepConst {
     double T0, dt, g0, b0, z0, omega_h;
     int M;
 };
-// The StepDev of the next step from the counter (one thread).
-__device__ __forceinline__ void step_advance(StepDev* sd, const StepConst& c)
+// The StepDev of step n.
+__device__ __forceinline__ StepDev step_state(int64_t n, const StepConst& c)
 {
-    const int64_t n = sd->next;
     StepDev v;
     v.n = n;
     v.next = n + 1;
@@ -114,16 +114,142 @@ __device__ __forceinline__ void step_advance(StepDev* sd, const StepConst& c)
     v.emit = n + 1 >= c.M ? 1 : 0;
     sincos(c.omega_h * ((double)n + 0.5) * c.dt, &v.sn, &v.cn);
     sincos(c.omega_h * ((double)(n - c.M) + 0.5) * c.dt, &v.so, &v.co);
-    *sd = v;
+    return v;
 }
 
-// Mur boundary values of level n+1: the faces, then the edges, then the corners (the corners in
-// the last block of the edge launch to finish; `counter` is a zeroed device word that the launch
-// leaves zeroed).  With x_faces_done the TMA stencil of this step has already written the x
-// faces.
+// The static undulator's phase tables of one node plane iz whose lab coordinate is zn (Sec. "Field
+// Initialization": the planar field's phase k_u zeta per node plane, evaluated once per step in
+// FP64).
+// FP32-mixed path, two float4 per node plane and planar field: the sin and cos of the plane's
+// phase k_u u times the FP64 rest-frame amplitudes (gamma0 beta0 c B, gamma0 B, B), and the
+// distances k_u u, k_u (u - L_u) to both ends of the undulator; FP64 throughout, rounded once.
+// For an array (ta != null) u is counted from the entrance of the plane's module i (the module
+// whose entrance lies at or before the plane, as in the direct evaluation; before the first
+// module, from the first entrance), B is that module's peak field, and ta holds per plane {B_i,
+// B_{i+1} (0 after the last module), 1 for the last module, 0}.
+__device__ __forceinline__ void phase_entry32(const ExtField& f, double zn, int iz, float4* t0, float4* t1, float4* ta)
+{
+    double Bp = f.B0, org = 0.0;
+    if (ta) {
+        const double P = f.Lu + f.gap;
+        int i = (int)floor(zn / P);
+        i = i < -1 ? -1 : (i > f.nmod - 1 ? f.nmod - 1 : i);
+        if (i >= 0 && zn - i * P < 0.0) --i;
+        if (i < f.nmod - 1 && zn - (i + 1) * P >= 0.0) ++i;
+        const int im = i < 0 ? 0 : i;
+        Bp = f.B0 + im * f.dB0;
+        org = im * P;
+        const bool last = i == f.nmod - 1;
+        ta[iz] = make_float4((float)Bp, (float)((i >= 0 && !last) ? Bp + f.dB0 : 0.0), last ? 1.f : 0.f, 0.f);
+    }
+    const double eB = f.g0 * f.b0 * kC * Bp, bB = f.g0 * Bp;
+    for (int j = 0; j < (t1 ? 2 : 1); ++j) {
+        const double ph = f.ku * (zn - (j ? f.qlam : org));
+        double s, c;
+        sincos(ph, &s, &c);
+        float4* t = (j ? t1 : t0) + 2 * iz;
+        t[0] = make_float4((float)(eB * s), (float)(eB * c), (float)(bB * s), (float)(bB * c));
+        t[1] = make_float4((float)(Bp * s), (float)(Bp * c), (float)ph, (float)(ph - f.ku * f.Lu));
+    }
+}
+// FP64 path: sin and cos of k_u zn (and of the helical second field's k_u (zn - lambda_u / 4)).
+__device__ __forceinline__ void phase_entry64(const ExtField& f, double zn, int iz, double2* t0, double2* t1)
+{
+    double s, c;
+    sincos(f.ku * zn, &s, &c);
+    t0[iz] = make_double2(s, c);
+    if (t1) {
+        sincos(f.ku * (zn - f.qlam), &s, &c);
+        t1[iz] = make_double2(s, c);
+    }
+}
+// The phase tables a step's push reads (null pointers: none), for the node planes 0..nz-1 at
+// lab offset Z0 + kz iz.
+struct PhaseTables {
+    ExtField ef;
+    double kz;
+    int nz;
+    float4 *t32[2], *ta32;
+    double2* t64[2];
+};
+__device__ __forceinline__ void phase_tables_entry(const PhaseTables& pt, double Z0, int iz)
+{
+    const double zn = fma(pt.kz, (double)iz, Z0);
+    if (pt.t32[0]) phase_entry32(pt.ef, zn, iz, pt.t32[0], pt.t32[1], pt.ta32);
+    if (pt.t64[0]) phase_entry64(pt.ef, zn, iz, pt.t64[0], pt.t64[1]);
+}
+
+// The radiated power (Sec. FEL-OUTPUT, radiation-power): one step of the running DFT of the
+// transverse fields on the power plane kp.
+struct PowerStep {
+    int kp;                 // plane index
+    double* ring;           // M x 4 x plane samples
+    double* acc;            // 8 x plane accumulators (re, im of Ex, Ey, Bx, By)
+    int64_t onaxis_id;
+    double* onaxis_series;  // on-axis E_x of step n goes to entry n
+    double scale;           // lab factor x (2 / M)^2 x dx dy / (2 mu0)
+    double* series;         // the power of step n goes to series[n] once the window is complete
+};
+// Plane point pl of step sd: it adds its new sample of E_x, E_y, B_x, B_y times exp(-j w t_n) to
+// its accumulators and, once the window is full, subtracts the sample of step n - M kept in the
+// ring (the DFT over the last M steps, updated instead of recomputed); an interior point returns
+// Re(Ex By* - Ey Bx*) of its accumulators, its share of the plane's power.  The on-axis E_x of the
+// step is recorded by its point.
+template <typename real>
+__device__ __forceinline__ double power_point(const Fields6<real>& eb, const Geom& g, const PowerStep& ps,
+                                              const StepDev& sd, int64_t pl)
+{
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    const int64_t id = (int64_t)ps.kp * g.sz + pl;
+    if (id == ps.onaxis_id) ps.onaxis_series[sd.n] = (double)eb.at(0, id);
+    const double x[4] = {(double)eb.at(0, id), (double)eb.at(1, id), (double)eb.at(3, id), (double)eb.at(4, id)};
+    double* r = ps.ring + (int64_t)sd.slot * 4 * plane + pl;
+    double re[4], im[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double a = ps.acc[(2 * q) * plane + pl], b = ps.acc[(2 * q + 1) * plane + pl];
+        a += x[q] * sd.cn;
+        b -= x[q] * sd.sn;
+        if (sd.full) {
+            const double o = r[q * plane];
+            a -= o * sd.co;
+            b += o * sd.so;
+        }
+        ps.acc[(2 * q) * plane + pl] = a;
+        ps.acc[(2 * q + 1) * plane + pl] = b;
+        r[q * plane] = x[q];
+        re[q] = a;
+        im[q] = b;
+    }
+    const int i = (int)(pl % g.nx), j = (int)(pl / g.nx);
+    if (sd.emit && i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2)
+        return (re[0] * re[3] + im[0] * im[3]) - (re[1] * re[2] + im[1] * im[2]);
+    return 0.0;
+}
+
+// The end of a step (the step tail): besides the Mur edges and corners, the radiated power's
+// running DFT of the step (eb: the step's E/B; series[n] once the window is complete), the phase
+// tables of the next step, and the step state's advance.
+struct StepTail {
+    const void* eb;         // the step's E/B (Fields6 of the run's precision)
+    PowerStep power;
+    double* partial;        // power block partials (at most npartial)
+    int npartial;
+    PhaseTables phase;      // the tables of step n + 1
+    StepDev* sd;
+    StepConst sc;
+};
+
+// Mur boundary values of level n+1 and the step tail: the faces (unless the TMA stencil of this
+// step has written them all: x_faces_done covers the x faces), then one launch with the edges,
+// the tail's power and phase-table blocks, and in the last block to finish the corners, the
+// power's sum and the step state's advance (`counter` is a zeroed device word that the launch
+// leaves zeroed).
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
-                       unsigned* counter, cudaStream_t st);
+                       unsigned* counter, const StepTail& tail, cudaStream_t st);
+// At a run's creation: the step state of step 0 and its phase tables.
+cudaError_t launch_step_init(StepDev* sd, const StepConst& sc, const PhaseTables& pt, cudaStream_t st);
 // Tensor maps of the seven arrays one E/B emission reads (A_x^n, A_x^{n+1}, A_y^n, A_y^{n+1},
 // A_z^n, A_z^{n+1}, phi^n), each with a box of kEmitBoxW x kEmitBoxH x 1 (the emission tile
 // plus a one-node halo, padded to whole 16-byte rows).
@@ -142,8 +268,6 @@ struct EmitBox {
     bool clear;          // clear the sources inside the box
     const EmitMaps* maps = nullptr;   // TMA loads (null: per-element asynchronous copies)
     int* err = nullptr;               // set when a bounded wait of the TMA loads expired
-    StepDev* step = nullptr;          // non-null: the emission also starts the step (step_advance)
-    StepConst step_c{};
 };
 template <typename real>
 cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, const Geom& g, const EmitBox& bx,
@@ -189,11 +313,6 @@ struct PushConst {
     float ltE, ltB, E0f, E0cf, w0f, izrf, zrf, kLf;
 };
 
-cudaError_t launch_phase_table(const ExtField& ef, const StepDev* sd, double kz, int nz, double2* t0, double2* t1,
-                               cudaStream_t st);
-cudaError_t launch_phase_table32(const ExtField& ef, const StepDev* sd, double kz, int nz, float4* t0, float4* t1,
-                                 float4* ta, cudaStream_t st);
-
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,
                         const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, int* box_out,
@@ -225,21 +344,6 @@ cudaError_t launch_sort(Particles<real>& P, Particles<real>& tmp, int64_t np, co
 size_t sort_scan_partials(int64_t nbins);
 
 // Diagnostics.
-struct PowerStep {
-    int kp;                 // plane index
-    const StepDev* sd;      // step n: ring slot, window state, exp(-j w t) of steps n and n - M
-    double* ring;           // M x 4 x plane samples
-    double* acc;            // 8 x plane accumulators (re, im of Ex, Ey, Bx, By)
-    int64_t onaxis_id;
-    double* onaxis_series;  // on-axis E_x of step n goes to entry n
-    unsigned* counter;      // zeroed device word: finds the last block (left zeroed)
-    double scale;           // set by launch_power_step
-    double* series;         // set by launch_power_step
-};
-// The power of step n goes to series[n] once the window is complete.
-template <typename real>
-cudaError_t launch_power_step(const Fields6<real>& eb, const Geom& g, const PowerStep& ps, double scale,
-                              double* partial, int npartial, double* series, cudaStream_t st);
 template <typename real>
 cudaError_t launch_energy(const Fields6<real>& eb, const Geom& g, double* partial, int npartial, double* out,
                           cudaStream_t st);

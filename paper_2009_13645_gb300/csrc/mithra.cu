@@ -411,6 +411,7 @@ struct RunT final : mithra_run {
         scst.z0 = d.z0;
         scst.omega_h = d.omega_h;
         scst.M = (int)d.M;
+        CU(launch_step_init(sd, scst, phase_tables(), stream));   // step 0's state and phase tables
         const char* no_graph = std::getenv("MITHRA_NO_GRAPHS");
         use_graphs = !(no_graph && no_graph[0] == '1');
         const char* no_tma = std::getenv("MITHRA_NO_TMA");
@@ -479,6 +480,21 @@ struct RunT final : mithra_run {
         prof_pending.push_back({kid, a, b});
     }
 
+    // The phase tables the push reads (filled for step n + 1 by step n's tail).
+    PhaseTables phase_tables() const
+    {
+        PhaseTables pt;
+        pt.ef = ef;
+        pt.kz = d.g0 * d.dz;
+        pt.nz = g.nz;
+        pt.t32[0] = ptab32[0];
+        pt.t32[1] = ptab32[1];
+        pt.ta32 = ptab32a;
+        pt.t64[0] = ptab[0];
+        pt.t64[1] = ptab[1];
+        return pt;
+    }
+
     FieldLevels<real> levels() const
     {
         FieldLevels<real> L;
@@ -521,8 +537,6 @@ struct RunT final : mithra_run {
         EmitMaps em;
         if (emit_maps(tma, lev(0), lev(1), &em)) bx.maps = &em;
         bx.err = err_word;
-        bx.step = sd;   // the emission starts the step: nothing before it reads the step state
-        bx.step_c = scst;
         pbeg(MITHRA_K_EMIT, &e0);
         CU(launch_emit<real>(L, E6, g, bx, stream));
         pend(MITHRA_K_EMIT, e0);
@@ -580,8 +594,6 @@ struct RunT final : mithra_run {
         pc.zrf = (float)ef.zr;
         pc.kLf = (float)ef.kL;
         pbeg(MITHRA_K_PUSH, &e0);
-        if (ptab[0]) CU(launch_phase_table(ef, sd, pc.kz, g.nz, ptab[0], ptab[1], stream));
-        if (ptab32[0]) CU(launch_phase_table32(ef, sd, pc.kz, g.nz, ptab32[0], ptab32[1], ptab32a, stream));
         CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
         pend(MITHRA_K_PUSH, e0);
         if (bunch_every > 0) {
@@ -618,40 +630,47 @@ struct RunT final : mithra_run {
             if (xf) CU(launch_mur_tfsf_xfaces<real>(L, g, mur_order, stream));
         }
         pend(MITHRA_K_STENCIL, e0);
-        pbeg(MITHRA_K_MUR, &e0);
-        CU(launch_mur<real>(L, g, mur_order, ncomp, xf, counters, stream));
-        pend(MITHRA_K_MUR, e0);
-        pbeg(MITHRA_K_POWER, &e0);
-        {
-            const int M = (int)d.M;
-            PowerStep ps;
-            ps.kp = (int)d.kp;
-            ps.sd = sd;
-            ps.ring = ring;
-            ps.acc = acc;
-            ps.onaxis_id = onaxis_id;
-            ps.onaxis_series = ser_e;
-            ps.counter = counters + 1;
-            const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
-            const double scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
-            if (!ring || !acc || !partial) return fail(MITHRA_EINVAL, "power diagnostic buffers missing");
-            CU(launch_power_step<real>(E6, g, ps, scale, partial, npartial, ser_p, stream));
-            if (nf > 0) {
-                SpecStep sp;
-                sp.kp = (int)d.kp;
-                sp.nf = nf;
-                sp.Mh = Mh;
-                sp.sd = sd;
-                sp.dt = d.dt;
-                sp.omega = spec_omega;
-                sp.M = spec_M;
-                sp.scale = spec_scale;
-                sp.ring = spec_ring;
-                sp.acc = spec_acc;
-                CU(launch_spectrum_step<real>(E6, g, sp, spec_partial, npartial, ser_s, stream));
-            }
+        if (nf > 0) {
+            // the spectrum reads this step's state: before the tail advances it
+            pbeg(MITHRA_K_POWER, &e0);
+            SpecStep sp;
+            sp.kp = (int)d.kp;
+            sp.nf = nf;
+            sp.Mh = Mh;
+            sp.sd = sd;
+            sp.dt = d.dt;
+            sp.omega = spec_omega;
+            sp.M = spec_M;
+            sp.scale = spec_scale;
+            sp.ring = spec_ring;
+            sp.acc = spec_acc;
+            CU(launch_spectrum_step<real>(E6, g, sp, spec_partial, npartial, ser_s, stream));
+            pend(MITHRA_K_POWER, e0);
         }
-        pend(MITHRA_K_POWER, e0);
+        // Mur faces, then the step tail: the edges and corners, the radiated power of the step,
+        // the phase tables of the next step and the step state's advance
+        pbeg(MITHRA_K_MUR, &e0);
+        {
+            if (!ring || !acc || !partial) return fail(MITHRA_EINVAL, "power diagnostic buffers missing");
+            const int M = (int)d.M;
+            StepTail tl;
+            tl.eb = eb;
+            tl.power.kp = (int)d.kp;
+            tl.power.ring = ring;
+            tl.power.acc = acc;
+            tl.power.onaxis_id = onaxis_id;
+            tl.power.onaxis_series = ser_e;
+            const double f = d.g0 * d.g0 * (1.0 + d.b0) * (1.0 + d.b0);
+            tl.power.scale = f * (2.0 / M) * (2.0 / M) * d.dx * d.dy / (2.0 * kMu0);
+            tl.power.series = ser_p;
+            tl.partial = partial;
+            tl.npartial = npartial;
+            tl.phase = phase_tables();
+            tl.sd = sd;
+            tl.sc = scst;
+            CU(launch_mur<real>(L, g, mur_order, ncomp, xf, counters, tl, stream));
+        }
+        pend(MITHRA_K_MUR, e0);
         base = (base + 1) % 3;
         ++nstep;
         if (prof && prof_pending.size() > 4096) {

@@ -261,81 +261,8 @@ __device__ __forceinline__ void optical_field_mixed(const ExtField& f, const Pus
     B[2] = -Bl;
 }
 
-// FP32 table for the mixed path, two float4 per node plane and planar field: the sin and cos of
-// the plane's phase k_u u times the FP64 rest-frame amplitudes (gamma0 beta0 c B, gamma0 B, B),
-// and the distances k_u u, k_u (u - L_u) to both ends of the undulator; FP64 throughout, rounded
-// once.  For an array (ta != null) u is counted from the entrance of the plane's module i (the
-// module whose entrance lies at or before the plane, as in the direct evaluation; before the
-// first module, from the first entrance), B is that module's peak field, and ta holds per plane
-// {B_i, B_{i+1} (0 after the last module), 1 for the last module, 0}.
-__global__ void k_phase_table32(ExtField f, const StepDev* sd, double kz, int nz, float4* t0, float4* t1, float4* ta)
-{
-    dep_begin();
-    const int iz = blockIdx.x * blockDim.x + threadIdx.x;
-    if (iz >= nz) return;
-    const double zn = fma(kz, (double)iz, sd->Z0);
-    double Bp = f.B0, org = 0.0;
-    if (ta) {
-        const double P = f.Lu + f.gap;
-        int i = (int)floor(zn / P);
-        i = i < -1 ? -1 : (i > f.nmod - 1 ? f.nmod - 1 : i);
-        if (i >= 0 && zn - i * P < 0.0) --i;
-        if (i < f.nmod - 1 && zn - (i + 1) * P >= 0.0) ++i;
-        const int im = i < 0 ? 0 : i;
-        Bp = f.B0 + im * f.dB0;
-        org = im * P;
-        const bool last = i == f.nmod - 1;
-        ta[iz] = make_float4((float)Bp, (float)((i >= 0 && !last) ? Bp + f.dB0 : 0.0), last ? 1.f : 0.f, 0.f);
-    }
-    const double eB = f.g0 * f.b0 * kC * Bp, bB = f.g0 * Bp;
-    for (int j = 0; j < (t1 ? 2 : 1); ++j) {
-        const double ph = f.ku * (zn - (j ? f.qlam : org));
-        double s, c;
-        sincos(ph, &s, &c);
-        float4* t = (j ? t1 : t0) + 2 * iz;
-        t[0] = make_float4((float)(eB * s), (float)(eB * c), (float)(bB * s), (float)(bB * c));
-        t[1] = make_float4((float)(Bp * s), (float)(Bp * c), (float)ph, (float)(ph - f.ku * f.Lu));
-    }
-}
-
-cudaError_t launch_phase_table32(const ExtField& ef, const StepDev* sd, double kz, int nz, float4* t0, float4* t1,
-                                 float4* ta, cudaStream_t st)
-{
-    {
-        const cudaError_t le = launch_dep(dep_launch_on<float>(st), k_phase_table32, dim3((nz + 127) / 128),
-                                          dim3(128), 0, st, ef, sd, kz, nz, t0, t1, ta);
-        if (le != cudaSuccess) return le;
-    }
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-__global__ void k_phase_table(ExtField f, const StepDev* sd, double kz, int nz, double2* t0, double2* t1)
-{
-    dep_begin();
-    const int iz = blockIdx.x * blockDim.x + threadIdx.x;
-    if (iz >= nz) return;
-    const double zn = fma(kz, (double)iz, sd->Z0);
-    double s, c;
-    sincos(f.ku * zn, &s, &c);
-    t0[iz] = make_double2(s, c);
-    if (t1) {
-        sincos(f.ku * (zn - f.qlam), &s, &c);
-        t1[iz] = make_double2(s, c);
-    }
-}
-
-cudaError_t launch_phase_table(const ExtField& ef, const StepDev* sd, double kz, int nz, double2* t0, double2* t1,
-                               cudaStream_t st)
-{
-    {
-        const cudaError_t le = launch_dep(dep_launch_on<double>(st), k_phase_table, dim3((nz + 127) / 128), dim3(128),
-                                          0, st, ef, sd, kz, nz, t0, t1);
-        if (le != cudaSuccess) return le;
-    }
-    count_launches(1);
-    return cudaGetLastError();
-}
+// The phase tables the push reads (phase_entry32 / phase_entry64 in kernels.h) are filled for each
+// step by the previous step's tail, and for step 0 when the run is created.
 
 __device__ __forceinline__ bool active_cell(int i, int j, int k, const Geom& g)
 {
