@@ -376,8 +376,11 @@ def main():
         return reduce_max_over_ranks(x, ws, "cuda")
 
     def emitted_nodes(run, wl) -> int:
-        """Nodes one E/B emission writes: the deposit box of the particles' active cells widened
-        to nodes [lo - 1, hi + 2], plus the power plane outside it."""
+        """Nodes one E/B emission writes (at least): per z chunk of 8 node planes, the xy box of
+        the active cells whose nodes [lo - 1, hi + 2] reach the chunk, over the planes of the
+        deposit box [lo_z - 1, hi_z + 2]; plus the power plane outside its chunk's box.  The
+        push widens each chunk's box by whole blocks of particles, so the emission writes a few
+        more: the count is a lower bound."""
         inf = run.info()
         P = run.particles()
         c = [np.floor((P[:, d] - inf[o]) / inf[s_]).astype(np.int64)
@@ -389,10 +392,24 @@ def main():
         plane = (wl.nx - 2) * (wl.ny - 2)
         if not act.any():
             return plane
-        lo = [max(int(c[d][act].min()) - 1, 1) for d in range(3)]
-        hi = [min(int(c[d][act].max()) + 2, n[d] - 2) for d in range(3)]
-        ext = [hi[d] - lo[d] + 1 for d in range(3)]
-        return ext[0] * ext[1] * ext[2] + plane - (ext[0] * ext[1] if lo[2] <= int(inf["kp"]) <= hi[2] else 0)
+        x, y, z = c[0][act], c[1][act], c[2][act]
+        zl, zh = max(int(z.min()) - 1, 1), min(int(z.max()) + 2, n[2] - 2)
+        kp = int(inf["kp"])
+        total, kp_box = 0, 0
+        for c0 in range(1, n[2] - 1, 8):
+            c1 = c0 + 7
+            a, b = max(c0, zl), min(c1, zh)
+            if a > b:
+                continue
+            sel = (z - 1 <= c1) & (z + 2 >= c0)
+            if not sel.any():
+                continue
+            ex = min(int(x[sel].max()) + 2, n[0] - 2) - max(int(x[sel].min()) - 1, 1) + 1
+            ey = min(int(y[sel].max()) + 2, n[1] - 2) - max(int(y[sel].min()) - 1, 1) + 1
+            total += ex * ey * (b - a + 1)
+            if a <= kp <= b:
+                kp_box = ex * ey
+        return total + plane - kp_box
 
     def timed_run(precision: int, steps: int, sample_clocks: bool, wl=None, labl=None):
         """K timed steps as a user runs them (captured graphs replayed), then K more steps with

@@ -323,13 +323,14 @@ __host__ __device__ inline void boris_f32(float u[3], const float E[3], const fl
 // threads, after its own global writes); the writes of every block are then visible to that
 // block, which reads them through L2 (__ldcg).  `counter` counts arrivals; the last block
 // resets it for the next launch.
-__device__ __forceinline__ bool last_block(unsigned* counter)
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned total = 0)
 {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        // total: the blocks that arrive (0: every block of the grid)
+        if (total == 0) total = gridDim.x * gridDim.y * gridDim.z;
         last = atomicAdd(counter, 1u) == total - 1;
     }
     __syncthreads();

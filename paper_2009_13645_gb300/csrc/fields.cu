@@ -105,30 +105,16 @@ struct MurArgs {
 
 __device__ inline int64_t lin(int i, int j, int k, int64_t sy, int64_t sz) { return (int64_t)k * sz + (int64_t)j * sy + i; }
 
-// One face per blockIdx.z (axis = f / 2, side = f % 2 with f = face0 + z), one component per
-// blockIdx.y.
+// Mur value of level n+1 at the face node p of face (ax, side sd) of component comp, from the
+// interior value beside it (already updated) and levels n, n-1.
 template <typename real>
-__global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
+__device__ __forceinline__ real mur_face_value(const MurArgs<real>& a, int comp, int ax, int sd, const int p[3],
+                                               int64_t sy, int64_t sz)
 {
-    dep_begin();
-    const int comp = blockIdx.y;
-    if (comp >= a.ncomp) return;
-    const int f = a.face0 + (int)blockIdx.z;
-    const int ax = f >> 1, sd = f & 1;
-    const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
-    const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;   // tangential axes, u before v
-    const int v0 = ax == 0 ? a.kmin : 1, v1 = ax == 0 ? min(a.kmax, e[v] - 2) : e[v] - 2;
-    const int nu = e[u] - 2, nv = v1 - v0 + 1;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (nv <= 0 || t >= nu * nv) return;
-    int p[3];
-    p[ax] = sd ? e[ax] - 1 : 0;
-    p[u] = 1 + t % nu;
-    p[v] = v0 + t / nu;
     const int64_t st[3] = {1, sy, sz};
     const int64_t ib = lin(p[0], p[1], p[2], sy, sz);
     const int64_t iq = ib + (sd ? -st[ax] : st[ax]);   // inward neighbour
-    real* __restrict__ n1 = a.n1[comp];
+    const real* __restrict__ n1 = a.n1[comp];
     const real* __restrict__ n0 = a.n0[comp];
     const real* __restrict__ nm = a.nm[comp];
     real sa = (real)0, sb = (real)0;
@@ -139,7 +125,35 @@ __global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
         sb = n0[ib + st[tb]] + n0[ib - st[tb]] + n0[iq + st[tb]] + n0[iq - st[tb]];
     }
     // first order: the tangential gammas are zero
-    n1[ib] = a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + a.ft[ax][0] * sa + a.ft[ax][1] * sb;
+    return a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + a.ft[ax][0] * sa + a.ft[ax][1] * sb;
+}
+
+// Face node t of face f (axis = f / 2, side = f % 2) of component comp, if it exists.
+template <typename real>
+__device__ __forceinline__ void mur_face_node(const MurArgs<real>& a, int comp, int f, int t, int64_t sy, int64_t sz)
+{
+    const int ax = f >> 1, sd = f & 1;
+    const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
+    const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;   // tangential axes, u before v
+    const int v0 = ax == 0 ? a.kmin : 1, v1 = ax == 0 ? min(a.kmax, e[v] - 2) : e[v] - 2;
+    const int nu = e[u] - 2, nv = v1 - v0 + 1;
+    if (nv <= 0 || t >= nu * nv) return;
+    int p[3];
+    p[ax] = sd ? e[ax] - 1 : 0;
+    p[u] = 1 + t % nu;
+    p[v] = v0 + t / nu;
+    a.n1[comp][lin(p[0], p[1], p[2], sy, sz)] = mur_face_value(a, comp, ax, sd, p, sy, sz);
+}
+
+// One face per blockIdx.z (f = face0 + z), one component per blockIdx.y (the x faces next to the
+// TF/SF planes after their correction).
+template <typename real>
+__global__ void k_mur_faces(MurArgs<real> a, int64_t sy, int64_t sz)
+{
+    dep_begin();
+    const int comp = blockIdx.y;
+    if (comp >= a.ncomp) return;
+    mur_face_node(a, comp, a.face0 + (int)blockIdx.z, (int)(blockIdx.x * blockDim.x + threadIdx.x), sy, sz);
 }
 
 // Edges and corners.  Class 0..2: the edges whose free axis is 0..2 (the two other coordinates
@@ -153,7 +167,10 @@ struct MurEdgeCoef {
 };
 
 // One edge (corners = false; t indexes the 12 edges' points) or corner (corners = true, t < 8)
-// point of component comp.  The corners read the new edge values of other blocks: through L2.
+// point of component comp.  The corners read the new edge values of other blocks (through L2).
+// A neighbour on a face that the same launch writes (faces of axes >= face0 / 2; the TMA stencil
+// wrote the x faces when face0 = 2) is evaluated here from the face formula, so the edges and
+// corners need not wait for the face blocks.
 template <typename real>
 __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeCoef<real>& cf, int64_t sy, int64_t sz,
                                           int comp, bool corners, int64_t t)
@@ -203,28 +220,58 @@ __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeC
         for (int s = 0; s < ns; ++s)
             if ((ei >> s) & 1) q[axes[s]] += sg[s];
         const int64_t id = lin(q[0], q[1], q[2], sy, sz);
-        if (ei != 0) num += cf.A[cls][ei] * (corners ? __ldcg(n1 + id) : n1[id]);
+        if (ei != 0) {
+            // the point's boundary axes: those not moved inward
+            int nb = 0, fa = 0;
+            for (int s = 0; s < ns; ++s)
+                if (!((ei >> s) & 1)) {
+                    ++nb;
+                    fa = axes[s];
+                }
+            real v;
+            if (nb == 1 && 2 * fa >= a.face0)
+                v = mur_face_value(a, comp, fa, q[fa] == 0 ? 0 : 1, q, sy, sz);   // a face node
+            else if (nb >= 1)
+                v = __ldcg(n1 + id);   // an edge node (corners), or an x-face node of the stencil
+            else
+                v = n1[id];            // the interior node
+            num += cf.A[cls][ei] * v;
+        }
         num += cf.B[cls][ei] * nm[id] + cf.C[cls] * n0[id];
     }
     n1[lin(p[0], p[1], p[2], sy, sz)] = num;
 }
 
 // The step tail, one launch of 1-D blocks of kTailThreads: blocks [0, ncomp nbe) the Mur edges of
-// component b / nbe; then npw blocks of the power step (plane points); then the blocks of the
-// next step's phase tables (node planes).  The last block to finish writes the 8 corners of every
-// component (the edges are in), adds the power partials (compensated, in a fixed order) into the
-// step's series entry once the window is complete, and advances the step state: nothing after
-// this launch in the step reads it.
+// component b / nbe; then npw blocks of the power step (plane points); then npt blocks of the
+// next step's phase tables (node planes); then nbb blocks that reduce the push's block records
+// into the deposit box (the whole box and its z chunks' xy boxes); then nfb blocks per face
+// f >= face0 and component (the Mur faces), which go last so that the others are scheduled first.
+// The face blocks leave without arriving; the last of the others to finish writes the 8 corners of every component (the edges are in; the
+// faces they need are evaluated in place), adds the power partials (compensated, in a fixed
+// order) into the step's series entry once the window is complete, and advances the step state:
+// nothing after this launch in the step reads it.
 constexpr int kTailThreads = 256;
+constexpr int kBoxRecs = 4 * kTailThreads;   // push records per deposit-box block of the tail
+constexpr int kBoxWin = 64;                  // z chunks per block kept in shared memory
 template <typename real>
 __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy,
-                                                            int64_t sz, int64_t maxpts, int nbe, int npw,
-                                                            Fields6<real> eb, Geom g, StepTail tl, unsigned* counter)
+                                                            int64_t sz, int64_t maxpts, int nfb, int nbe, int npw,
+                                                            int npt, int nbb, Fields6<real> eb, Geom g, StepTail tl,
+                                                            unsigned* counter)
 {
     dep_begin();
     __shared__ double sh[32];
-    const int b = (int)blockIdx.x;
     const int ne = a.ncomp * nbe;
+    const int nrest = ne + npw + npt + nbb;
+    if ((int)blockIdx.x >= nrest) {
+        const int fi = (int)blockIdx.x - nrest;
+        const int fb = fi % (nfb * a.ncomp);
+        mur_face_node(a, fb / nfb, a.face0 + fi / (nfb * a.ncomp), (fb % nfb) * kTailThreads + (int)threadIdx.x, sy,
+                      sz);
+        return;
+    }
+    const int b = (int)blockIdx.x;
     if (b < ne) {
         const int64_t t = (int64_t)(b % nbe) * blockDim.x + threadIdx.x;
         if (t < maxpts) mur_point(a, cf, sy, sz, b / nbe, false, t);
@@ -234,15 +281,68 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
         const double c = pl < (int64_t)g.nx * g.ny ? power_point(eb, g, tl.power, sd, pl) : 0.0;
         const double tot = block_sum(c, sh);
         if (threadIdx.x == 0) tl.partial[b - ne] = tot;
-    } else {
+    } else if (b < ne + npw + npt) {
         const int iz = (b - ne - npw) * (int)blockDim.x + (int)threadIdx.x;
         if (iz < tl.phase.nz) {
             // the next step's lab offset, from the same function that advances the state below
             const StepDev nx = step_state(tl.sd->next, tl.sc);
             phase_tables_entry(tl.phase, nx.Z0, iz);
         }
+    } else {
+        // the deposit box from the push's block records: this block takes kBoxRecs consecutive
+        // records (cell order, so they span few z chunks), gathers the whole box and the xy
+        // boxes of the chunks in a window of kBoxWin chunks in shared memory, and adds them to
+        // the deposit box with a few atomics (a chunk outside the window goes straight out)
+        __shared__ int sg[6], swin[kBoxWin][4], scb;
+        const int nchunk = emit_chunks(g.nz);
+        const int64_t base = (int64_t)(b - ne - npw - npt) * kBoxRecs;
+        if (threadIdx.x < 6) sg[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
+        for (int q = threadIdx.x; q < 4 * kBoxWin; q += blockDim.x)
+            swin[q >> 2][q & 3] = (q & 3) < 2 ? 0x7fffffff : (int)0x80000000;
+        if (threadIdx.x == 0) scb = 0x7fffffff;
+        __syncthreads();
+        int v[kBoxRecs / kTailThreads][6];
+        for (int i = 0; i < kBoxRecs / kTailThreads; ++i) {
+            const int64_t r = base + i * kTailThreads + threadIdx.x;
+            for (int q = 0; q < 6; ++q)
+                v[i][q] = r < tl.nrec ? __ldcg(tl.box_rec + 6 * r + q) : (q < 3 ? 0x7fffffff : (int)0x80000000);
+            if (v[i][0] != 0x7fffffff) {
+                for (int q = 0; q < 3; ++q) {
+                    atomicMin(sg + q, v[i][q]);
+                    atomicMax(sg + 3 + q, v[i][3 + q]);
+                }
+                atomicMin(&scb, max((v[i][2] - 2) / kEmitKZ, 0));
+            }
+        }
+        __syncthreads();
+        const int cb = scb;
+        for (int i = 0; i < kBoxRecs / kTailThreads; ++i) {
+            if (v[i][0] == 0x7fffffff) continue;
+            // the z chunks of this record's node planes [lo_z - 1, hi_z + 2]
+            const int c0 = max((v[i][2] - 2) / kEmitKZ, 0), c1 = min((v[i][5] + 1) / kEmitKZ, nchunk - 1);
+            for (int c = c0; c <= c1; ++c) {
+                int* w = c - cb < kBoxWin ? swin[c - cb] : tl.box_out + 6 + 4 * c;
+                atomicMin(w, v[i][0]);
+                atomicMin(w + 1, v[i][1]);
+                atomicMax(w + 2, v[i][3]);
+                atomicMax(w + 3, v[i][4]);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 6 && sg[0] != 0x7fffffff) {
+            if (threadIdx.x < 3) atomicMin(tl.box_out + threadIdx.x, sg[threadIdx.x]);
+            else atomicMax(tl.box_out + threadIdx.x, sg[threadIdx.x]);
+        }
+        for (int q = threadIdx.x; q < kBoxWin; q += blockDim.x)
+            if (swin[q][0] != 0x7fffffff && cb + q < nchunk) {
+                int* w = tl.box_out + 6 + 4 * (cb + q);
+                atomicMin(w, swin[q][0]);
+                atomicMin(w + 1, swin[q][1]);
+                atomicMax(w + 2, swin[q][2]);
+                atomicMax(w + 3, swin[q][3]);
+            }
     }
-    if (last_block(counter)) {
+    if (last_block(counter, (unsigned)nrest)) {
         const int c = (int)threadIdx.x >> 3;
         if (c < a.ncomp) mur_point(a, cf, sy, sz, c, true, (int64_t)(threadIdx.x & 7));
         const StepDev sd = *tl.sd;
@@ -321,10 +421,7 @@ struct EmitArgs {
     int* err;            // set when a bounded wait on the tensor copies expired (may be null)
 };
 
-#ifndef MITHRA_EMIT_KZ
-#define MITHRA_EMIT_KZ 8
-#endif
-constexpr int EX = 32, EY = 8, EKZ = MITHRA_EMIT_KZ;  // tile and planes per block
+constexpr int EX = 32, EY = 8, EKZ = kEmitKZ;        // tile and planes per block
 constexpr int RL = EX + 2, RH = EY + 2;               // region: columns i0-1 .. i0+32, rows j0-1 .. j0+8
 constexpr int RW = kEmitBoxW, RN = RW * RH;           // region rows are stored kEmitBoxW wide
 constexpr int EHALO = 2 * RL + 2 * EY;                // region positions outside the tile
@@ -382,8 +479,9 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
     EmitSmem<real>& sm = *reinterpret_cast<EmitSmem<real>*>(
         emit_smem_raw + ((128 - (mithra::su32(emit_smem_raw) & 127)) & 127));
     const int t = threadIdx.x, tx = t % EX, ty = t / EX;
-    if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t < 6)
-        a.box_reset[t] = t < 3 ? 0x7fffffff : (int)0x80000000;
+    if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+        for (int q = t; q < 6 + 4 * a.nchunk; q += ENT)
+            a.box_reset[q] = (q < 6 ? q < 3 : (q - 6) % 4 < 2) ? 0x7fffffff : (int)0x80000000;
     // nodes [lo - 1, hi + 2] around the cells of the last deposit: the particles gather at their
     // cells' nodes next step, and with sub-steps they move up to one cell during that step
     int bl[3] = {1, 1, 1}, bh[3] = {g.nx - 2, g.ny - 2, g.nz - 2};
@@ -394,12 +492,21 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
             bh[d] = min(__ldg(a.box + 3 + d) + 2, d == 0 ? g.nx - 2 : (d == 1 ? g.ny - 2 : g.nz - 2));
         }
     }
+    // the nodes [lo - 1, hi + 2] of z chunk c's xy box of cells (empty: x0 > x1)
+    auto chunk_xy = [&](int c, int& x0, int& x1, int& y0, int& y1) {
+        const int* cb = a.box + 6 + 4 * c;
+        x0 = max(__ldg(cb) - 1, 1);
+        y0 = max(__ldg(cb + 1) - 1, 1);
+        x1 = min(__ldg(cb + 2) + 2, g.nx - 2);
+        y1 = min(__ldg(cb + 3) + 2, g.ny - 2);
+    };
     const bool plane_slice = (int)blockIdx.z == a.nchunk;   // the power plane, whole interior
     int xl = 1, xh = g.nx - 2, yl = 1, yh = g.ny - 2, ka, kb;
     if (plane_slice) {
         ka = kb = a.kp;
     } else {
         xl = bl[0], xh = bh[0], yl = bl[1], yh = bh[1];
+        if (a.box) chunk_xy((int)blockIdx.z, xl, xh, yl, yh);   // this chunk's part of the box
         ka = max(1 + (int)blockIdx.z * EKZ, bl[2]);
         kb = min((int)(blockIdx.z + 1) * EKZ, bh[2]);
     }
@@ -411,8 +518,13 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
     if (ka > kb || xl > xh || yl > yh || i0 > xh || j0 > yh) return;
     const int i = i0 + tx, j = j0 + ty;
     const bool emit = i >= xl && i <= xh && j >= yl && j <= yh;
-    // with a box, the plane slice leaves the box's nodes to the box blocks
-    const bool skip_xy = plane_slice && a.box && i >= bl[0] && i <= bh[0] && j >= bl[1] && j <= bh[1];
+    // with a box, the plane slice leaves the nodes of the chunk's box to the box blocks
+    bool skip_xy = false;
+    if (plane_slice && a.box && a.kp >= bl[2] && a.kp <= bh[2]) {
+        int x0, x1, y0, y1;
+        chunk_xy((a.kp - 1) / EKZ, x0, x1, y0, y1);
+        skip_xy = i >= x0 && i <= x1 && j >= y0 && j <= y1;
+    }
     const bool clear = a.box && !plane_slice;
     const int64_t sy = g.sy, sz = g.sz;
 
@@ -713,25 +825,15 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
         a.ft[ax][0] = (real)m.ft[ax][0];
         a.ft[ax][1] = (real)m.ft[ax][1];
     }
-    int nl = 0;
-    {
-        int64_t maxface = 0;
-        for (int c = 0; c < ncomp; ++c) {
-            const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
-            for (int ax = 0; ax < 3; ++ax) {
-                const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
-                maxface = std::max<int64_t>(maxface, (e[u] - 2) * (e[v] - 2));
-            }
+    int64_t maxface = 0;
+    for (int c = 0; c < ncomp; ++c) {
+        const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
+        for (int ax = a.face0 / 2; ax < 3; ++ax) {
+            const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
+            maxface = std::max<int64_t>(maxface, (e[u] - 2) * (e[v] - 2));
         }
-        const int thr = 256;
-        {
-            const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_mur_faces<real>,
-                                              dim3((unsigned)((maxface + thr - 1) / thr), ncomp, 6 - a.face0),
-                                              dim3(thr), 0, st, a, g.sy, g.sz);
-            if (le != cudaSuccess) return le;
-        }
-        ++nl;
     }
+    const int nfb = (int)((maxface + kTailThreads - 1) / kTailThreads);
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
     const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
     const int nbe = (int)((edges + kTailThreads - 1) / kTailThreads);
@@ -743,12 +845,15 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     Fields6<real> E6;
     E6.p = (real*)tail.eb;
     {
+        const int nface = nfb * ncomp * (6 - a.face0);
+        // deposit-box blocks: kBoxRecs push records each
+        const int nbb = (int)((tail.nrec + kBoxRecs - 1) / kBoxRecs);
         const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_step_tail<real>,
-                                          dim3((unsigned)(ncomp * nbe + npw + npt)), dim3(kTailThreads), 0, st, a, ec,
-                                          g.sy, g.sz, edges, nbe, npw, E6, g, tail, counter);
+                                          dim3((unsigned)(nface + ncomp * nbe + npw + npt + nbb)), dim3(kTailThreads), 0,
+                                          st, a, ec, g.sy, g.sz, edges, nfb, nbe, npw, npt, nbb, E6, g, tail, counter);
         if (le != cudaSuccess) return le;
     }
-    count_launches(nl + 1);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -238,13 +238,16 @@ struct StepTail {
     PhaseTables phase;      // the tables of step n + 1
     StepDev* sd;
     StepConst sc;
+    const int* box_rec;     // the push's per-block bounds (nrec records of six ints)
+    int64_t nrec;
+    int* box_out;           // the deposit box they reduce into (deposit_box_ints, reset to empty)
 };
 
-// Mur boundary values of level n+1 and the step tail: the faces (unless the TMA stencil of this
-// step has written them all: x_faces_done covers the x faces), then one launch with the edges,
-// the tail's power and phase-table blocks, and in the last block to finish the corners, the
-// power's sum and the step state's advance (`counter` is a zeroed device word that the launch
-// leaves zeroed).
+// Mur boundary values of level n+1 and the step tail, in one launch: the faces (x_faces_done: the
+// TMA stencil of this step has written the x faces), the edges (their face neighbours evaluated
+// in place), the tail's power, phase-table and deposit-box blocks, and in the last of the edge,
+// power, table and box blocks to finish the corners, the power's sum and the step state's
+// advance (`counter` is a zeroed device word that the launch leaves zeroed).
 template <typename real>
 cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int ncomp, bool x_faces_done,
                        unsigned* counter, const StepTail& tail, cudaStream_t st);
@@ -261,8 +264,15 @@ struct EmitMaps {
 bool emit_maps(const TmaMaps* maps, int lev_n, int lev_n1, EmitMaps* out);
 
 // Region of one E/B emission: box == null emits the whole interior and clears nothing.
+// Planes per emission block; the deposit boxes also hold, per such z chunk c of node planes
+// [1 + c kEmitKZ, (c + 1) kEmitKZ], the xy box of the cells whose gather or deposit reaches it.
+constexpr int kEmitKZ = 8;
+__host__ __device__ inline int emit_chunks(int nz) { return (nz - 2 + kEmitKZ - 1) / kEmitKZ; }
+// Ints of one deposit box: [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the cells, then per z chunk
+// [lo_x, lo_y, hi_x, hi_y].
+inline int deposit_box_ints(int nz) { return 6 + 4 * emit_chunks(nz); }
 struct EmitBox {
-    const int* box;      // device: cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit
+    const int* box;      // device: the deposit box of the last push (deposit_box_ints)
     int* box_reset;      // device: box the next push reduces into, reset to empty by the emission
     int kp;              // plane always emitted in full (< 0: none)
     bool clear;          // clear the sources inside the box
@@ -313,10 +323,15 @@ struct PushConst {
     float ltE, ltB, E0f, E0cf, w0f, izrf, zrf, kLf;
 };
 
+// box_rec: per block of 128 particles, the six bounds [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the
+// cells its particles deposited into or end in (empty bounds: none); the step tail reduces them
+// into the deposit box the next emission reads.
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,
-                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, int* box_out,
+                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, int* box_rec,
                         cudaStream_t st);
+// Blocks of 128 particles the push launches.
+inline int64_t push_blocks(int64_t np) { return (np + 127) / 128; }
 
 template <typename real>
 cudaError_t launch_boost(const double* lab6, int64_t np, const Particles<real>& P, const Geom& g,

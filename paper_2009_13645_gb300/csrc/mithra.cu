@@ -251,7 +251,8 @@ struct RunT final : mithra_run {
     double* ser_b = nullptr;   // rows(ser_cap) x 15
     double* rest_buf = nullptr;
     int64_t onaxis_id = 0;
-    int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (cells lo_xyz, hi_xyz)
+    int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (deposit_box_ints each)
+    int* box_rec = nullptr;              // the push's per-block bounds (six ints per block of 128)
     double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables, FP64 path (one per planar field)
     float4* ptab32[2] = {nullptr, nullptr};  // FP32-mixed path: phase and edge distances rounded to FP32
     float4* ptab32a = nullptr;               // FP32-mixed path, undulator array: module peak fields per plane
@@ -275,8 +276,16 @@ struct RunT final : mithra_run {
     // Make the box read by the next emission cover every active cell (start, new particles).
     int full_box(int which)
     {
-        const int h[6] = {1, 1, 1, g.nx - 3, g.ny - 3, g.nz - 3};
-        CU(cudaMemcpyAsync(box[which], h, sizeof h, cudaMemcpyHostToDevice, stream));
+        std::vector<int> h(deposit_box_ints(g.nz));
+        const int whole[6] = {1, 1, 1, g.nx - 3, g.ny - 3, g.nz - 3};
+        for (int q = 0; q < 6; ++q) h[q] = whole[q];
+        for (size_t q = 6; q < h.size(); q += 4) {
+            h[q] = 1;
+            h[q + 1] = 1;
+            h[q + 2] = g.nx - 3;
+            h[q + 3] = g.ny - 3;
+        }
+        CU(cudaMemcpyAsync(box[which], h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
         CU(cudaStreamSynchronize(stream));
         return MITHRA_OK;
     }
@@ -382,7 +391,10 @@ struct RunT final : mithra_run {
         if (bunch_every > 0 && !(bunch_partial = (double*)mem.get((size_t)14 * npartial * 8)))
             return fail(MITHRA_ENOMEM, "device allocation failed (bunch sampling)");
         for (int b = 0; b < 2; ++b)
-            if (!(box[b] = (int*)mem.get(6 * sizeof(int)))) return fail(MITHRA_ENOMEM, "device allocation failed (box)");
+            if (!(box[b] = (int*)mem.get((size_t)deposit_box_ints(g.nz) * sizeof(int))))
+                return fail(MITHRA_ENOMEM, "device allocation failed (box)");
+        if (!(box_rec = (int*)mem.get((size_t)6 * std::max<int64_t>(push_blocks(np), 1) * sizeof(int))))
+            return fail(MITHRA_ENOMEM, "device allocation failed (box records)");
         if (ef.kind == 0 || ef.kind == 1) {
             for (int b = 0; b < (ef.kind == 1 ? 2 : 1); ++b) {
                 if (sizeof(real) == 8) ptab[b] = (double2*)mem.get((size_t)g.nz * sizeof(double2));
@@ -594,7 +606,7 @@ struct RunT final : mithra_run {
         pc.zrf = (float)ef.zr;
         pc.kLf = (float)ef.kL;
         pbeg(MITHRA_K_PUSH, &e0);
-        CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box[(n + 1) % 2], stream));
+        CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box_rec, stream));
         pend(MITHRA_K_PUSH, e0);
         if (bunch_every > 0) {
             pbeg(MITHRA_K_POWER, &e0);
@@ -668,6 +680,9 @@ struct RunT final : mithra_run {
             tl.phase = phase_tables();
             tl.sd = sd;
             tl.sc = scst;
+            tl.box_rec = box_rec;
+            tl.nrec = np > 0 ? push_blocks(np) : 0;
+            tl.box_out = box[(n + 1) % 2];   // reset by this step's emission
             CU(launch_mur<real>(L, g, mur_order, ncomp, xf, counters, tl, stream));
         }
         pend(MITHRA_K_MUR, e0);

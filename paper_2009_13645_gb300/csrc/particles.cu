@@ -498,9 +498,11 @@ __device__ __forceinline__ void block_box(const int lo[3], const int hi[3], int 
     for (int q = 0; q < 6; ++q) out[q] = res[q];
 }
 
-// Block-wide min/max of the cells this block deposited into (or will gather from next step),
-// merged into box_out with one atomic per bound and block.
-__device__ __forceinline__ void box_merge(int lo[3], int hi[3], int* box_out)
+// Block-wide min/max of the cells this block deposited into (or will gather from next step): its
+// six bounds [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] go to rec[6 b] for block b (empty bounds when it
+// has no active cell).  The step tail reduces the records into the deposit box; atomics here, on
+// the same few words from every block, slowed the push.
+__device__ __forceinline__ void box_record(int lo[3], int hi[3], int* rec)
 {
     __shared__ int sh[6][4];   // 128 threads = 4 warps
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -518,11 +520,7 @@ __device__ __forceinline__ void box_merge(int lo[3], int hi[3], int* box_out)
         const int q = threadIdx.x;
         int v = sh[q][0];
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = q < 3 ? min(v, sh[q][k]) : max(v, sh[q][k]);
-        if (q < 3) {
-            if (v != 0x7fffffff) atomicMin(box_out + q, v);
-        } else if (v != (int)0x80000000) {
-            atomicMax(box_out + q, v);
-        }
+        rec[6 * (int64_t)blockIdx.x + q] = v;
     }
 }
 
@@ -674,7 +672,7 @@ constexpr int kTileInts = MITHRA_PUSH_TILE_INTS;
 template <typename real>
 __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCKS_F32 : MITHRA_PUSH_MIN_BLOCKS_F64)
     k_push(Particles<real> P, int64_t np, Geom g, ExtField ef, Fields6<real> eb, Fields4<real> src, PushConst pc,
-           int* box_out)
+           int* box_rec)
 {
     dep_begin();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -867,7 +865,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
         P.uy[p] = u[1];
         P.uz[p] = u[2];
     }
-    box_merge(lo, hi, box_out);
+    box_record(lo, hi, box_rec);
 }
 
 // Lab-frame macro-particles (x, y, z relative to the bunch reference at t' = 0, gamma*beta) to
@@ -930,13 +928,13 @@ static inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1)
 
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,
-                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, int* box_out,
+                        const Fields6<real>& eb, const Fields4<real>& src, const PushConst& pc, int* box_rec,
                         cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
     {
         const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_push<real>, dim3(nblocks(np, 128)), dim3(128), 0,
-                                          st, P, np, g, ef, eb, src, pc, box_out);
+                                          st, P, np, g, ef, eb, src, pc, box_rec);
         if (le != cudaSuccess) return le;
     }
     count_launches(1);
