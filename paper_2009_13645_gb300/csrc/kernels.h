@@ -333,6 +333,9 @@ cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, con
 // Blocks of 128 particles the push launches.
 inline int64_t push_blocks(int64_t np) { return (np + 127) / 128; }
 
+// *flag |= 1 when one of the n values at a is not finite (flag: a device word).
+cudaError_t launch_finite_check(const double* a, int64_t n, int* flag, cudaStream_t st);
+
 template <typename real>
 cudaError_t launch_boost(const double* lab6, int64_t np, const Particles<real>& P, const Geom& g,
                          const ExtField& ef, double z_ref, cudaStream_t st);

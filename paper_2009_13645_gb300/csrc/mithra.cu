@@ -1189,8 +1189,18 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
             return fail(MITHRA_ENOMEM, "device allocation failed (lab particles)");
         }
         cudaError_t e = cudaSuccess;
+        int* bad = nullptr;   // set on the device when a given particle value is not finite
         if (b.lab_particles) {
-            e = cudaMemcpyAsync(lab, b.lab_particles, (size_t)b.n * 6 * 8, cudaMemcpyHostToDevice, r->stream);
+            if (!(bad = (int*)r->mem.get(sizeof(int)))) {
+                r->mem.release(lab);
+                r->destroy_all();
+                delete r;
+                return fail(MITHRA_ENOMEM, "device allocation failed (check word)");
+            }
+            e = cudaMemsetAsync(bad, 0, sizeof(int), r->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(lab, b.lab_particles, (size_t)b.n * 6 * 8, cudaMemcpyHostToDevice, r->stream);
+            if (e == cudaSuccess) e = launch_finite_check(lab, (int64_t)b.n * 6, bad, r->stream);
         } else {
             // generated ellipsoid bunch (Sec. BUNCH, bunch-initialization): the quasi-random loader
             // with the bunch's parameters, written straight to device memory
@@ -1223,11 +1233,19 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
         }
         if (e == cudaSuccess) e = launch_boost<real>(lab, b.n, r->P, g, r->ef, d.z_ref, r->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+        int bad_h = 0;
+        if (e == cudaSuccess && bad) e = cudaMemcpy(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost);
         r->mem.release(lab);
+        if (bad) r->mem.release(bad);
         if (e != cudaSuccess) {
             r->destroy_all();
             delete r;
             return fail(MITHRA_ECUDA, std::string("particle boost: ") + cudaGetErrorString(e));
+        }
+        if (bad_h) {
+            r->destroy_all();
+            delete r;
+            return fail(MITHRA_EINVAL, "create: non-finite particle value");
         }
         if (r->sort_every > 0 && b.n > 1 && (rc = r->sort_now())) {
             r->destroy_all();
@@ -1284,10 +1302,8 @@ int mithra::validate_request(const mithra_grid* gr, double dt_lab, const mithra_
     if (b->n < 0 || b->n >= (int64_t(1) << 31)) return fail(MITHRA_EINVAL, "create: particle count out of range");
     if (b->n > 0) {
         if (!(b->charge_e > 0)) return fail(MITHRA_EINVAL, "create: charge_e must be > 0");
-        if (b->lab_particles) {
-            for (int64_t i = 0; i < 6 * b->n; ++i)
-                if (!std::isfinite(b->lab_particles[i])) return fail(MITHRA_EINVAL, "create: non-finite particle value");
-        } else {
+        // (non-finite given particle values are found on the device at creation)
+        if (!b->lab_particles) {
             if (!finite_all({b->rel_espread, b->sig_x, b->sig_y, b->eps_n_x, b->eps_n_y, b->cse_sigma, b->lambda_r,
                              b->bunching, b->bunching_phase}))
                 return fail(MITHRA_EINVAL, "create: non-finite bunch parameter");

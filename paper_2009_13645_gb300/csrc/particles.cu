@@ -868,6 +868,22 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
     box_record(lo, hi, box_rec);
 }
 
+__global__ void k_finite_check(const double* __restrict__ a, int64_t n, int* flag)
+{
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad = bad || !isfinite(a[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_finite_check(const double* a, int64_t n, int* flag, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_finite_check<<<1216, 256, 0, st>>>(a, n, flag);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // Lab-frame macro-particles (x, y, z relative to the bunch reference at t' = 0, gamma*beta) to
 // the rest frame at the common time T0 + dt/2 (the time of r^{1/2}).
 template <typename real>

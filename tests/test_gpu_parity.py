@@ -290,6 +290,23 @@ def test_edge_cases_empty_and_outside():
     _compare_run(o, g, 30, 1e-11, 1e-10, w2, lab2)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_non_finite_particle_rejected(precision):
+    """A non-finite value among the given lab particles is found on the device after the copy:
+    mithra_create returns EINVAL and leaves no run; the same bunch without it creates one."""
+    w = workloads.scaled(SMALL, n_particles=5000)
+    lab = workloads.lab_bunch(w)
+    for bad in (np.nan, np.inf, -np.inf):
+        l2 = lab.copy()
+        l2[4321, 4] = bad
+        with pytest.raises(mithra.MithraError) as ei:
+            mithra.Run.from_workload(w, l2, precision=precision)
+        assert ei.value.code == mithra.EINVAL
+    g = mithra.Run.from_workload(w, lab, precision=precision)
+    g.step(1)
+    g.close()
+
+
 def test_fullsize_fel_two_steps():
     """The full 128x128x512 grid with 2M macro-particles, in the bench's launch configuration,
     two steps against the oracle (all potentials, a sample of particles).  Errors of the vector
