@@ -89,19 +89,43 @@ extern "C" const char* mithra_kernel_name(int id)
 // 16-byte vector atomics of the deposit flush and the vector loads rely on it.  cudaMalloc
 // guarantees it; a caller-installed allocator may return any alignment, so its blocks are
 // requested 256 bytes longer and aligned here (the original pointer is what gets freed).
+// Without a caller's allocator the run first reserves one slab for its known arrays and hands
+// them out of it (one cudaMalloc instead of some fifty: a third of the time to create the FEL
+// run); what does not fit, and temporaries, take their own cudaMalloc.
 struct DevMem {
     struct Block {
         void* p;      // the aligned pointer handed out
         size_t bytes; // bytes taken from the allocator
-        void* raw;    // the pointer the allocator returned
+        void* raw;    // the pointer the allocator returned (null: part of the slab)
     };
     Allocator a;
     std::vector<Block> blocks;
     size_t total = 0;
-    void* get(size_t bytes)
+    char* slab = nullptr;
+    size_t slab_size = 0, slab_used = 0;
+    void reserve(size_t bytes)
+    {
+        if (a.alloc || slab) return;
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (cudaMalloc((void**)&slab, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            slab = nullptr;
+            return;
+        }
+        slab_size = bytes;
+    }
+    // temp: a block released soon (not taken from the slab)
+    void* get(size_t bytes, bool temp = false)
     {
         if (bytes == 0) bytes = 16;
         bytes = (bytes + 255) & ~(size_t)255;
+        if (!temp && slab && slab_used + bytes <= slab_size) {
+            void* p = slab + slab_used;
+            slab_used += bytes;
+            blocks.push_back(Block{p, bytes, nullptr});
+            total += bytes;
+            return p;
+        }
         void* raw = nullptr;
         if (a.alloc) {
             bytes += 256;
@@ -121,8 +145,14 @@ struct DevMem {
         for (size_t i = 0; i < blocks.size(); ++i)
             if (blocks[i].p == p) {
                 total -= blocks[i].bytes;
-                if (a.free_fn) a.free_fn(a.ctx, blocks[i].raw);
-                else cudaFree(blocks[i].raw);
+                if (!blocks[i].raw) {
+                    // a slab block: its space is reused only if it was the last one handed out
+                    if ((char*)p + blocks[i].bytes == slab + slab_used) slab_used -= blocks[i].bytes;
+                } else if (a.free_fn) {
+                    a.free_fn(a.ctx, blocks[i].raw);
+                } else {
+                    cudaFree(blocks[i].raw);
+                }
                 blocks.erase(blocks.begin() + (long)i);
                 return;
             }
@@ -130,9 +160,13 @@ struct DevMem {
     void release_all()
     {
         for (auto& b : blocks) {
+            if (!b.raw) continue;
             if (a.free_fn) a.free_fn(a.ctx, b.raw);
             else cudaFree(b.raw);
         }
+        if (slab) cudaFree(slab);
+        slab = nullptr;
+        slab_size = slab_used = 0;
         blocks.clear();
         total = 0;
     }
@@ -1176,13 +1210,18 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
         return fail(MITHRA_ECUDA, "cudaStreamCreateWithFlags failed");
     }
     r->own_stream = true;
+    {
+        // the run's arrays for its first 1024 steps, without the boost's temporary lab copy
+        const int64_t nb = b.n > 0 ? b.n : 1;
+        r->mem.reserve((size_t)(mithra::footprint(&gr, &u, &b, 1024) - ((nb * 48 + 255) & ~(int64_t)255)));
+    }
     if ((rc = r->alloc_all())) {
         r->destroy_all();
         delete r;
         return rc;
     }
     if (b.n > 0) {
-        double* lab = (double*)r->mem.get((size_t)b.n * 6 * 8);
+        double* lab = (double*)r->mem.get((size_t)b.n * 6 * 8, true);
         if (!lab) {
             r->destroy_all();
             delete r;
@@ -1191,7 +1230,7 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
         cudaError_t e = cudaSuccess;
         int* bad = nullptr;   // set on the device when a given particle value is not finite
         if (b.lab_particles) {
-            if (!(bad = (int*)r->mem.get(sizeof(int)))) {
+            if (!(bad = (int*)r->mem.get(sizeof(int), true))) {
                 r->mem.release(lab);
                 r->destroy_all();
                 delete r;
@@ -1220,7 +1259,7 @@ int create_t(const mithra_grid& gr, double dt_lab, const mithra_undulator& u, co
             el.shot_noise = b.shot_noise;
             el.charge_e = b.charge_e;
             struct Adapter {
-                static void* get(void* c, size_t n) { return ((DevMem*)c)->get(n); }
+                static void* get(void* c, size_t n) { return ((DevMem*)c)->get(n, true); }
                 static void put(void* c, void* q) { ((DevMem*)c)->release(q); }
             };
             rc = ellipsoid_device(el, b.n, b.seed, lab, Adapter::get, Adapter::put, &r->mem, r->stream);
@@ -1364,7 +1403,7 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
     const int64_t ncell = (int64_t)gr->nx * gr->ny * gr->nz;
     const int64_t rs = gr->precision == 0 ? 8 : 4;
     const int64_t n = b->n > 0 ? b->n : 1;
-    int64_t t = 22 * up(ncell * rs);                                          // potentials, sources, E/B
+    int64_t t = 16 * up(ncell * rs) + up(ncell * rs * kEBStride);             // potentials, sources, E/B
     t += 2 * (4 * up(n * 4) + 3 * up(n * rs) + 3 * up(n * 8));               // particles and sort copy
     t += 2 * up(n * 4) + 2 * up((ncell + 1) * 4) + up((ncell / 4096 + 16) * 4);   // sort scratch
     // the power window M is only known after the rest frame is fixed; bound it by the run's steps
@@ -1374,7 +1413,8 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
     int64_t cap = 1024;
     while (cap < nsteps) cap *= 2;
     t += 4 * up(cap * 8);                                                     // series (old and new while growing)
-    t += 2 * up(6 * 4) + 2 * up(gr->nz * 32);                                 // boxes, phase tables
+    t += 2 * up(deposit_box_ints(gr->nz) * 4) + up(6 * push_blocks(n) * 4) + 2 * up(gr->nz * 32);
+    t += up(gr->nz * 16);                                                     // boxes and records, phase tables
     t += up(n * 48);                                                          // lab particles during the boost
     if (gr->nf_points > 0) {                                                  // spectrum: ring, accumulators, series
         const int64_t nf = gr->nf_points;
