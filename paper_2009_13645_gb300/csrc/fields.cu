@@ -245,30 +245,42 @@ __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeC
 // The step tail, one launch of 1-D blocks of kTailThreads: blocks [0, ncomp nbe) the Mur edges of
 // component b / nbe; then npw blocks of the power step (plane points); then npt blocks of the
 // next step's phase tables (node planes); then nbb blocks that reduce the push's block records
-// into the deposit box (the whole box and its z chunks' xy boxes); then nfb blocks per face
-// f >= face0 and component (the Mur faces), which go last so that the others are scheduled first.
-// The face blocks leave without arriving; the last of the others to finish writes the 8 corners of every component (the edges are in; the
-// faces they need are evaluated in place), adds the power partials (compensated, in a fixed
-// order) into the step's series entry once the window is complete, and advances the step state:
-// nothing after this launch in the step reads it.
+// into the deposit box (the whole box and its z chunks' xy boxes); then the Mur faces f >= face0,
+// per normal axis as many blocks per side and component as its largest face needs, which go
+// last so that the others are scheduled first.  The face blocks leave without arriving; the last
+// of the others to finish writes the 8 corners of every component (the edges are in; the faces
+// they need are evaluated in place), adds the power partials (compensated, in a fixed order) into
+// the step's series entry once the window is complete, and advances the step state: nothing
+// after this launch in the step reads it.
 constexpr int kTailThreads = 256;
 constexpr int kBoxRecs = 4 * kTailThreads;   // push records per deposit-box block of the tail
 constexpr int kBoxWin = 64;                  // z chunks per block kept in shared memory
 template <typename real>
 __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy,
-                                                            int64_t sz, int64_t maxpts, int nfb, int nbe, int npw,
-                                                            int npt, int nbb, Fields6<real> eb, Geom g, StepTail tl,
-                                                            unsigned* counter)
+                                                            int64_t sz, int64_t maxpts, int nfx, int nfy, int nfz,
+                                                            int nbe, int npw, int npt, int nbb, Fields6<real> eb,
+                                                            Geom g, StepTail tl, unsigned* counter)
 {
     dep_begin();
     __shared__ double sh[32];
     const int ne = a.ncomp * nbe;
     const int nrest = ne + npw + npt + nbb;
     if ((int)blockIdx.x >= nrest) {
-        const int fi = (int)blockIdx.x - nrest;
-        const int fb = fi % (nfb * a.ncomp);
-        mur_face_node(a, fb / nfb, a.face0 + fi / (nfb * a.ncomp), (fb % nfb) * kTailThreads + (int)threadIdx.x, sy,
-                      sz);
+        // the faces normal to x (nfx blocks per side and component; none when the stencil wrote
+        // them), then to y (nfy), then to z (nfz)
+        int fi = (int)blockIdx.x - nrest, ax = 0, nf = nfx;
+        if (fi >= 2 * a.ncomp * nfx) {
+            fi -= 2 * a.ncomp * nfx;
+            ax = 1;
+            nf = nfy;
+            if (fi >= 2 * a.ncomp * nfy) {
+                fi -= 2 * a.ncomp * nfy;
+                ax = 2;
+                nf = nfz;
+            }
+        }
+        const int side = fi / (a.ncomp * nf), r = fi - side * a.ncomp * nf;
+        mur_face_node(a, r / nf, 2 * ax + side, (r % nf) * kTailThreads + (int)threadIdx.x, sy, sz);
         return;
     }
     const int b = (int)blockIdx.x;
@@ -417,7 +429,8 @@ struct EmitArgs {
     int nchunk;          // blocks along z covering the box; a further z slice emits plane kp
     int kp;              // plane emitted in full (< 0: none)
     const int* box;      // cells [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the last deposit; null: whole grid
-    int* box_reset;      // box the next push reduces into: reset to empty here (may be null)
+    int* box_reset;      // box the next push reduces into: reset to empty here, with the far-move flag
+                         // after it (may be null)
     int* err;            // set when a bounded wait on the tensor copies expired (may be null)
 };
 
@@ -480,8 +493,9 @@ __global__ void __launch_bounds__(ENT, sizeof(real) == 4 ? 4 : 2)
         emit_smem_raw + ((128 - (mithra::su32(emit_smem_raw) & 127)) & 127));
     const int t = threadIdx.x, tx = t % EX, ty = t / EX;
     if (a.box_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
-        for (int q = t; q < 6 + 4 * a.nchunk; q += ENT)
-            a.box_reset[q] = (q < 6 ? q < 3 : (q - 6) % 4 < 2) ? 0x7fffffff : (int)0x80000000;
+        for (int q = t; q <= 6 + 4 * a.nchunk; q += ENT)
+            a.box_reset[q] = q == 6 + 4 * a.nchunk ? 0
+                                                    : ((q < 6 ? q < 3 : (q - 6) % 4 < 2) ? 0x7fffffff : (int)0x80000000);
     // nodes [lo - 1, hi + 2] around the cells of the last deposit: the particles gather at their
     // cells' nodes next step, and with sub-steps they move up to one cell during that step
     int bl[3] = {1, 1, 1}, bh[3] = {g.nx - 2, g.ny - 2, g.nz - 2};
@@ -825,15 +839,17 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
         a.ft[ax][0] = (real)m.ft[ax][0];
         a.ft[ax][1] = (real)m.ft[ax][1];
     }
-    int64_t maxface = 0;
-    for (int c = 0; c < ncomp; ++c) {
-        const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
-        for (int ax = a.face0 / 2; ax < 3; ++ax) {
+    // face blocks per side and component along each normal axis: the largest face of the axis
+    int nf[3] = {0, 0, 0};
+    for (int ax = a.face0 / 2; ax < 3; ++ax) {
+        int64_t maxface = 0;
+        for (int c = 0; c < ncomp; ++c) {
+            const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
             const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
-            maxface = std::max<int64_t>(maxface, (e[u] - 2) * (e[v] - 2));
+            maxface = std::max<int64_t>(maxface, std::max<int64_t>(e[u] - 2, 0) * std::max<int64_t>(e[v] - 2, 0));
         }
+        nf[ax] = (int)((maxface + kTailThreads - 1) / kTailThreads);
     }
-    const int nfb = (int)((maxface + kTailThreads - 1) / kTailThreads);
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
     const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
     const int nbe = (int)((edges + kTailThreads - 1) / kTailThreads);
@@ -845,12 +861,13 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
     Fields6<real> E6;
     E6.p = (real*)tail.eb;
     {
-        const int nface = nfb * ncomp * (6 - a.face0);
+        const int nface = 2 * ncomp * (nf[0] + nf[1] + nf[2]);
         // deposit-box blocks: kBoxRecs push records each
         const int nbb = (int)((tail.nrec + kBoxRecs - 1) / kBoxRecs);
         const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_step_tail<real>,
                                           dim3((unsigned)(nface + ncomp * nbe + npw + npt + nbb)), dim3(kTailThreads), 0,
-                                          st, a, ec, g.sy, g.sz, edges, nfb, nbe, npw, npt, nbb, E6, g, tail, counter);
+                                          st, a, ec, g.sy, g.sz, edges, nf[0], nf[1], nf[2], nbe, npw, npt, nbb, E6, g,
+                                          tail, counter);
         if (le != cudaSuccess) return le;
     }
     count_launches(1);

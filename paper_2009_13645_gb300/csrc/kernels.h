@@ -57,10 +57,16 @@ MurFaceCoef mur_face_coef(const Geom& g, int order);
 // updates; tma_x_faces<real>() tells whether it does.  test_skip_plane >= 0 (failure tests only):
 // every block leaves the copy of its plane pfirst + test_skip_plane out and its waits give up
 // after 1024 polls, so the bounded-wait path runs and sets *err.
+// Sources: with src_box (device, the previous step's deposit box) and *src_far == 0 (device,
+// the far-move flag of this step's push), a block copies the source of a plane only where the
+// tile meets the nodes [lo - src_grow, hi + 1 + src_grow] of that box; elsewhere the source is
+// zero (this step's push deposited nothing there and the emission cleared the last one).
+// src_box null: every source is read.
 template <typename real>
 cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* const prev[4], const MurFaceCoef* mur,
-                               int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp, int* err,
-                               cudaStream_t st, int test_skip_plane = -1);
+                               int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp,
+                               const int* src_box, const int* src_far, int src_grow, int* err, cudaStream_t st,
+                               int test_skip_plane = -1);
 
 template <typename real>
 constexpr bool tma_x_faces()
@@ -271,9 +277,12 @@ __host__ __device__ inline int emit_chunks(int nz) { return (nz - 2 + kEmitKZ - 
 // Ints of one deposit box: [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the cells, then per z chunk
 // [lo_x, lo_y, hi_x, hi_y].
 inline int deposit_box_ints(int nz) { return 6 + 4 * emit_chunks(nz); }
+// The deposit box buffer: deposit_box_ints ints, then the push's far-move flag (PushConst::far).
+inline int deposit_box_words(int nz) { return deposit_box_ints(nz) + 1; }
 struct EmitBox {
     const int* box;      // device: the deposit box of the last push (deposit_box_ints)
-    int* box_reset;      // device: box the next push reduces into, reset to empty by the emission
+    int* box_reset;      // device: box the next push reduces into, reset to empty (and its far flag to 0)
+                         // by the emission
     int kp;              // plane always emitted in full (< 0: none)
     bool clear;          // clear the sources inside the box
     const EmitMaps* maps = nullptr;   // TMA loads (null: per-element asynchronous copies)
@@ -321,10 +330,15 @@ struct PushConst {
     // and gamma0 (1 + beta0) E0 / c (the Lorentz transform of a wave travelling along -z, evaluated in
     // FP64), E0, E0 / c, the waist, 1 / z_R, z_R and k_L, rounded to FP32
     float ltE, ltB, E0f, E0cf, w0f, izrf, zrf, kLf;
+    // set to 1 when a deposit of this step may fall outside the previous step's deposit box grown
+    // by the sub-step count: a move longer than one cell on an axis, or a deposit by a particle
+    // that started the step outside the active cells (the stencil then reads every source)
+    int* far;
 };
 
 // box_rec: per block of 128 particles, the six bounds [lo_x, lo_y, lo_z, hi_x, hi_y, hi_z] of the
-// cells its particles deposited into or end in (empty bounds: none); the step tail reduces them
+// cells its particles deposited into or end in (the end cells of the particles in the active
+// cells or the one-cell margin around them; empty bounds: none); the step tail reduces them
 // into the deposit box the next emission reads.
 template <typename real>
 cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, const ExtField& ef,

@@ -285,7 +285,7 @@ struct RunT final : mithra_run {
     double* ser_b = nullptr;   // rows(ser_cap) x 15
     double* rest_buf = nullptr;
     int64_t onaxis_id = 0;
-    int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (deposit_box_ints each)
+    int* box[2] = {nullptr, nullptr};   // deposit boxes of alternate steps (deposit_box_words each)
     int* box_rec = nullptr;              // the push's per-block bounds (six ints per block of 128)
     double2* ptab[2] = {nullptr, nullptr};   // static-undulator phase tables, FP64 path (one per planar field)
     float4* ptab32[2] = {nullptr, nullptr};  // FP32-mixed path: phase and edge distances rounded to FP32
@@ -425,7 +425,7 @@ struct RunT final : mithra_run {
         if (bunch_every > 0 && !(bunch_partial = (double*)mem.get((size_t)14 * npartial * 8)))
             return fail(MITHRA_ENOMEM, "device allocation failed (bunch sampling)");
         for (int b = 0; b < 2; ++b)
-            if (!(box[b] = (int*)mem.get((size_t)deposit_box_ints(g.nz) * sizeof(int))))
+            if (!(box[b] = (int*)mem.get((size_t)deposit_box_words(g.nz) * sizeof(int))))
                 return fail(MITHRA_ENOMEM, "device allocation failed (box)");
         if (!(box_rec = (int*)mem.get((size_t)6 * std::max<int64_t>(push_blocks(np), 1) * sizeof(int))))
             return fail(MITHRA_ENOMEM, "device allocation failed (box records)");
@@ -639,6 +639,8 @@ struct RunT final : mithra_run {
         pc.izrf = (float)(1.0 / ef.zr);
         pc.zrf = (float)ef.zr;
         pc.kLf = (float)ef.kL;
+        int* far = box[(n + 1) % 2] + deposit_box_ints(g.nz);   // reset by this step's emission
+        pc.far = far;
         pbeg(MITHRA_K_PUSH, &e0);
         CU(launch_push<real>(P, np, g, ef, E6, S4, pc, box_rec, stream));
         pend(MITHRA_K_PUSH, e0);
@@ -663,8 +665,10 @@ struct RunT final : mithra_run {
         if (tma) {
             real* outp[4] = {pot[lev(2)][0], pot[lev(2)][1], pot[lev(2)][2], pot[lev(2)][3]};
             real* prevp[4] = {pot[lev(0)][0], pot[lev(0)][1], pot[lev(0)][2], pot[lev(0)][3]};
-            CU(launch_stencil_tma<real>(tma, outp, prevp, &murc, lev(1), lev(0), g, cf, ncomp, err_word, stream,
-                                        test_tma_skip));
+            // the sources lie in the nodes of the last deposit box grown by one cell per sub-step,
+            // unless the push set the far flag
+            CU(launch_stencil_tma<real>(tma, outp, prevp, &murc, lev(1), lev(0), g, cf, ncomp, box[n % 2], far,
+                                        g.substeps, err_word, stream, test_tma_skip));
         } else {
             CU(launch_stencil<real>(L, g, cf, ncomp, stream));
         }
@@ -1413,7 +1417,7 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
     int64_t cap = 1024;
     while (cap < nsteps) cap *= 2;
     t += 4 * up(cap * 8);                                                     // series (old and new while growing)
-    t += 2 * up(deposit_box_ints(gr->nz) * 4) + up(6 * push_blocks(n) * 4) + 2 * up(gr->nz * 32);
+    t += 2 * up(deposit_box_words(gr->nz) * 4) + up(6 * push_blocks(n) * 4) + 2 * up(gr->nz * 32);
     t += up(gr->nz * 16);                                                     // boxes and records, phase tables
     t += up(n * 48);                                                          // lab particles during the boost
     if (gr->nf_points > 0) {                                                  // spectrum: ring, accumulators, series

@@ -269,6 +269,15 @@ __device__ __forceinline__ bool active_cell(int i, int j, int k, const Geom& g)
     return i >= 1 && i <= g.nx - 3 && j >= 1 && j <= g.ny - 3 && k >= 1 && k <= g.nz - 3;
 }
 
+// A cell of the active ones or of the one-cell margin around them.  The push's bounds include the
+// end cell of every particle in such a cell, so a particle entering the active cells in the next
+// step deposits inside the deposit box grown by a cell per sub-step.
+__device__ __forceinline__ bool recorded_cell(int i, int j, int k, const Geom& g)
+{
+    return (unsigned)i <= (unsigned)(g.nx - 2) && (unsigned)j <= (unsigned)(g.ny - 2) &&
+           (unsigned)k <= (unsigned)(g.nz - 2);
+}
+
 template <typename real>
 __device__ __forceinline__ void split_pos(double X, int32_t* c, real* f)
 {
@@ -716,6 +725,11 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
     G.sz = g.sz;
     const double t_half = pc.sd->t_half, Z0 = pc.sd->Z0;
     bool rho_done = false;
+    // The previous step's deposit box holds the start cell of every particle that can deposit in
+    // this step (recorded_cell), so the deposits of its moves of at most one cell per sub-step stay
+    // in that box grown by the sub-step count; any other deposit sets the far-move flag.  The start
+    // cell is read again from the particle arrays (still unchanged) where it is needed.
+    auto started_recorded = [&]() { return recorded_cell(P.ix[p], P.iy[p], P.iz[p], g); };
     for (int m = 0; m < g.substeps; ++m) {
         real b[3] = {f[0], f[1], f[2]};
         int nc[3] = {ci[0], ci[1], ci[2]};
@@ -729,6 +743,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 hi[l] = max(hi[l], max(ci[l], nc[l]));
             }
             real mx = fmax(fabs(b[0] - f[0]), fmax(fabs(b[1] - f[1]), fabs(b[2] - f[2])));
+            if (!(mx <= (real)1) || (m > 0 && !started_recorded())) *pc.far = 1;
             if (mx <= (real)1) {
                 simple = true;
             } else {
@@ -846,13 +861,16 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
             f[l] = nf[l];
         }
     }
-    if (alive && active_cell(ci[0], ci[1], ci[2], g)) {
+    if (alive && recorded_cell(ci[0], ci[1], ci[2], g)) {
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
             lo[l] = min(lo[l], ci[l]);
             hi[l] = max(hi[l], ci[l]);
         }
-        if (g.space_charge && !rho_done) deposit_rho(ci, f, q, G);
+        if (g.space_charge && !rho_done && active_cell(ci[0], ci[1], ci[2], g)) {
+            if (!started_recorded()) *pc.far = 1;
+            deposit_rho(ci, f, q, G);
+        }
     }
     if (alive) {
         P.ix[p] = ci[0];

@@ -6,7 +6,10 @@
 //   psi^n   (TX + 2 HX) x (TY + 2)  (the tile plus the x/y halo; the x origin is moved down to a
 //                                     16-byte boundary, so HX = 16 bytes of elements),
 //   psi^{n-1}, source  TX x TY,
-// into a ring of NST shared-memory stages, NST - 1 planes ahead of the plane being computed.
+// into a ring of NST shared-memory stages, NST - 1 planes ahead of the plane being computed.  The
+// source is copied only for the block's own planes and only where the tile meets the nodes the
+// step's push can have deposited into (the previous deposit box grown by a cell per sub-step);
+// elsewhere it is zero, so early in a run, with a compact bunch, most tiles skip its bytes.
 // Each thread owns two x-adjacent columns and keeps planes k-1, k, k+1 of them and of their
 // neighbours (x-1, x+2, and the rows above and below) in registers, reading only the new plane
 // k+1 from shared memory, with 64-bit (FP32) / 128-bit (FP64) loads for the column pairs; both
@@ -83,6 +86,11 @@ struct TmaArgs {
     int ncomp;
     real a1, ax, ay, a6, w, w0, s[4];
     real axw, axw0, ayw, ayw0;   // ax w, ax w0, ay w, ay w0 (products taken in FP64)
+    // the previous step's deposit box, this step's far-move flag and the box's growth in nodes
+    // (sbox null: every source is read)
+    const int* sbox;
+    const int* sfar;
+    int sgrow;
     int* err;
     // failure test: the plane pfirst + skip_plane of every block is never copied (-1: none), and
     // every wait gives up after `spin` polls
@@ -126,6 +134,22 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     const CUtensorMap* mb = &maps.body[comp];
     const CUtensorMap* ms = &maps.src[comp];
     const int pfirst = k0 - 1, plast = k1 + 1;
+    // planes [zs0, zs1] whose source this block copies: the source enters the update of the
+    // block's own planes only, and only where this step's push can have deposited (empty:
+    // zs0 > zs1).  The box ints were written by earlier kernels of the stream and the flag by
+    // the push just before: read through L2.
+    int zs0 = k0, zs1 = k1;
+    if (a.sbox && __ldcg(a.sfar) == 0) {
+        const int d = a.sgrow;
+        const int lx = __ldcg(a.sbox) - d, ly = __ldcg(a.sbox + 1) - d, lz = __ldcg(a.sbox + 2) - d;
+        const int hx = __ldcg(a.sbox + 3) + 1 + d, hy = __ldcg(a.sbox + 4) + 1 + d, hz = __ldcg(a.sbox + 5) + 1 + d;
+        if (lx <= xt + TX - 1 && hx >= xt && ly <= yt + TY - 1 && hy >= yt) {
+            zs0 = max(zs0, lz);
+            zs1 = min(zs1, hz);
+        } else {
+            zs1 = zs0 - 1;
+        }
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(bars + s, 1);
@@ -138,10 +162,11 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
         unsigned char* st = smem + s * T::STAGE;
         // the stage held plane p - NST, which the block read before its last barrier
         if (p >= pfirst + NST) fence_proxy_async_smem();
-        mbar_expect_tx(bars + s, (uint32_t)T::TX_BYTES);
+        const bool sp = p >= zs0 && p <= zs1;
+        mbar_expect_tx(bars + s, (uint32_t)(sp ? T::TX_BYTES : T::TX_BYTES - T::BODY_BYTES));
         tma_load_3d(st, mh, xt - T::HX, yt - 1, p, bars + s);
         tma_load_3d(st + T::OFF_PREV, mb, xt, yt, p, bars + s);
-        tma_load_3d(st + T::OFF_SRC, ms, xt, yt, p, bars + s);
+        if (sp) tma_load_3d(st + T::OFF_SRC, ms, xt, yt, p, bars + s);
     };
     int last_issued = pfirst - 1;
     if (threadIdx.x == 0)
@@ -199,7 +224,13 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
         load(k + 1, N);
         const unsigned char* stk = smem + ((k - pfirst) % NST) * T::STAGE;
         const V2 pm = *(const V2*)((const real*)(stk + T::OFF_PREV) + ty * TX + cx);
-        const V2 sr = *(const V2*)((const real*)(stk + T::OFF_SRC) + ty * TX + cx);
+        V2 sr;
+        if (k >= zs0 && k <= zs1) {
+            sr = *(const V2*)((const real*)(stk + T::OFF_SRC) + ty * TX + cx);
+        } else {
+            sr.x = (real)0;
+            sr.y = (real)0;
+        }
         if ((mineA || mineB) && ok) {
             // ax (w (N^{k-1} + N^{k+1}) + w0 N^k) over the two x neighbours, likewise along y
             const real vA = a.a1 * C.ca - pm.x + a.axw * (L.XA + N.XA) + a.axw0 * C.XA + a.ayw * (L.YA + N.YA) +
@@ -339,8 +370,9 @@ bool emit_maps(const TmaMaps* maps, int lev_n, int lev_n1, EmitMaps* out)
 
 template <typename real>
 cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* const prev[4], const MurFaceCoef* mur,
-                               int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp, int* err,
-                               cudaStream_t st, int test_skip_plane)
+                               int lev_n, int lev_m, const Geom& g, const StencilCoef& cf, int ncomp,
+                               const int* src_box, const int* src_far, int src_grow, int* err, cudaStream_t st,
+                               int test_skip_plane)
 {
     using T = Tile<real>;
     static bool attr_set = false;
@@ -371,6 +403,9 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* co
     a.axw0 = (real)(cf.ax * cf.w0);
     a.ayw = (real)(cf.ay * cf.w);
     a.ayw0 = (real)(cf.ay * cf.w0);
+    a.sbox = src_box;
+    a.sfar = src_far;
+    a.sgrow = src_grow;
     a.err = err;
     a.skip_plane = test_skip_plane;
     a.spin = test_skip_plane >= 0 ? 1024u : kSpinLimit;
@@ -401,9 +436,10 @@ template bool tma_supported<double>(const Geom&);
 template TmaMaps* make_tma_maps<float>(float* const[3][4], float* const[4], const Geom&);
 template TmaMaps* make_tma_maps<double>(double* const[3][4], double* const[4], const Geom&);
 template cudaError_t launch_stencil_tma<float>(const TmaMaps*, float* const[4], float* const[4], const MurFaceCoef*,
-                                               int, int, const Geom&, const StencilCoef&, int, int*, cudaStream_t, int);
+                                               int, int, const Geom&, const StencilCoef&, int, const int*, const int*,
+                                               int, int*, cudaStream_t, int);
 template cudaError_t launch_stencil_tma<double>(const TmaMaps*, double* const[4], double* const[4],
                                                 const MurFaceCoef*, int, int, const Geom&, const StencilCoef&, int,
-                                                int*, cudaStream_t, int);
+                                                const int*, const int*, int, int*, cudaStream_t, int);
 
 }  // namespace mithra
