@@ -411,6 +411,24 @@ def main():
                 kp_box = ex * ey
         return total + plane - kp_box
 
+    def source_nodes(run, wl) -> int:
+        """Nodes the step's deposit can reach: the box of the nodes [lo, hi + 1] of the cells of
+        the active particles (the stencil needs a source there only; elsewhere it is zero)."""
+        inf = run.info()
+        P = run.particles()
+        c = [np.floor((P[:, d] - inf[o]) / inf[s_]).astype(np.int64)
+             for d, (o, s_) in enumerate((("x0", "dx"), ("y0", "dy"), ("z0", "dz")))]
+        n = (wl.nx, wl.ny, wl.nz)
+        act = np.ones(len(P), bool)
+        for d in range(3):
+            act &= (c[d] >= 1) & (c[d] <= n[d] - 3)
+        if not act.any():
+            return 0
+        tot = 1
+        for d in range(3):
+            tot *= int(c[d][act].max()) + 1 - int(c[d][act].min()) + 1
+        return tot
+
     def timed_run(precision: int, steps: int, sample_clocks: bool, wl=None, labl=None):
         """K timed steps as a user runs them (captured graphs replayed), then K more steps with
         CUDA events around every kernel (launched one by one) for the per-kernel times."""
@@ -435,6 +453,7 @@ def main():
         clocks = clk.stop() if clk else None
         ms = ev0.elapsed_time(ev1)
         nodes0 = emitted_nodes(run, wl)
+        src0 = source_nodes(run, wl)
         run.set_profiling(True)
         e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e2.record(stream)
@@ -445,6 +464,7 @@ def main():
         stats = run.kernel_stats()
         info = run.info()
         info["emitted_nodes"] = 0.5 * (nodes0 + emitted_nodes(run, wl))
+        info["source_nodes"] = 0.5 * (src0 + source_nodes(run, wl))
         run.close()
         return ms, stats, launches, clocks, info, ms_prof
 
@@ -520,8 +540,10 @@ def main():
                    "steps": Kb, "grid": [wb.nx, wb.ny, wb.nz], "particles": wb.n_particles,
                    "precision": "fp32-mixed", "kernel_ms_per_step": {k: v[0] / Kb for k, v in statsb.items() if v[1]}}
             if plb.get("stencil"):
-                a = 64 * cb / (plb["stencil"] * 1e-3) / 1e9
-                ent["stencil_roofline"] = {"achieved": a, "frac": a / _peaks()[0], "ms_per_launch": plb["stencil"]}
+                sb = 48 * cb + 16 * infob["source_nodes"]
+                a = sb / (plb["stencil"] * 1e-3) / 1e9
+                ent["stencil_roofline"] = {"achieved": a, "frac": a / _peaks()[0], "ms_per_launch": plb["stencil"],
+                                           "alg_bytes_per_launch": sb}
             if plb.get("push_deposit"):
                 a = 80 * wb.n_particles / (plb["push_deposit"] * 1e-3) / 1e9
                 ent["push_roofline"] = {"achieved": a, "frac": a / _peaks()[0], "ms_per_launch": plb["push_deposit"]}
@@ -580,7 +602,9 @@ def main():
     ncell = cells
     # algorithmic bytes per launch (FP32-mixed)
     alg = {
-        "stencil": 4 * 4 * 4 * ncell,                       # 4 potentials x (psi^n, psi^{n-1}, source, psi^{n+1})
+        # 4 potentials x (psi^n, psi^{n-1}, psi^{n+1}) at every cell, and their sources where the
+        # step's deposit can reach (zero elsewhere)
+        "stencil": 4 * 3 * 4 * ncell + 4 * 4 * info["source_nodes"],
         "emit_eb": 68 * info["emitted_nodes"],              # see emit_roof below
         # particle state in and out counted as one int32 cell index, three FP32 offsets and three
         # 8-byte momenta: 40 B each way (the layout keeps three int32 cells: 48 B moved each way)
@@ -605,6 +629,7 @@ def main():
     if per_launch.get("stencil"):
         a = alg["stencil"] / (per_launch["stencil"] * 1e-3) / 1e9
         stencil_roof = {"achieved": a, "frac": a / hbm, "ms_per_launch": per_launch["stencil"],
+                        "alg_bytes_per_launch": alg["stencil"], "source_nodes": info["source_nodes"],
                         "traffic": _ncu_traffic("stencil")}
     emit_roof = None
     if per_launch.get("emit_eb"):

@@ -383,10 +383,19 @@ __device__ __forceinline__ void dep_begin()
 // st: on the FP32-mixed path when launched directly.  Steps captured into a graph already start
 // back to back, and there waiting blocks of the small kernels (phase table, Mur, power) made a
 // replayed period slower; the FP64 path was slower with it in both modes.
+// kernel: its bit in MITHRA_DEP_MASK, the kernels that may start early.  The emission, the push
+// and the stencil each gained 1-3 us per step of the FEL run 128x128x512 (steps 5-25: 0.267 ms
+// with none, 0.264-0.266 with one of them); the step tail lost 10 us (its thousands of small
+// blocks, resident early, wait while the stencil's last wave runs), and the optional kernels
+// (spectrum, bunch sampling, seed) are small enough to lose like it.
+enum DepKernel : unsigned { kDepEmit = 1, kDepPush = 2, kDepStencil = 4, kDepTail = 8, kDepOther = 16 };
+#ifndef MITHRA_DEP_MASK
+#define MITHRA_DEP_MASK 7u
+#endif
 template <typename real>
-inline bool dep_launch_on(cudaStream_t st)
+inline bool dep_launch_on(cudaStream_t st, unsigned kernel)
 {
-    if (!MITHRA_DEP_LAUNCH || sizeof(real) != 4) return false;
+    if (!MITHRA_DEP_LAUNCH || sizeof(real) != 4 || !(kernel & (MITHRA_DEP_MASK))) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
 }

@@ -202,17 +202,17 @@ cudaError_t launch_spectrum_step(const Fields6<real>& eb, const Geom& g, const S
     const unsigned nb = (unsigned)((plane + kRedThreads - 1) / kRedThreads);
     if ((int)nb > npartial || s.nf < 1) return cudaErrorInvalidValue;
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_spec_step<real>, dim3(nb, s.nf),
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_spec_step<real>, dim3(nb, s.nf),
                                           dim3(kRedThreads), 0, st, eb, g, s, partial);
         if (le != cudaSuccess) return le;
     }
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_spec_ring<real>, dim3(nb), dim3(kRedThreads), 0,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_spec_ring<real>, dim3(nb), dim3(kRedThreads), 0,
                                           st, eb, g, s);
         if (le != cudaSuccess) return le;
     }
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_spec_final, dim3(s.nf), dim3(kRedThreads), 0, st,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_spec_final, dim3(s.nf), dim3(kRedThreads), 0, st,
                                           partial, (int)nb, s, series);
         if (le != cudaSuccess) return le;
     }
@@ -313,12 +313,12 @@ cudaError_t launch_bunch_sample(const Particles<real>& P, int64_t np, const Geom
     int nb = (int)std::min<int64_t>((np + kRedThreads - 1) / kRedThreads, (int64_t)npartial);
     if (nb < 1) nb = 1;
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_bunch_moments<real>, dim3(nb), dim3(kRedThreads),
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_bunch_moments<real>, dim3(nb), dim3(kRedThreads),
                                           0, st, P, np, g, b, partial);
         if (le != cudaSuccess) return le;
     }
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_bunch_row, dim3(1), dim3(kRedThreads), 0, st,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_bunch_row, dim3(1), dim3(kRedThreads), 0, st,
                                           partial, nb, np, b, series);
         if (le != cudaSuccess) return le;
     }

@@ -107,25 +107,72 @@ __device__ inline int64_t lin(int i, int j, int k, int64_t sy, int64_t sz) { ret
 
 // Mur value of level n+1 at the face node p of face (ax, side sd) of component comp, from the
 // interior value beside it (already updated) and levels n, n-1.
+template <int AX, typename real>
+__device__ __forceinline__ real mur_face_value_ax(const MurArgs<real>& a, int comp, int sd, const int p[3], int64_t sy,
+                                                  int64_t sz)
+{
+    constexpr int TA = (AX + 1) % 3, TB = (AX + 2) % 3;
+    const int64_t sn = AX == 0 ? 1 : (AX == 1 ? sy : sz);   // strides along the normal and the two
+    const int64_t sa = TA == 0 ? 1 : (TA == 1 ? sy : sz);   // tangential axes
+    const int64_t sb = TB == 0 ? 1 : (TB == 1 ? sy : sz);
+    const int64_t ib = lin(p[0], p[1], p[2], sy, sz);
+    const int64_t iq = ib + (sd ? -sn : sn);   // inward neighbour
+    const real* __restrict__ n1 = a.n1[comp];
+    const real* __restrict__ n0 = a.n0[comp];
+    const real* __restrict__ nm = a.nm[comp];
+    real ta = (real)0, tb = (real)0;
+    if (a.order != 1) {
+        // tangential neighbours at level n on the face and on the inner plane
+        ta = n0[ib + sa] + n0[ib - sa] + n0[iq + sa] + n0[iq - sa];
+        tb = n0[ib + sb] + n0[ib - sb] + n0[iq + sb] + n0[iq - sb];
+    }
+    // first order: the tangential gammas are zero
+    return a.f0[AX] * (nm[ib] + n1[iq]) + a.f1[AX] * (n0[ib] + n0[iq]) - nm[iq] + a.ft[AX][0] * ta + a.ft[AX][1] * tb;
+}
+
+// The same with the normal axis ax known at run time (edges, corners, the faces beside the TF/SF
+// planes): one copy of the code, the strides taken from a small table.
 template <typename real>
 __device__ __forceinline__ real mur_face_value(const MurArgs<real>& a, int comp, int ax, int sd, const int p[3],
                                                int64_t sy, int64_t sz)
 {
     const int64_t st[3] = {1, sy, sz};
     const int64_t ib = lin(p[0], p[1], p[2], sy, sz);
-    const int64_t iq = ib + (sd ? -st[ax] : st[ax]);   // inward neighbour
+    const int64_t iq = ib + (sd ? -st[ax] : st[ax]);
     const real* __restrict__ n1 = a.n1[comp];
     const real* __restrict__ n0 = a.n0[comp];
     const real* __restrict__ nm = a.nm[comp];
-    real sa = (real)0, sb = (real)0;
+    real ta = (real)0, tb = (real)0;
     if (a.order != 1) {
-        // tangential neighbours at level n on the face and on the inner plane
-        const int ta = (ax + 1) % 3, tb = (ax + 2) % 3;
-        sa = n0[ib + st[ta]] + n0[ib - st[ta]] + n0[iq + st[ta]] + n0[iq - st[ta]];
-        sb = n0[ib + st[tb]] + n0[ib - st[tb]] + n0[iq + st[tb]] + n0[iq - st[tb]];
+        const int64_t sa = st[(ax + 1) % 3], sb = st[(ax + 2) % 3];
+        ta = n0[ib + sa] + n0[ib - sa] + n0[iq + sa] + n0[iq - sa];
+        tb = n0[ib + sb] + n0[ib - sb] + n0[iq + sb] + n0[iq - sb];
     }
-    // first order: the tangential gammas are zero
-    return a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + a.ft[ax][0] * sa + a.ft[ax][1] * sb;
+    return a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + a.ft[ax][0] * ta + a.ft[ax][1] * tb;
+}
+
+// Two rows of face (AX, side sd) of component comp: the rows v = v0 + 2 rp and v0 + 2 rp + 1 of the
+// tangential axis v, each 128 threads walking its interior nodes along u (x for the y and z faces:
+// coalesced).
+constexpr int kFaceRowThreads = 128;
+template <int AX, typename real>
+__device__ __forceinline__ void mur_face_rows(const MurArgs<real>& a, int comp, int sd, int rp, int64_t sy, int64_t sz)
+{
+    constexpr int U = AX == 0 ? 1 : 0, V = AX == 2 ? 1 : 2;   // tangential axes, u before v
+    const int eu = U == 0 ? a.ex[comp] : a.ey[comp];
+    const int ev = V == 1 ? a.ey[comp] : a.ez[comp];
+    const int en = AX == 0 ? a.ex[comp] : (AX == 1 ? a.ey[comp] : a.ez[comp]);
+    const int v0 = AX == 0 ? a.kmin : 1, v1 = AX == 0 ? min(a.kmax, ev - 2) : ev - 2;
+    const int v = v0 + 2 * rp + (int)(threadIdx.x / kFaceRowThreads);
+    if (v > v1) return;
+#pragma unroll 1
+    for (int u = 1 + (int)(threadIdx.x % kFaceRowThreads); u <= eu - 2; u += kFaceRowThreads) {
+        int p[3];
+        p[AX] = sd ? en - 1 : 0;
+        p[U] = u;
+        p[V] = v;
+        a.n1[comp][lin(p[0], p[1], p[2], sy, sz)] = mur_face_value_ax<AX>(a, comp, sd, p, sy, sz);
+    }
 }
 
 // Face node t of face f (axis = f / 2, side = f % 2) of component comp, if it exists.
@@ -280,7 +327,13 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
             }
         }
         const int side = fi / (a.ncomp * nf), r = fi - side * a.ncomp * nf;
-        mur_face_node(a, r / nf, 2 * ax + side, (r % nf) * kTailThreads + (int)threadIdx.x, sy, sz);
+        const int comp = r / nf, rp = r - comp * nf;
+        if (ax == 0)
+            mur_face_rows<0>(a, comp, side, rp, sy, sz);
+        else if (ax == 1)
+            mur_face_rows<1>(a, comp, side, rp, sy, sz);
+        else
+            mur_face_rows<2>(a, comp, side, rp, sy, sz);
         return;
     }
     const int b = (int)blockIdx.x;
@@ -744,7 +797,7 @@ cudaError_t launch_stencil(const FieldLevels<real>& L, const Geom& g, const Sten
     const int nchunk = (g.nz - 2 + a.kchunk - 1) / a.kchunk;
     const dim3 grd((g.nx - 2 + 31) / 32, (g.ny - 2 + 7) / 8, nchunk * ncomp);
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_stencil<real>, dim3(grd), dim3(blk), 0, st, a,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepStencil), k_stencil<real>, dim3(grd), dim3(blk), 0, st, a,
                                           g.sy, g.sz);
         if (le != cudaSuccess) return le;
     }
@@ -839,16 +892,18 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
         a.ft[ax][0] = (real)m.ft[ax][0];
         a.ft[ax][1] = (real)m.ft[ax][1];
     }
-    // face blocks per side and component along each normal axis: the largest face of the axis
+    // face blocks per side and component along each normal axis: two rows of the axis's longest
+    // tangential v range each (mur_face_rows)
+    static_assert(2 * kFaceRowThreads == kTailThreads, "two face rows per tail block");
     int nf[3] = {0, 0, 0};
     for (int ax = a.face0 / 2; ax < 3; ++ax) {
-        int64_t maxface = 0;
+        int rows = 0;
         for (int c = 0; c < ncomp; ++c) {
-            const int64_t e[3] = {a.ex[c], a.ey[c], a.ez[c]};
+            const int e[3] = {a.ex[c], a.ey[c], a.ez[c]};
             const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
-            maxface = std::max<int64_t>(maxface, std::max<int64_t>(e[u] - 2, 0) * std::max<int64_t>(e[v] - 2, 0));
+            if (e[u] - 2 > 0) rows = std::max(rows, e[v] - 2);
         }
-        nf[ax] = (int)((maxface + kTailThreads - 1) / kTailThreads);
+        nf[ax] = (rows + 1) / 2;
     }
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
     const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
@@ -864,7 +919,7 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
         const int nface = 2 * ncomp * (nf[0] + nf[1] + nf[2]);
         // deposit-box blocks: kBoxRecs push records each
         const int nbb = (int)((tail.nrec + kBoxRecs - 1) / kBoxRecs);
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_step_tail<real>,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepTail), k_step_tail<real>,
                                           dim3((unsigned)(nface + ncomp * nbe + npw + npt + nbb)), dim3(kTailThreads), 0,
                                           st, a, ec, g.sy, g.sz, edges, nf[0], nf[1], nf[2], nbe, npw, npt, nbb, E6, g,
                                           tail, counter);
@@ -900,7 +955,7 @@ cudaError_t launch_mur_tfsf_xfaces(const FieldLevels<real>& L, const Geom& g, in
     }
     const int64_t pts = 2 * (int64_t)g.ny;
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_mur_faces<real>,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_mur_faces<real>,
                                           dim3((unsigned)((pts + 127) / 128), 2, 2), dim3(128), 0, st, a, g.sy, g.sz);
         if (le != cudaSuccess) return le;
     }
@@ -945,7 +1000,7 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
             cudaFuncSetAttribute(k_emit<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (attr != cudaSuccess) return attr;
         {
-            const cudaError_t le = launch_dep(dep_launch_on<real>(st), (k_emit<real, true>), dim3(grd), dim3(ENT),
+            const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepEmit), (k_emit<real, true>), dim3(grd), dim3(ENT),
                                               smem, st, a, g, *bx.maps);
             if (le != cudaSuccess) return le;
         }
@@ -957,7 +1012,7 @@ cudaError_t launch_emit(const FieldLevels<real>& L, const Fields6<real>& eb, con
         EmitMaps none;
         memset(&none, 0, sizeof none);
         {
-            const cudaError_t le = launch_dep(dep_launch_on<real>(st), (k_emit<real, false>), dim3(grd), dim3(ENT),
+            const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepEmit), (k_emit<real, false>), dim3(grd), dim3(ENT),
                                               smem, st, a, g, none);
             if (le != cudaSuccess) return le;
         }
@@ -1023,7 +1078,7 @@ cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf
 {
     const int64_t plane = (int64_t)g.nx * g.ny;
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_seed_eval,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_seed_eval,
                                           dim3((unsigned)((2 * plane + 127) / 128)), dim3(128), 0, st, s, g, sd, T0,
                                           fbuf);
         if (le != cudaSuccess) return le;
@@ -1039,7 +1094,7 @@ cudaError_t launch_tfsf(real* const out[2], const Geom& g, const StencilCoef& cf
     a.a4 = cf.ay;
     a.a6 = cf.a6;
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_tfsf<real>,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepOther), k_tfsf<real>,
                                           dim3((unsigned)((plane + 127) / 128), 2), dim3(128), 0, st, a, g, fbuf);
         if (le != cudaSuccess) return le;
     }

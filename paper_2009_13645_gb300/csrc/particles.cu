@@ -480,11 +480,11 @@ __device__ __forceinline__ void tile_move(const float f[3], const float b[3], co
 }
 
 // Block-wide bounding box of [lo, hi] (inclusive node ranges; empty when lo > hi), returned to
-// every thread.  Two barriers.
+// every thread.  One barrier: every thread reduces the four warps' bounds itself.  A second call
+// must not start before every thread has read the first's bounds (a barrier in between).
 __device__ __forceinline__ void block_box(const int lo[3], const int hi[3], int out[6])
 {
-    __shared__ int sh[6][4];   // 128 threads = 4 warps
-    __shared__ int res[6];
+    __shared__ __align__(16) int sh[6][4];   // 128 threads = 4 warps
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -496,15 +496,11 @@ __device__ __forceinline__ void block_box(const int lo[3], const int hi[3], int 
         }
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
-        const int q = threadIdx.x;
-        int v = sh[q][0];
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = q < 3 ? min(v, sh[q][k]) : max(v, sh[q][k]);
-        res[q] = v;
-    }
-    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 6; ++q) out[q] = res[q];
+    for (int q = 0; q < 6; ++q) {
+        const int4 v = *reinterpret_cast<const int4*>(sh[q]);
+        out[q] = q < 3 ? min(min(v.x, v.y), min(v.z, v.w)) : max(max(v.x, v.y), max(v.z, v.w));
+    }
 }
 
 // Block-wide min/max of the cells this block deposited into (or will gather from next step): its
@@ -684,6 +680,13 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
            int* box_rec)
 {
     dep_begin();
+    // FP32-mixed deposit tile (see below), cleared once here while the particle loads are in flight;
+    // the flush of every sub-step but the last clears what it read
+    __shared__ __align__(16) int tile[sizeof(real) == 4 ? kTileInts : 4];
+    if constexpr (std::is_same<real, float>::value) {
+        int4* t4 = reinterpret_cast<int4*>(tile);
+        for (int i = threadIdx.x; i < kTileInts / 4; i += blockDim.x) t4[i] = make_int4(0, 0, 0, 0);
+    }
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff};
     int hi[3] = {(int)0x80000000, (int)0x80000000, (int)0x80000000};
@@ -765,14 +768,13 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
         const bool last = m == g.substeps - 1;
         const bool rho_t = simple && g.space_charge && last;
         if constexpr (std::is_same<real, float>::value) {
-            __shared__ __align__(16) int tile[kTileInts];
             int tlo[3], thi[3], box[6];
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
                 tlo[l] = simple ? min(ci[l], nc[l]) : 0x7fffffff;
                 thi[l] = simple ? max(ci[l], nc[l]) + 1 : (int)0x80000000;
             }
-            block_box(tlo, thi, box);
+            block_box(tlo, thi, box);   // its barrier also orders the tile's clearing
             // the tile's rows start on a multiple of four nodes and hold whole quads of nodes, so
             // that a quad of a row is added to the grid with one vector atomic
             const int bx0 = box[0] & ~3;
@@ -787,8 +789,6 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                 const int cs = nent + 4;
                 const int lc = 4 * cs <= kTileInts ? 2 : (2 * cs <= kTileInts ? 1 : 0);
                 int4* tile4 = reinterpret_cast<int4*>(tile);
-                for (int i = threadIdx.x; i < (cs << lc) >> 2; i += blockDim.x) tile4[i] = make_int4(0, 0, 0, 0);
-                __syncthreads();
                 // A particle adds at most |qJ_l| to any node of J_l over its two pieces (the
                 // path-averaged weights lie in [0, 1] and the pieces' extents along l sum to at
                 // most one cell) and at most |q| to a node of rho, so a block of 128 sums to at most
@@ -826,6 +826,8 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                         v.z += w.z;
                         v.w += w.w;
                     }
+                    if (!last)
+                        for (int cp = 0; cp < (1 << lc); ++cp) tile4[cp * (cs >> 2) + i] = make_int4(0, 0, 0, 0);
                     if ((v.x | v.y | v.z | v.w) != 0) {
                         const int c = (int)(((float)i + 0.5f) * ivq), r = i - c * vq;
                         const int k = (int)(((float)r + 0.5f) * iqxy), r2 = r - k * qx * ty;
@@ -844,10 +846,13 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? MITHRA_PUSH_MIN_BLOCK
                         }
                     }
                 }
-                __syncthreads();   // the tile is reused by the next sub-step
-            } else if (simple) {
-                zigzag(f, b, ci, G, qJ);
-                if (rho_t) deposit_rho(nc, nf, q, G);
+                if (!last) __syncthreads();   // the tile and the bounds are reused by the next sub-step
+            } else {
+                if (simple) {
+                    zigzag(f, b, ci, G, qJ);
+                    if (rho_t) deposit_rho(nc, nf, q, G);
+                }
+                if (!last) __syncthreads();   // the bounds are reused by the next sub-step
             }
         } else if (simple) {
             // FP64 path: floating-point adds straight into the grids
@@ -967,7 +972,7 @@ cudaError_t launch_push(const Particles<real>& P, int64_t np, const Geom& g, con
 {
     if (np <= 0) return cudaSuccess;
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_push<real>, dim3(nblocks(np, 128)), dim3(128), 0,
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepPush), k_push<real>, dim3(nblocks(np, 128)), dim3(128), 0,
                                           st, P, np, g, ef, eb, src, pc, box_rec);
         if (le != cudaSuccess) return le;
     }

@@ -98,24 +98,48 @@ struct TmaArgs {
     uint32_t spin;
 };
 
+// Cells per thread: the x-adjacent columns one 16-byte shared-memory load fetches (four in FP32,
+// two in FP64), loaded and stored as one vector.
 template <typename real>
-struct Vec2T;
-template <>
-struct Vec2T<float> {
-    using type = float2;
-};
-template <>
-struct Vec2T<double> {
-    using type = double2;
-};
+constexpr int cells_per_thread()
+{
+    return 16 / (int)sizeof(real);
+}
+
+template <typename real, int N>
+__device__ __forceinline__ void ld16(const real* p, real (&v)[N])
+{
+    static_assert(N * sizeof(real) == 16, "16-byte vector");
+    if constexpr (sizeof(real) == 4) {
+        const float4 t = *(const float4*)p;
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else {
+        const double2 t = *(const double2*)p;
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+}
+
+template <typename real, int N>
+__device__ __forceinline__ void st16(real* p, const real (&v)[N])
+{
+    if constexpr (sizeof(real) == 4) {
+        *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *(double2*)p = make_double2(v[0], v[1]);
+    }
+}
 
 template <typename real>
-__global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_constant__ StencilMaps maps, TmaArgs<real> a,
-                                                              int64_t sy, int64_t sz)
+__global__ void __launch_bounds__(TX / cells_per_thread<real>() * TY)
+    k_stencil_tma(const __grid_constant__ StencilMaps maps, TmaArgs<real> a, int64_t sy, int64_t sz)
 {
+    constexpr int CT = cells_per_thread<real>();
     dep_begin();
     using T = Tile<real>;
-    using V2 = typename Vec2T<real>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = (uint64_t*)(smem + NST * T::STAGE);
     const int comp = blockIdx.z % a.ncomp;
@@ -125,11 +149,17 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
     if (k0 > ez - 2) return;
     const int k1 = min(ez - 2, k0 + KZ - 1);
     const int xt = blockIdx.x * TX, yt = blockIdx.y * TY;
-    const int tp = threadIdx.x % (TX / 2), ty = threadIdx.x / (TX / 2);
-    const int cx = 2 * tp;                 // tile column of the pair's first cell
+    const int tp = threadIdx.x % (TX / CT), ty = threadIdx.x / (TX / CT);
+    const int cx = CT * tp;                // tile column of the thread's first cell
     const int x = xt + cx, y = yt + ty;
     const bool yin = y >= 1 && y <= ey - 2;
-    const bool mineA = yin && x >= 1 && x <= ex - 2, mineB = yin && x + 1 >= 1 && x + 1 <= ex - 2;
+    bool mine[CT], all = true, any = false;   // the thread's interior cells
+#pragma unroll
+    for (int i = 0; i < CT; ++i) {
+        mine[i] = yin && x + i >= 1 && x + i <= ex - 2;
+        all = all && mine[i];
+        any = any || mine[i];
+    }
     const CUtensorMap* mh = &maps.halo[comp];
     const CUtensorMap* mb = &maps.body[comp];
     const CUtensorMap* ms = &maps.src[comp];
@@ -180,32 +210,31 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
         const uint32_t parity = (uint32_t)(((p - pfirst) / NST) & 1);
         if (!mbar_wait(bars + s, parity, a.spin)) ok = false;
     };
-    // row dy of plane p's halo tile, at the pair's first cell
+    // row dy of plane p's halo tile, at the thread's first cell
     auto hrow = [&](int p, int dy) -> const real* {
         return (const real*)(smem + ((p - pfirst) % NST) * T::STAGE) + (ty + 1 + dy) * T::W + cx + T::HX;
     };
-    // registers of one plane: the pair (ca, cb), and the sums of each cell's two x neighbours (XA =
-    // x-1 + x+1 of the first cell, XB of the second) and of its two y neighbours (YA, YB), formed
-    // once per plane and used in three updates; x+2 alone (xq) for the Mur x face.  Planes k-1,
-    // k and k+1 are live; the loop below is unrolled three times so that moving on a plane renames
-    // them instead of copying.
+    // registers of one plane: the thread's cells c, and the sums of each cell's two x neighbours
+    // (X) and of its two y neighbours (Y), formed once per plane and used in three updates; the
+    // cell after the last (xq) for the Mur x face.  Planes k-1, k and k+1 are live; the loop below
+    // is unrolled three times so that moving on a plane renames them instead of copying.
     struct Plane {
-        real ca, cb, xq, XA, XB, YA, YB;
+        real c[CT], X[CT], Y[CT], xq;
     };
     Plane P0, P1, P2;
     auto load = [&](int p, Plane& P) {
         const real* r = hrow(p, 0);
-        const V2 c = *(const V2*)r;
-        P.ca = c.x;
-        P.cb = c.y;
+        ld16(r, P.c);
         const real xm = r[-1];
-        P.xq = r[2];
-        const V2 m = *(const V2*)hrow(p, -1);
-        const V2 q = *(const V2*)hrow(p, 1);
-        P.XA = P.cb + xm;
-        P.XB = P.xq + P.ca;
-        P.YA = q.x + m.x;
-        P.YB = q.y + m.y;
+        P.xq = r[CT];
+        real m[CT], q[CT];
+        ld16(hrow(p, -1), m);
+        ld16(hrow(p, 1), q);
+#pragma unroll
+        for (int i = 0; i < CT; ++i) {
+            P.X[i] = (i == CT - 1 ? P.xq : P.c[i + 1]) + (i == 0 ? xm : P.c[i - 1]);
+            P.Y[i] = q[i] + m[i];
+        }
     };
     wait_plane(pfirst);
     wait_plane(pfirst + 1);
@@ -223,47 +252,49 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_stencil_tma(const __grid_consta
         wait_plane(k + 1);
         load(k + 1, N);
         const unsigned char* stk = smem + ((k - pfirst) % NST) * T::STAGE;
-        const V2 pm = *(const V2*)((const real*)(stk + T::OFF_PREV) + ty * TX + cx);
-        V2 sr;
+        real pm[CT], sr[CT];
+        ld16((const real*)(stk + T::OFF_PREV) + ty * TX + cx, pm);
         if (k >= zs0 && k <= zs1) {
-            sr = *(const V2*)((const real*)(stk + T::OFF_SRC) + ty * TX + cx);
+            ld16((const real*)(stk + T::OFF_SRC) + ty * TX + cx, sr);
         } else {
-            sr.x = (real)0;
-            sr.y = (real)0;
+#pragma unroll
+            for (int i = 0; i < CT; ++i) sr[i] = (real)0;
         }
-        if ((mineA || mineB) && ok) {
+        if (any && ok) {
             // ax (w (N^{k-1} + N^{k+1}) + w0 N^k) over the two x neighbours, likewise along y
-            const real vA = a.a1 * C.ca - pm.x + a.axw * (L.XA + N.XA) + a.axw0 * C.XA + a.ayw * (L.YA + N.YA) +
-                            a.ayw0 * C.YA + a.a6 * (L.ca + N.ca) + s * sr.x;
-            const real vB = a.a1 * C.cb - pm.y + a.axw * (L.XB + N.XB) + a.axw0 * C.XB + a.ayw * (L.YB + N.YB) +
-                            a.ayw0 * C.YB + a.a6 * (L.cb + N.cb) + s * sr.y;
+            real v[CT];
+#pragma unroll
+            for (int i = 0; i < CT; ++i)
+                v[i] = a.a1 * C.c[i] - pm[i] + a.axw * (L.X[i] + N.X[i]) + a.axw0 * C.X[i] + a.ayw * (L.Y[i] + N.Y[i]) +
+                       a.ayw0 * C.Y[i] + a.a6 * (L.c[i] + N.c[i]) + s * sr[i];
             const int64_t row = (int64_t)k * sz + (int64_t)y * sy;
-            if (mineA && mineB) {
-                V2 v;
-                v.x = vA;
-                v.y = vB;
-                *(V2*)(o + row + x) = v;
-            } else if (mineA) {
-                o[row + x] = vA;
+            if (all) {
+                st16(o + row + x, v);
             } else {
-                o[row + x + 1] = vB;
+#pragma unroll
+                for (int i = 0; i < CT; ++i)
+                    if (mine[i]) o[row + x + i] = v[i];
             }
             if (tma_x_faces<real>() && a.mur) {
-                // Mur x faces (the formula and the summation order of k_mur_faces)
+                // Mur x faces (the formula and the summation order of k_mur_faces): face node b,
+                // its interior neighbour q
                 const bool o2 = a.mur != 1;
-                if (x == 0 && mineB)   // b = x (this pair's first cell), q = x + 1
-                    o[row] = a.mf0 * (pm.x + vB) + a.mf1 * (C.ca + C.cb) - pm.y +
-                             a.mfy * (o2 ? C.YA + C.YB : (real)0) + a.mfz * (o2 ? N.ca + L.ca + N.cb + L.cb : (real)0);
-                if (mineA && x == ex - 2)   // q = x, b = x + 1 (this pair's second cell)
-                    o[row + x + 1] = a.mf0 * (pm.y + vA) + a.mf1 * (C.cb + C.ca) - pm.x +
-                                     a.mfy * (o2 ? C.YB + C.YA : (real)0) +
-                                     a.mfz * (o2 ? N.cb + L.cb + N.ca + L.ca : (real)0);
-                if (mineB && x + 1 == ex - 2) {   // q = x + 1, b = x + 2 (the next pair's first cell)
-                    const real nmb = cx + 2 < TX ? ((const real*)(stk + T::OFF_PREV))[ty * TX + cx + 2]
-                                                 : a.prev[comp][row + x + 2];
-                    o[row + x + 2] = a.mf0 * (nmb + vB) + a.mf1 * (C.xq + C.cb) - pm.y +
-                                     a.mfy * (o2 ? hrow(k, 1)[2] + hrow(k, -1)[2] + C.YB : (real)0) +
-                                     a.mfz * (o2 ? N.xq + L.xq + N.cb + L.cb : (real)0);
+                if (x == 0 && mine[1])   // b = x (the thread's first cell), q = x + 1
+                    o[row] = a.mf0 * (pm[0] + v[1]) + a.mf1 * (C.c[0] + C.c[1]) - pm[1] +
+                             a.mfy * (o2 ? C.Y[0] + C.Y[1] : (real)0) +
+                             a.mfz * (o2 ? N.c[0] + L.c[0] + N.c[1] + L.c[1] : (real)0);
+#pragma unroll
+                for (int i = 0; i + 1 < CT; ++i)
+                    if (mine[i] && x + i == ex - 2)   // q = x + i, b = x + i + 1 (a cell of this thread)
+                        o[row + x + i + 1] = a.mf0 * (pm[i + 1] + v[i]) + a.mf1 * (C.c[i + 1] + C.c[i]) - pm[i] +
+                                             a.mfy * (o2 ? C.Y[i + 1] + C.Y[i] : (real)0) +
+                                             a.mfz * (o2 ? N.c[i + 1] + L.c[i + 1] + N.c[i] + L.c[i] : (real)0);
+                if (mine[CT - 1] && x + CT - 1 == ex - 2) {   // q = the last cell, b = the next thread's first
+                    const real nmb = cx + CT < TX ? ((const real*)(stk + T::OFF_PREV))[ty * TX + cx + CT]
+                                                  : a.prev[comp][row + x + CT];
+                    o[row + x + CT] = a.mf0 * (nmb + v[CT - 1]) + a.mf1 * (C.xq + C.c[CT - 1]) - pm[CT - 1] +
+                                      a.mfy * (o2 ? hrow(k, 1)[CT] + hrow(k, -1)[CT] + C.Y[CT - 1] : (real)0) +
+                                      a.mfz * (o2 ? N.xq + L.xq + N.c[CT - 1] + L.c[CT - 1] : (real)0);
                 }
             }
         }
@@ -423,7 +454,8 @@ cudaError_t launch_stencil_tma(const TmaMaps* maps, real* const out[4], real* co
         sm.src[c] = maps->src[c];
     }
     {
-        const cudaError_t le = launch_dep(dep_launch_on<real>(st), k_stencil_tma<real>, dim3(grd), dim3(TX / 2 * TY),
+        const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepStencil), k_stencil_tma<real>, dim3(grd),
+                                          dim3(TX / cells_per_thread<real>() * TY),
                                           T::SMEM, st, sm, a, g.sy, g.sz);
         if (le != cudaSuccess) return le;
     }
