@@ -479,6 +479,29 @@ struct Fields6 {
     __host__ __device__ real& at(int c, int64_t id) const { return p[id * kEBStride + c]; }
 };
 
+// Field energy density at a node, eps0 E^2 / 2 + B^2 / (2 mu0).  From FP32 components it is formed
+// in FP32 (relative error below 1e-6, against the 6e-8 of the stored values), so that a sum over
+// nodes in FP64 spends one conversion and one add of the FP64 pipe per node.
+__device__ __forceinline__ double node_energy(float ex, float ey, float ez, float bx, float by, float bz)
+{
+    constexpr double eps0 = 1.0 / (kMu0 * kC * kC);
+    const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const float b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+    return (double)fmaf((float)(0.5 * eps0), e2, (float)(0.5 / kMu0) * b2);
+}
+__device__ __forceinline__ double node_energy(double ex, double ey, double ez, double bx, double by, double bz)
+{
+    constexpr double eps0 = 1.0 / (kMu0 * kC * kC);
+    double e2 = 0.0, b2 = 0.0;
+    e2 += ex * ex;
+    b2 += bx * bx;
+    e2 += ey * ey;
+    b2 += by * by;
+    e2 += ez * ez;
+    b2 += bz * bz;
+    return 0.5 * eps0 * e2 + 0.5 * b2 / kMu0;
+}
+
 // Six separate arrays of E_x .. B_z (the allocation-free energy's caller arrays).
 template <typename real>
 struct Fields6Soa {

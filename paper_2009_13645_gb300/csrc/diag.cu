@@ -30,21 +30,20 @@ __global__ void k_final(const double* __restrict__ partial, int npartial, int nc
 // The power step runs in the step tail (power_point in kernels.h, the launch in fields.cu).
 
 // ---- field energy ----------------------------------------------------------------------
+// The field energy (node_energy summed in FP64 over every node).
 template <typename real>
 __global__ void __launch_bounds__(kRedThreads) k_energy(Fields6<real> eb, int64_t n, double* __restrict__ partial)
 {
     __shared__ double sh[32];
-    constexpr double eps0 = 1.0 / (kMu0 * kC * kC);
     double acc = 0.0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        double e2 = 0.0, b2 = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double e = (double)eb.at(c, t), b = (double)eb.at(3 + c, t);
-            e2 += e * e;
-            b2 += b * b;
+        if constexpr (sizeof(real) == 4) {
+            const float4 e = __ldg(reinterpret_cast<const float4*>(eb.p + t * kEBStride));
+            const float2 b = __ldg(reinterpret_cast<const float2*>(eb.p + t * kEBStride + 4));
+            acc += node_energy(e.x, e.y, e.z, e.w, b.x, b.y);
+        } else {
+            acc += node_energy(eb.at(0, t), eb.at(1, t), eb.at(2, t), eb.at(3, t), eb.at(4, t), eb.at(5, t));
         }
-        acc += 0.5 * eps0 * e2 + 0.5 * b2 / kMu0;
     }
     const double tot = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
@@ -63,16 +62,27 @@ cudaError_t launch_energy(const Fields6<real>& eb, const Geom& g, double* partia
 // ---- bunching factor -------------------------------------------------------------------
 template <typename real>
 __global__ void __launch_bounds__(kRedThreads) k_bunching(Particles<real> P, int64_t np, Geom g, double kb,
+                                                          const float2* __restrict__ tab, float kbdz,
                                                           double* __restrict__ partial)
 {
     __shared__ double sh[32];
     double cr = 0.0, ci = 0.0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-        const double z = g.z0 + ((double)P.iz[p] + (double)P.fz[p]) * g.dz;
-        double s, c;
-        sincos(kb * z, &s, &c);
-        cr += c;
-        ci += s;
+        const int iz = P.iz[p];
+        if (tab && iz >= 0 && iz < g.nz) {
+            // the plane's phase from the FP64 table, turned by the FP32 phase of the offset
+            const float2 t = __ldg(tab + iz);
+            float sf, cf;
+            sincosf(kbdz * (float)P.fz[p], &sf, &cf);
+            cr += (double)(t.x * cf - t.y * sf);
+            ci += (double)(t.y * cf + t.x * sf);
+        } else {
+            const double z = g.z0 + ((double)iz + (double)P.fz[p]) * g.dz;
+            double s, c;
+            sincos(kb * z, &s, &c);
+            cr += c;
+            ci += s;
+        }
     }
     const double tr = block_sum(cr, sh);
     const double ti = block_sum(ci, sh);
@@ -92,14 +102,32 @@ __global__ void k_bunch_final(double* out3, double inv_n)
     }
 }
 
+// (cos, sin) of k_b z at every node plane, in FP64, rounded to FP32.
+__global__ void k_bunch_table(float2* __restrict__ tab, int nz, double z0, double dz, double kb)
+{
+    const int k = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (k >= nz) return;
+    double s, c;
+    sincos(kb * (z0 + (double)k * dz), &s, &c);
+    tab[k] = make_float2((float)c, (float)s);
+}
+
 template <typename real>
 cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g, double kb, double* partial,
-                            int npartial, double* out3, cudaStream_t st)
+                            int npartial, double* out3, float2* tab, cudaStream_t st)
 {
     if (np <= 0) {
         return cudaMemsetAsync(out3, 0, 3 * sizeof(double), st);
     }
-    k_bunching<real><<<npartial, kRedThreads, 0, st>>>(P, np, g, kb, partial);
+    // FP32 offsets: the phase of a particle is its plane's (FP64 table) plus k_b dz times its offset
+    // (FP32, below k_b dz); FP64 offsets keep the whole phase in FP64
+    const bool use_tab = tab && sizeof(real) == 4;
+    if (use_tab) {
+        k_bunch_table<<<(g.nz + 255) / 256, 256, 0, st>>>(tab, g.nz, g.z0, g.dz, kb);
+        count_launches(1);
+    }
+    k_bunching<real><<<npartial, kRedThreads, 0, st>>>(P, np, g, kb, use_tab ? tab : nullptr, (float)(kb * g.dz),
+                                                       partial);
     k_final<<<1, kRedThreads, 0, st>>>(partial, npartial, 2, 1.0, out3 + 1);
     k_bunch_final<<<1, 32, 0, st>>>(out3, 1.0 / (double)np);
     count_launches(3);
@@ -333,7 +361,7 @@ cudaError_t launch_bunch_sample(const Particles<real>& P, int64_t np, const Geom
                                                    double*, int, double*, cudaStream_t);                             \
     template cudaError_t launch_energy<real>(const Fields6<real>&, const Geom&, double*, int, double*, cudaStream_t); \
     template cudaError_t launch_bunching<real>(const Particles<real>&, int64_t, const Geom&, double, double*, int,    \
-                                               double*, cudaStream_t);
+                                               double*, float2*, cudaStream_t);
 MITHRA_INST(float)
 MITHRA_INST(double)
 #undef MITHRA_INST

@@ -3,6 +3,7 @@
 // (Sec. "Field Evaluation").
 #include <algorithm>
 #include <cstring>
+#include <utility>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -151,10 +152,17 @@ __device__ __forceinline__ real mur_face_value(const MurArgs<real>& a, int comp,
     return a.f0[ax] * (nm[ib] + n1[iq]) + a.f1[ax] * (n0[ib] + n0[iq]) - nm[iq] + a.ft[ax][0] * ta + a.ft[ax][1] * tb;
 }
 
-// Two rows of face (AX, side sd) of component comp: the rows v = v0 + 2 rp and v0 + 2 rp + 1 of the
-// tangential axis v, each 128 threads walking its interior nodes along u (x for the y and z faces:
-// coalesced).
-constexpr int kFaceRowThreads = 128;
+// Rows of face (AX, side sd) of component comp: block rp takes the kFaceRows rows v = v0 +
+// kFaceRows rp + r of the tangential axis v; each of its threads kFaceRowsPerThread of them at one
+// position u (128 threads per row group walking the interior nodes along u: x for the y and z faces,
+// coalesced).  A thread evaluates all its nodes before it stores any, so that their loads are in
+// flight together.
+constexpr int kTailThreads = 256;   // threads of a step-tail block
+#ifndef MITHRA_FACE_ROWS_PER_THREAD
+#define MITHRA_FACE_ROWS_PER_THREAD 1
+#endif
+constexpr int kFaceRowThreads = 128, kFaceRowsPerThread = MITHRA_FACE_ROWS_PER_THREAD;
+constexpr int kFaceRows = kTailThreads / kFaceRowThreads * kFaceRowsPerThread;
 template <int AX, typename real>
 __device__ __forceinline__ void mur_face_rows(const MurArgs<real>& a, int comp, int sd, int rp, int64_t sy, int64_t sz)
 {
@@ -163,15 +171,24 @@ __device__ __forceinline__ void mur_face_rows(const MurArgs<real>& a, int comp, 
     const int ev = V == 1 ? a.ey[comp] : a.ez[comp];
     const int en = AX == 0 ? a.ex[comp] : (AX == 1 ? a.ey[comp] : a.ez[comp]);
     const int v0 = AX == 0 ? a.kmin : 1, v1 = AX == 0 ? min(a.kmax, ev - 2) : ev - 2;
-    const int v = v0 + 2 * rp + (int)(threadIdx.x / kFaceRowThreads);
-    if (v > v1) return;
+    const int vb = v0 + kFaceRows * rp + (int)(threadIdx.x / kFaceRowThreads) * kFaceRowsPerThread;
+    if (vb > v1) return;
 #pragma unroll 1
     for (int u = 1 + (int)(threadIdx.x % kFaceRowThreads); u <= eu - 2; u += kFaceRowThreads) {
-        int p[3];
-        p[AX] = sd ? en - 1 : 0;
-        p[U] = u;
-        p[V] = v;
-        a.n1[comp][lin(p[0], p[1], p[2], sy, sz)] = mur_face_value_ax<AX>(a, comp, sd, p, sy, sz);
+        real val[kFaceRowsPerThread];
+        int64_t id[kFaceRowsPerThread];
+#pragma unroll
+        for (int r = 0; r < kFaceRowsPerThread; ++r) {
+            int p[3];
+            p[AX] = sd ? en - 1 : 0;
+            p[U] = u;
+            p[V] = min(vb + r, v1);   // rows past the face repeat its last row (stored once below)
+            id[r] = lin(p[0], p[1], p[2], sy, sz);
+            val[r] = mur_face_value_ax<AX>(a, comp, sd, p, sy, sz);
+        }
+#pragma unroll
+        for (int r = 0; r < kFaceRowsPerThread; ++r)
+            if (vb + r <= v1) a.n1[comp][id[r]] = val[r];
     }
 }
 
@@ -213,79 +230,74 @@ struct MurEdgeCoef {
     real C[4];      // n values (all points alike)
 };
 
-// One edge (corners = false; t indexes the 12 edges' points) or corner (corners = true, t < 8)
-// point of component comp.  The corners read the new edge values of other blocks (through L2).
-// A neighbour on a face that the same launch writes (faces of axes >= face0 / 2; the TMA stencil
-// wrote the x faces when face0 = 2) is evaluated here from the face formula, so the edges and
-// corners need not wait for the face blocks.
-template <typename real>
-__device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeCoef<real>& cf, int64_t sy, int64_t sz,
-                                          int comp, bool corners, int64_t t)
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>)
 {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+// f(std::integral_constant<int, i>) for i = 0 .. N - 1, i usable as a template argument.
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// One edge point (class C < 3: the edges whose free axis is C; `which` bit 0 / 1: the high end of
+// the lower / higher of the two boundary axes; pos: the point's index along C) or corner (C = 3,
+// `which` bit d: the high end of axis d) of component comp.  The boundary axes are known at compile
+// time, so the loads of all the point's terms can be in flight together.  The corners read the
+// new edge values of other blocks (through L2).  A neighbour on a face that the same launch writes
+// (faces of axes >= face0 / 2; the TMA stencil wrote the x faces when face0 = 2) is evaluated here
+// from the face formula, so the edges and corners need not wait for the face blocks.
+template <int C, typename real>
+__device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeCoef<real>& cf, int64_t sy, int64_t sz,
+                                          int comp, int which, int pos)
+{
+    constexpr int NS = C == 3 ? 3 : 2;                                    // boundary axes
+    constexpr int U = (C + 1) % 3, V = (C + 2) % 3;
+    constexpr int AX[3] = {C == 3 ? 0 : (U < V ? U : V), C == 3 ? 1 : (U < V ? V : U), 2};
     const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
-    int p[3], sg[3], axes[3], ns = 0, cls = 3;
-    if (corners) {
-        for (int d = 0; d < 3; ++d) {
-            const int hi = (int)(t >> d) & 1;
-            p[d] = hi ? e[d] - 1 : 0;
-            sg[ns] = hi ? -1 : 1;
-            axes[ns++] = d;
-        }
+    int p[3], sg[3];
+    if constexpr (C == 3) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) p[d] = ((which >> d) & 1) ? e[d] - 1 : 0;
     } else {
-        // 12 edges: the free axis f runs over 1..e[f]-2, the two others sit on a boundary
-        bool found = false;
-        for (int f = 0; f < 3 && !found; ++f) {
-            const int64_t len = e[f] - 2;
-            for (int c = 0; c < 4 && !found; ++c) {
-                if (t < len) {
-                    const int u = (f + 1) % 3, v = (f + 2) % 3;
-                    p[f] = 1 + (int)t;
-                    p[u] = (c & 1) ? e[u] - 1 : 0;
-                    p[v] = (c & 2) ? e[v] - 1 : 0;
-                    const int lo = u < v ? u : v, hi = u < v ? v : u;
-                    axes[0] = lo;
-                    axes[1] = hi;
-                    sg[0] = (p[lo] == 0) ? 1 : -1;
-                    sg[1] = (p[hi] == 0) ? 1 : -1;
-                    ns = 2;
-                    cls = f;
-                    found = true;
-                } else {
-                    t -= len;
-                }
-            }
-        }
-        if (!found) return;
+        p[C] = pos;
+        p[AX[0]] = (which & 1) ? e[AX[0]] - 1 : 0;
+        p[AX[1]] = (which & 2) ? e[AX[1]] - 1 : 0;
     }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sg[s] = p[AX[s]] == 0 ? 1 : -1;
     real* __restrict__ n1 = a.n1[comp];
     const real* __restrict__ n0 = a.n0[comp];
     const real* __restrict__ nm = a.nm[comp];
-    const int npts = 1 << ns;
     real num = (real)0;
-    for (int ei = 0; ei < npts; ++ei) {
+    static_for<(1 << NS)>([&](auto eic) {
+        constexpr int ei = decltype(eic)::value;
         int q[3] = {p[0], p[1], p[2]};
-        for (int s = 0; s < ns; ++s)
-            if ((ei >> s) & 1) q[axes[s]] += sg[s];
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if ((ei >> s) & 1) q[AX[s]] += sg[s];
         const int64_t id = lin(q[0], q[1], q[2], sy, sz);
-        if (ei != 0) {
+        if constexpr (ei != 0) {
             // the point's boundary axes: those not moved inward
-            int nb = 0, fa = 0;
-            for (int s = 0; s < ns; ++s)
-                if (!((ei >> s) & 1)) {
-                    ++nb;
-                    fa = axes[s];
-                }
+            constexpr int nb = NS - ((ei & 1) + ((ei >> 1) & 1) + ((ei >> 2) & 1));
+            constexpr int fa = !(ei & 1) ? AX[0] : (!((ei >> 1) & 1) ? AX[1] : AX[2]);   // nb = 1: that axis
             real v;
-            if (nb == 1 && 2 * fa >= a.face0)
-                v = mur_face_value(a, comp, fa, q[fa] == 0 ? 0 : 1, q, sy, sz);   // a face node
-            else if (nb >= 1)
-                v = __ldcg(n1 + id);   // an edge node (corners), or an x-face node of the stencil
-            else
-                v = n1[id];            // the interior node
-            num += cf.A[cls][ei] * v;
+            if constexpr (nb == 1) {
+                if (2 * fa >= a.face0)
+                    v = mur_face_value_ax<fa>(a, comp, q[fa] == 0 ? 0 : 1, q, sy, sz);   // a face node
+                else
+                    v = __ldcg(n1 + id);   // an x-face node of the stencil
+            } else if constexpr (nb >= 2) {
+                v = __ldcg(n1 + id);       // an edge node (corners)
+            } else {
+                v = n1[id];                // the interior node
+            }
+            num += cf.A[C][ei] * v;
         }
-        num += cf.B[cls][ei] * nm[id] + cf.C[cls] * n0[id];
-    }
+        num += cf.B[C][ei] * nm[id] + cf.C[C] * n0[id];
+    });
     n1[lin(p[0], p[1], p[2], sy, sz)] = num;
 }
 
@@ -299,12 +311,12 @@ __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeC
 // they need are evaluated in place), adds the power partials (compensated, in a fixed order) into
 // the step's series entry once the window is complete, and advances the step state: nothing
 // after this launch in the step reads it.
-constexpr int kTailThreads = 256;
+
 constexpr int kBoxRecs = 4 * kTailThreads;   // push records per deposit-box block of the tail
 constexpr int kBoxWin = 64;                  // z chunks per block kept in shared memory
 template <typename real>
 __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, MurEdgeCoef<real> cf, int64_t sy,
-                                                            int64_t sz, int64_t maxpts, int nfx, int nfy, int nfz,
+                                                            int64_t sz, int nfx, int nfy, int nfz,
                                                             int nbe, int npw, int npt, int nbb, Fields6<real> eb,
                                                             Geom g, StepTail tl, unsigned* counter)
 {
@@ -338,8 +350,24 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
     }
     const int b = (int)blockIdx.x;
     if (b < ne) {
-        const int64_t t = (int64_t)(b % nbe) * blockDim.x + threadIdx.x;
-        if (t < maxpts) mur_point(a, cf, sy, sz, b / nbe, false, t);
+        // point t of the 12 edges: free axis f, edge c of its four, position 1 + t along f
+        int64_t t = (int64_t)(b % nbe) * blockDim.x + threadIdx.x;
+        const int comp = b / nbe;
+        const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
+        for (int f = 0; f < 3; ++f) {
+            const int64_t len = e[f] - 2;
+            if (t < 4 * len) {
+                const int c = (int)(t / len), pos = 1 + (int)(t % len);
+                if (f == 0)
+                    mur_point<0>(a, cf, sy, sz, comp, c, pos);
+                else if (f == 1)
+                    mur_point<1>(a, cf, sy, sz, comp, c, pos);
+                else
+                    mur_point<2>(a, cf, sy, sz, comp, c, pos);
+                break;
+            }
+            t -= 4 * len;
+        }
     } else if (b < ne + npw) {
         const StepDev sd = *tl.sd;
         const int64_t pl = (int64_t)(b - ne) * blockDim.x + threadIdx.x;
@@ -355,42 +383,76 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
         }
     } else {
         // the deposit box from the push's block records: this block takes kBoxRecs consecutive
-        // records (cell order, so they span few z chunks), gathers the whole box and the xy
-        // boxes of the chunks in a window of kBoxWin chunks in shared memory, and adds them to
-        // the deposit box with a few atomics (a chunk outside the window goes straight out)
+        // records (cell order, so they span few z chunks), each thread RPT consecutive ones; the
+        // whole box and the xy boxes of the chunks are reduced per warp (the warp's records reach
+        // one or two chunks) and gathered with one shared-memory atomic per warp and bound in a
+        // window of kBoxWin chunks, then added to the deposit box with a few atomics (a chunk
+        // outside the window goes straight out)
         __shared__ int sg[6], swin[kBoxWin][4], scb;
+        constexpr int RPT = kBoxRecs / kTailThreads;
+        constexpr int kLo = 0x7fffffff, kHi = (int)0x80000000;
+        const unsigned full = 0xffffffffu;
+        const int lane = (int)threadIdx.x & 31;
         const int nchunk = emit_chunks(g.nz);
-        const int64_t base = (int64_t)(b - ne - npw - npt) * kBoxRecs;
-        if (threadIdx.x < 6) sg[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : (int)0x80000000;
-        for (int q = threadIdx.x; q < 4 * kBoxWin; q += blockDim.x)
-            swin[q >> 2][q & 3] = (q & 3) < 2 ? 0x7fffffff : (int)0x80000000;
-        if (threadIdx.x == 0) scb = 0x7fffffff;
-        __syncthreads();
-        int v[kBoxRecs / kTailThreads][6];
-        for (int i = 0; i < kBoxRecs / kTailThreads; ++i) {
-            const int64_t r = base + i * kTailThreads + threadIdx.x;
-            for (int q = 0; q < 6; ++q)
-                v[i][q] = r < tl.nrec ? __ldcg(tl.box_rec + 6 * r + q) : (q < 3 ? 0x7fffffff : (int)0x80000000);
-            if (v[i][0] != 0x7fffffff) {
-                for (int q = 0; q < 3; ++q) {
-                    atomicMin(sg + q, v[i][q]);
-                    atomicMax(sg + 3 + q, v[i][3 + q]);
-                }
-                atomicMin(&scb, max((v[i][2] - 2) / kEmitKZ, 0));
+        const int64_t base = (int64_t)(b - ne - npw - npt) * kBoxRecs + (int64_t)RPT * threadIdx.x;
+        if (threadIdx.x < 6) sg[threadIdx.x] = threadIdx.x < 3 ? kLo : kHi;
+        for (int q = threadIdx.x; q < 4 * kBoxWin; q += blockDim.x) swin[q >> 2][q & 3] = (q & 3) < 2 ? kLo : kHi;
+        if (threadIdx.x == 0) scb = kLo;
+        int v[RPT][6], c0[RPT], c1[RPT];
+        int lo[3] = {kLo, kLo, kLo}, hi[3] = {kHi, kHi, kHi}, cmin = kLo, cmax = kHi;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int64_t r = base + i;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[i][q] = r < tl.nrec ? __ldcg(tl.box_rec + 6 * r + q) : (q < 3 ? kLo : kHi);
+            // the z chunks of this record's node planes [lo_z - 1, hi_z + 2] (empty record: none)
+            c0[i] = v[i][0] != kLo ? max((v[i][2] - 2) / kEmitKZ, 0) : kLo;
+            c1[i] = v[i][0] != kLo ? min((v[i][5] + 1) / kEmitKZ, nchunk - 1) : kHi;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                lo[q] = min(lo[q], v[i][q]);
+                hi[q] = max(hi[q], v[i][3 + q]);
             }
+            cmin = min(cmin, c0[i]);
+            cmax = max(cmax, c1[i]);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            lo[q] = __reduce_min_sync(full, lo[q]);
+            hi[q] = __reduce_max_sync(full, hi[q]);
+        }
+        const int wc0 = __reduce_min_sync(full, cmin), wc1 = __reduce_max_sync(full, cmax);
+        __syncthreads();   // the shared bounds are initialised
+        if (lane == 0 && wc0 <= wc1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                atomicMin(sg + q, lo[q]);
+                atomicMax(sg + 3 + q, hi[q]);
+            }
+            atomicMin(&scb, wc0);
         }
         __syncthreads();
         const int cb = scb;
-        for (int i = 0; i < kBoxRecs / kTailThreads; ++i) {
-            if (v[i][0] == 0x7fffffff) continue;
-            // the z chunks of this record's node planes [lo_z - 1, hi_z + 2]
-            const int c0 = max((v[i][2] - 2) / kEmitKZ, 0), c1 = min((v[i][5] + 1) / kEmitKZ, nchunk - 1);
-            for (int c = c0; c <= c1; ++c) {
+        for (int c = wc0; c <= wc1; ++c) {   // the same chunks for the whole warp
+            int x0 = kLo, y0 = kLo, x1 = kHi, y1 = kHi;
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+                if (c0[i] <= c && c <= c1[i]) {
+                    x0 = min(x0, v[i][0]);
+                    y0 = min(y0, v[i][1]);
+                    x1 = max(x1, v[i][3]);
+                    y1 = max(y1, v[i][4]);
+                }
+            x0 = __reduce_min_sync(full, x0);
+            y0 = __reduce_min_sync(full, y0);
+            x1 = __reduce_max_sync(full, x1);
+            y1 = __reduce_max_sync(full, y1);
+            if (lane == 0 && x0 != kLo) {
                 int* w = c - cb < kBoxWin ? swin[c - cb] : tl.box_out + 6 + 4 * c;
-                atomicMin(w, v[i][0]);
-                atomicMin(w + 1, v[i][1]);
-                atomicMax(w + 2, v[i][3]);
-                atomicMax(w + 3, v[i][4]);
+                atomicMin(w, x0);
+                atomicMin(w + 1, y0);
+                atomicMax(w + 2, x1);
+                atomicMax(w + 3, y1);
             }
         }
         __syncthreads();
@@ -409,7 +471,7 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
     }
     if (last_block(counter, (unsigned)nrest)) {
         const int c = (int)threadIdx.x >> 3;
-        if (c < a.ncomp) mur_point(a, cf, sy, sz, c, true, (int64_t)(threadIdx.x & 7));
+        if (c < a.ncomp) mur_point<3>(a, cf, sy, sz, c, (int)(threadIdx.x & 7), 0);
         const StepDev sd = *tl.sd;
         if (npw > 0 && sd.emit) {
             double s = 0.0, comp = 0.0;
@@ -892,9 +954,9 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
         a.ft[ax][0] = (real)m.ft[ax][0];
         a.ft[ax][1] = (real)m.ft[ax][1];
     }
-    // face blocks per side and component along each normal axis: two rows of the axis's longest
-    // tangential v range each (mur_face_rows)
-    static_assert(2 * kFaceRowThreads == kTailThreads, "two face rows per tail block");
+    // face blocks per side and component along each normal axis: kFaceRows rows of the axis's
+    // longest tangential v range each (mur_face_rows)
+    static_assert(kTailThreads % kFaceRowThreads == 0, "whole row groups per tail block");
     int nf[3] = {0, 0, 0};
     for (int ax = a.face0 / 2; ax < 3; ++ax) {
         int rows = 0;
@@ -903,7 +965,7 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
             const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
             if (e[u] - 2 > 0) rows = std::max(rows, e[v] - 2);
         }
-        nf[ax] = (rows + 1) / 2;
+        nf[ax] = (rows + kFaceRows - 1) / kFaceRows;
     }
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
     const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
@@ -921,7 +983,7 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
         const int nbb = (int)((tail.nrec + kBoxRecs - 1) / kBoxRecs);
         const cudaError_t le = launch_dep(dep_launch_on<real>(st, kDepTail), k_step_tail<real>,
                                           dim3((unsigned)(nface + ncomp * nbe + npw + npt + nbb)), dim3(kTailThreads), 0,
-                                          st, a, ec, g.sy, g.sz, edges, nf[0], nf[1], nf[2], nbe, npw, npt, nbb, E6, g,
+                                          st, a, ec, g.sy, g.sz, nf[0], nf[1], nf[2], nbe, npw, npt, nbb, E6, g,
                                           tail, counter);
         if (le != cudaSuccess) return le;
     }

@@ -414,8 +414,10 @@ struct BunchSample {
 template <typename real>
 cudaError_t launch_bunch_sample(const Particles<real>& P, int64_t np, const Geom& g, const BunchSample& b,
                                 double* partial, int npartial, double* series, cudaStream_t st);
+// Bunching factor |<exp(i k_b z)>| and its real and imaginary parts into out3.  tab (nz entries,
+// may be null): scratch for the FP32 path's table of the node planes' phases.
 template <typename real>
 cudaError_t launch_bunching(const Particles<real>& P, int64_t np, const Geom& g, double kb, double* partial,
-                            int npartial, double* out3, cudaStream_t st);
+                            int npartial, double* out3, float2* tab, cudaStream_t st);
 
 }  // namespace mithra

@@ -61,6 +61,11 @@ void mithra::count_launches(int64_t n)
     t_launches += n;
 }
 static int64_t launch_count() { return t_launches; }
+
+// Block partials of the run's reductions: enough blocks of 256 threads to fill the GPU (8 on each of
+// its 152 SMs), and one per 256 nodes of the power plane.
+constexpr int kMinPartials = 1216;
+static int run_partials(int64_t plane) { return std::max<int>(kMinPartials, (int)((plane + 255) / 256)); }
 extern "C" int64_t mithra_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" const char* mithra_last_error(void) { return g_err.c_str(); }
@@ -260,7 +265,8 @@ struct RunT final : mithra_run {
     double* ring = nullptr;
     double* acc = nullptr;      // running DFT accumulators of the power plane
     double* partial = nullptr;
-    int npartial = 304;
+    float2* btab = nullptr;   // bunching: the node planes' phases (FP32 path)
+    int npartial = kMinPartials;
     double* ser_p = nullptr;
     double* ser_e = nullptr;
     int64_t ser_cap = 0;
@@ -384,12 +390,13 @@ struct RunT final : mithra_run {
             return fail(MITHRA_ENOMEM, "device allocation failed (sort scratch)");
         const int M = (int)d.M;
         const size_t plane = (size_t)g.nx * g.ny;
-        npartial = std::max<int>(304, (int)((plane + 255) / 256));
+        npartial = run_partials(plane);
         ring = (double*)mem.get((size_t)M * 4 * plane * 8);
         acc = (double*)mem.get((size_t)8 * plane * 8);
         partial = (double*)mem.get((size_t)4 * npartial * 8);   // energy: [0, n); bunching: [n, 3n)
         small = (double*)mem.get(8 * 8);
-        if (!ring || !acc || !partial || !small)
+        if (sizeof(real) == 4) btab = (float2*)mem.get((size_t)g.nz * sizeof(float2));
+        if (!ring || !acc || !partial || !small || (sizeof(real) == 4 && !btab))
             return fail(MITHRA_ENOMEM, "device allocation failed (diagnostics)");
         CU(cudaMemsetAsync(ring, 0, (size_t)M * 4 * plane * 8, stream));
         CU(cudaMemsetAsync(acc, 0, (size_t)8 * plane * 8, stream));
@@ -927,7 +934,7 @@ struct RunT final : mithra_run {
             if (rc) return rc;
             CU(launch_energy<real>(E6, g, partial, npartial, small, stream));
         }
-        if (b3) CU(launch_bunching<real>(P, np, g, d.kb, partial + npartial, npartial, small + 4, stream));
+        if (b3) CU(launch_bunching<real>(P, np, g, d.kb, partial + npartial, npartial, small + 4, btab, stream));
         CU(cudaMemcpyAsync(h, small, 8, cudaMemcpyDeviceToHost, stream));
         double hb[3] = {0, 0, 0};
         CU(cudaMemcpyAsync(hb, small + 4, 24, cudaMemcpyDeviceToHost, stream));
@@ -1413,19 +1420,20 @@ int64_t mithra::footprint(const mithra_grid* gr, const mithra_undulator* u, cons
     // the power window M is only known after the rest frame is fixed; bound it by the run's steps
     const int64_t plane = (int64_t)gr->nx * gr->ny;
     const int64_t M = std::min<int64_t>(std::max<int64_t>(nsteps, 1), 4096);
-    t += up(M * 4 * plane * 8) + up(2 * M * 8) + 2 * up(4 * 304 * 8) + up(64);
+    const int64_t np_ = run_partials(plane);
+    t += up(M * 4 * plane * 8) + up(2 * M * 8) + 2 * up(4 * np_ * 8) + up(64);
     int64_t cap = 1024;
     while (cap < nsteps) cap *= 2;
     t += 4 * up(cap * 8);                                                     // series (old and new while growing)
     t += 2 * up(deposit_box_words(gr->nz) * 4) + up(6 * push_blocks(n) * 4) + 2 * up(gr->nz * 32);
-    t += up(gr->nz * 16);                                                     // boxes and records, phase tables
+    t += up(gr->nz * 16) + up(gr->nz * 8);                                    // phase tables, bunching table
     t += up(n * 48);                                                          // lab particles during the boost
     if (gr->nf_points > 0) {                                                  // spectrum: ring, accumulators, series
         const int64_t nf = gr->nf_points;
-        t += up(M * 4 * plane * 8) + up(nf * 8 * plane * 8) + 4 * up(nf * 8) + up(nf * 4 * 304 * 8) +
+        t += up(M * 4 * plane * 8) + up(nf * 8 * plane * 8) + 4 * up(nf * 8) + up(nf * np_ * 8) +
              2 * up(cap * nf * 8);
     }
-    if (gr->bunch_every > 0) t += up(14 * 304 * 8) + 2 * up((cap / gr->bunch_every + 1) * 15 * 8);
+    if (gr->bunch_every > 0) t += up(14 * np_ * 8) + 2 * up((cap / gr->bunch_every + 1) * 15 * 8);
     // the small buffers (step state, counters, error word, seed planes' bookkeeping) and the 256
     // bytes of alignment slack every allocation takes from a caller's allocator (at most 128)
     t += 128 * 256;

@@ -55,22 +55,13 @@ __device__ __forceinline__ double block_total(double v)
 template <typename real>
 __global__ void __launch_bounds__(kThreads) k_energy_tiles(mithra::Fields6Soa<real> eb, int64_t n, double* partial)
 {
-    constexpr double eps0 = 1.0 / (mithra::kMu0 * mithra::kC * mithra::kC);
     const int64_t base = (int64_t)blockIdx.x * kTileNodes;
     double acc = 0.0;
 #pragma unroll 4
     for (int q = 0; q < kItems; ++q) {
         const int64_t t = base + (int64_t)q * kThreads + threadIdx.x;
-        if (t < n) {
-            double e2 = 0.0, b2 = 0.0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double e = (double)eb.c[c][t], b = (double)eb.c[3 + c][t];
-                e2 += e * e;
-                b2 += b * b;
-            }
-            acc += 0.5 * eps0 * e2 + 0.5 * b2 / mithra::kMu0;
-        }
+        if (t < n)
+            acc += mithra::node_energy(eb.c[0][t], eb.c[1][t], eb.c[2][t], eb.c[3][t], eb.c[4][t], eb.c[5][t]);
     }
     const double tot = block_total(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
