@@ -10,12 +10,12 @@
 // source is copied only for the block's own planes and only where the tile meets the nodes the
 // step's push can have deposited into (the previous deposit box grown by a cell per sub-step);
 // elsewhere it is zero, so early in a run, with a compact bunch, most tiles skip its bytes.
-// Each thread owns two x-adjacent columns and keeps planes k-1, k, k+1 of them and of their
-// neighbours (x-1, x+2, and the rows above and below) in registers, reading only the new plane
-// k+1 from shared memory, with 64-bit (FP32) / 128-bit (FP64) loads for the column pairs; both
-// results leave in one vector store (coalesced rows).  Two cells per thread halve the per-cell
-// cost of the loop, the barrier and the addressing (the stencil is issue bound: 80 % issue with
-// one cell per thread; the FEL step's stencil went from 137 to 102 us).
+// Each thread owns the x-adjacent columns one 16-byte load fetches (four in FP32, two in FP64) and
+// keeps planes k-1, k, k+1 of them and of their neighbours (the columns either side, and the rows
+// above and below) in registers, reading only the new plane k+1 from shared memory with 16-byte
+// loads; the results leave in one vector store (coalesced rows).  Several cells per thread share
+// the per-cell cost of the loop, the barrier and the addressing (the stencil is issue bound: the
+// FEL step's stencil took 137 us with one cell per thread, 102 with two, 89 with four in FP32).
 //
 // In FP32 the threads next to an x boundary also write the Mur value of the face node beside them
 // (Sec. "First/Second Order ABCs"): every input of the face formula is already in their registers
