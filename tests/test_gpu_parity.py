@@ -409,7 +409,7 @@ def test_tma_stencil_matches_oracle_and_plain_kernel(shape, precision, tol, orde
             a, b = runs["tma"].field(c, lev), runs["plain"].field(c, lev)
             assert rel(a, o.field(c, lev)) < tol
             # the two kernels evaluate the same expression, but the compiler may contract it into
-            # FMAs differently (the TMA kernel updates two cells per thread): FP32 rounding
+            # FMAs differently (the TMA kernel updates four cells per FP32 thread): FP32 rounding
             # differences grow to a few 1e-6 over 25 steps of random fields
             assert rel(a, b) <= (1e-14 if precision == 0 else 1e-5)
 
