@@ -242,33 +242,23 @@ __device__ __forceinline__ void static_for(F&& f)
     static_for_impl(f, std::make_integer_sequence<int, N>{});
 }
 
-// One edge point (class C < 3: the edges whose free axis is C; `which` bit 0 / 1: the high end of
-// the lower / higher of the two boundary axes; pos: the point's index along C) or corner (C = 3,
-// `which` bit d: the high end of axis d) of component comp.  The boundary axes are known at compile
-// time, so the loads of all the point's terms can be in flight together.  The corners read the
-// new edge values of other blocks (through L2).  A neighbour on a face that the same launch writes
-// (faces of axes >= face0 / 2; the TMA stencil wrote the x faces when face0 = 2) is evaluated here
-// from the face formula, so the edges and corners need not wait for the face blocks.
+// The Mur value of an edge point (class C < 3: the edges whose free axis is C) or corner (C = 3)
+// p of component comp.  The boundary axes are known at compile time, so the loads of all the
+// point's terms can be in flight together.  A neighbour on a face that the same launch writes
+// (faces of axes >= face0 / 2; the TMA stencil wrote the x faces when face0 = 2) is evaluated
+// here from the face formula, and a corner's edge neighbours from the edge formula, so that no
+// point waits for the blocks that write its neighbours (the same code gives the same values).
 template <int C, typename real>
-__device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeCoef<real>& cf, int64_t sy, int64_t sz,
-                                          int comp, int which, int pos)
+__device__ __forceinline__ real mur_point_value(const MurArgs<real>& a, const MurEdgeCoef<real>& cf, int64_t sy,
+                                                int64_t sz, int comp, const int p[3])
 {
     constexpr int NS = C == 3 ? 3 : 2;                                    // boundary axes
     constexpr int U = (C + 1) % 3, V = (C + 2) % 3;
     constexpr int AX[3] = {C == 3 ? 0 : (U < V ? U : V), C == 3 ? 1 : (U < V ? V : U), 2};
-    const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
-    int p[3], sg[3];
-    if constexpr (C == 3) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) p[d] = ((which >> d) & 1) ? e[d] - 1 : 0;
-    } else {
-        p[C] = pos;
-        p[AX[0]] = (which & 1) ? e[AX[0]] - 1 : 0;
-        p[AX[1]] = (which & 2) ? e[AX[1]] - 1 : 0;
-    }
+    int sg[3];
 #pragma unroll
     for (int s = 0; s < NS; ++s) sg[s] = p[AX[s]] == 0 ? 1 : -1;
-    real* __restrict__ n1 = a.n1[comp];
+    const real* __restrict__ n1 = a.n1[comp];
     const real* __restrict__ n0 = a.n0[comp];
     const real* __restrict__ nm = a.nm[comp];
     real num = (real)0;
@@ -283,6 +273,7 @@ __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeC
             // the point's boundary axes: those not moved inward
             constexpr int nb = NS - ((ei & 1) + ((ei >> 1) & 1) + ((ei >> 2) & 1));
             constexpr int fa = !(ei & 1) ? AX[0] : (!((ei >> 1) & 1) ? AX[1] : AX[2]);   // nb = 1: that axis
+            constexpr int ea = (ei & 1) ? AX[0] : (((ei >> 1) & 1) ? AX[1] : AX[2]);      // nb = 2: the moved axis
             real v;
             if constexpr (nb == 1) {
                 if (2 * fa >= a.face0)
@@ -290,7 +281,7 @@ __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeC
                 else
                     v = __ldcg(n1 + id);   // an x-face node of the stencil
             } else if constexpr (nb >= 2) {
-                v = __ldcg(n1 + id);       // an edge node (corners)
+                v = mur_point_value<ea>(a, cf, sy, sz, comp, q);   // an edge node (corners)
             } else {
                 v = n1[id];                // the interior node
             }
@@ -298,19 +289,40 @@ __device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeC
         }
         num += cf.B[C][ei] * nm[id] + cf.C[C] * n0[id];
     });
-    n1[lin(p[0], p[1], p[2], sy, sz)] = num;
+    return num;
 }
 
-// The step tail, one launch of 1-D blocks of kTailThreads: blocks [0, ncomp nbe) the Mur edges of
-// component b / nbe; then npw blocks of the power step (plane points); then npt blocks of the
-// next step's phase tables (node planes); then nbb blocks that reduce the push's block records
-// into the deposit box (the whole box and its z chunks' xy boxes); then the Mur faces f >= face0,
-// per normal axis as many blocks per side and component as its largest face needs, which go
-// last so that the others are scheduled first.  The face blocks leave without arriving; the last
-// of the others to finish writes the 8 corners of every component (the edges are in; the faces
-// they need are evaluated in place), adds the power partials (compensated, in a fixed order) into
-// the step's series entry once the window is complete, and advances the step state: nothing
-// after this launch in the step reads it.
+// Edge point of class C < 3 (`which` bit 0 / 1: the high end of the lower / higher of the two
+// boundary axes; pos: its index along C) or corner (C = 3, `which` bit d: the high end of axis d).
+template <int C, typename real>
+__device__ __forceinline__ void mur_point(const MurArgs<real>& a, const MurEdgeCoef<real>& cf, int64_t sy, int64_t sz,
+                                          int comp, int which, int pos)
+{
+    constexpr int U = (C + 1) % 3, V = (C + 2) % 3;
+    constexpr int A0 = U < V ? U : V, A1 = U < V ? V : U;
+    const int e[3] = {a.ex[comp], a.ey[comp], a.ez[comp]};
+    int p[3];
+    if constexpr (C == 3) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) p[d] = ((which >> d) & 1) ? e[d] - 1 : 0;
+    } else {
+        p[C] = pos;
+        p[A0] = (which & 1) ? e[A0] - 1 : 0;
+        p[A1] = (which & 2) ? e[A1] - 1 : 0;
+    }
+    a.n1[comp][lin(p[0], p[1], p[2], sy, sz)] = mur_point_value<C>(a, cf, sy, sz, comp, p);
+}
+
+// The step tail, one launch of 1-D blocks of kTailThreads: blocks [0, ncomp nbe) the Mur edges and
+// then the 8 corners of component b / nbe (their face and edge neighbours evaluated in place);
+// then npw blocks of the power step (plane points); then npt blocks of the next step's phase
+// tables (node planes); then nbb blocks that reduce the push's block records into the deposit box
+// (the whole box and its z chunks' xy boxes); then the Mur faces f >= face0, per normal axis as
+// many blocks per side and component as its largest face needs, which go last so that the others
+// are scheduled first.  The face blocks leave without arriving; the last of the others to finish
+// adds the power partials (compensated, in a fixed order) into the step's series entry once the
+// window is complete, and advances the step state: nothing after this launch in the step reads
+// it.
 
 constexpr int kBoxRecs = 4 * kTailThreads;   // push records per deposit-box block of the tail
 constexpr int kBoxWin = 64;                  // z chunks per block kept in shared memory
@@ -364,10 +376,12 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
                     mur_point<1>(a, cf, sy, sz, comp, c, pos);
                 else
                     mur_point<2>(a, cf, sy, sz, comp, c, pos);
+                t = -1;
                 break;
             }
             t -= 4 * len;
         }
+        if (t >= 0 && t < 8) mur_point<3>(a, cf, sy, sz, comp, (int)t, 0);   // the 8 corners after the edges
     } else if (b < ne + npw) {
         const StepDev sd = *tl.sd;
         const int64_t pl = (int64_t)(b - ne) * blockDim.x + threadIdx.x;
@@ -470,8 +484,6 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
             }
     }
     if (last_block(counter, (unsigned)nrest)) {
-        const int c = (int)threadIdx.x >> 3;
-        if (c < a.ncomp) mur_point<3>(a, cf, sy, sz, c, (int)(threadIdx.x & 7), 0);
         const StepDev sd = *tl.sd;
         if (npw > 0 && sd.emit) {
             double s = 0.0, comp = 0.0;
@@ -968,7 +980,8 @@ cudaError_t launch_mur(const FieldLevels<real>& L, const Geom& g, int order, int
         nf[ax] = (rows + kFaceRows - 1) / kFaceRows;
     }
     const MurEdgeCoef<real> ec = mur_edge_coef<real>(g);
-    const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2));
+    // edge points of the widest component, then its 8 corners
+    const int64_t edges = 4 * ((int64_t)(g.nx - 2) + (g.ny - 2) + (g.nz - 2)) + 8;
     const int nbe = (int)((edges + kTailThreads - 1) / kTailThreads);
     const int64_t plane = (int64_t)g.nx * g.ny;
     const int npw = (int)((plane + kTailThreads - 1) / kTailThreads);
