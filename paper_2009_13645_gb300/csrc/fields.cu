@@ -391,9 +391,11 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
     } else if (b < ne + npw + npt) {
         const int iz = (b - ne - npw) * (int)blockDim.x + (int)threadIdx.x;
         if (iz < tl.phase.nz) {
-            // the next step's lab offset, from the same function that advances the state below
+            // the next step's lab offset, from the same function that gives the next state; the
+            // first thread also leaves that state for the last block
             const StepDev nx = step_state(tl.sd->next, tl.sc);
             phase_tables_entry(tl.phase, nx.Z0, iz);
+            if (iz == 0) tl.sd[1] = nx;
         }
     } else {
         // the deposit box from the push's block records: this block takes kBoxRecs consecutive
@@ -498,7 +500,15 @@ __global__ void __launch_bounds__(kTailThreads) k_step_tail(MurArgs<real> a, Mur
         }
         __syncthreads();   // every thread of this block has read the state
         if (threadIdx.x == 0) {
-            *tl.sd = step_state(sd.next, tl.sc);
+            if (npt > 0) {
+                // formed by the phase-table blocks (their writes are visible: read through L2)
+                const unsigned long long* src = reinterpret_cast<const unsigned long long*>(tl.sd + 1);
+                unsigned long long* dst = reinterpret_cast<unsigned long long*>(tl.sd);
+                static_assert(sizeof(StepDev) % 8 == 0, "whole 8-byte words");
+                for (int w = 0; w < (int)(sizeof(StepDev) / 8); ++w) dst[w] = __ldcg(src + w);
+            } else {
+                *tl.sd = step_state(sd.next, tl.sc);
+            }
             *counter = 0;
         }
     }

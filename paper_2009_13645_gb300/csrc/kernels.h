@@ -242,7 +242,7 @@ struct StepTail {
     double* partial;        // power block partials (at most npartial)
     int npartial;
     PhaseTables phase;      // the tables of step n + 1
-    StepDev* sd;
+    StepDev* sd;            // the step state; sd[1]: the next one, written by the phase-table blocks
     StepConst sc;
     const int* box_rec;     // the push's per-block bounds (nrec records of six ints)
     int64_t nrec;

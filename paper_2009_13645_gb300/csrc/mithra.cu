@@ -455,8 +455,9 @@ struct RunT final : mithra_run {
         if (!(counters = (unsigned*)mem.get(2 * sizeof(unsigned))))
             return fail(MITHRA_ENOMEM, "device allocation failed (counters)");
         CU(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), stream));
-        if (!(sd = (StepDev*)mem.get(sizeof(StepDev)))) return fail(MITHRA_ENOMEM, "device allocation failed (step state)");
-        CU(cudaMemsetAsync(sd, 0, sizeof(StepDev), stream));   // the counter starts at step 0
+        // the state and, in sd[1], the next step's, formed by the step tail's phase-table blocks
+        if (!(sd = (StepDev*)mem.get(2 * sizeof(StepDev)))) return fail(MITHRA_ENOMEM, "device allocation failed (step state)");
+        CU(cudaMemsetAsync(sd, 0, 2 * sizeof(StepDev), stream));   // the counter starts at step 0
         scst.T0 = d.T0;
         scst.dt = d.dt;
         scst.g0 = d.g0;
