@@ -576,22 +576,26 @@ def main():
         del pinned_out
 
     # ---- end to end through the C ABI from pinned host memory -------------------------------
+    # the median of three whole runs (a single one of about 8 ms varies by several per cent with
+    # the host)
     pinned = torch.empty(lab.shape, dtype=torch.float64, pin_memory=True)
     pinned.numpy()[:] = lab
-    barrier()
-    t0 = time.perf_counter()
-    b = m.Bunch()
-    b.n = lab.shape[0]
-    b.charge_e, b.gamma, b.sig_z = w.charge_e, w.gamma, w.sig_z
     import ctypes
-    b.lab_particles = ctypes.cast(ctypes.c_void_p(pinned.data_ptr()), ctypes.POINTER(ctypes.c_double))
-    run = m.Run(m.grid_from(w, 1), m.undulator_from(w), b)
-    run.step(K)
-    p_ser, t_ser, _ = run.series()
-    fe, bunch = run.diag()
-    t_e2e = time.perf_counter() - t0
-    run.close()
-    t_e2e = reduce_max(t_e2e)
+    t_runs = []
+    for _ in range(3):
+        barrier()
+        t0 = time.perf_counter()
+        b = m.Bunch()
+        b.n = lab.shape[0]
+        b.charge_e, b.gamma, b.sig_z = w.charge_e, w.gamma, w.sig_z
+        b.lab_particles = ctypes.cast(ctypes.c_void_p(pinned.data_ptr()), ctypes.POINTER(ctypes.c_double))
+        run = m.Run(m.grid_from(w, 1), m.undulator_from(w), b)
+        run.step(K)
+        p_ser, t_ser, _ = run.series()
+        fe, bunch = run.diag()
+        t_runs.append(time.perf_counter() - t0)
+        run.close()
+    t_e2e = reduce_max(sorted(t_runs)[1])
     h2d = lab.nbytes
     d2h = 2 * 8 * K + 8 * 4
 
@@ -717,7 +721,7 @@ def main():
         "large_runs": big or None,
         "e2e": {"value": whole_job_rate(ws, cells, K, t_e2e * 1e3), "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K, "what": "mithra_create from pinned host particles (H2D), "
-                f"{K} steps, power series + diagnostics to host (D2H)"},
+                f"{K} steps, power series + diagnostics to host (D2H); median of three runs"},
         "served": served,
         "gpu_launches": launches,
         "clocks": clocks,
